@@ -1,0 +1,306 @@
+#!/usr/bin/env python3
+"""Benchmark of the multi-tone synthesis hot path on GB300.
+
+Workload (the one the headline metric is quoted on): 1000 tones, each chirped from a seeded
+frequency to a seeded target in 80-180 MHz over 35 ms at 280 MS/s (9.8M samples); even tones
+linear, odd tones minimum-jerk; amplitudes U[0.5, 1]/1000; int16 output in 2^18-sample chunks.
+
+One step = the whole record rendered chunk by chunk through the C ABI (per chunk: the chirp
+tile set-up kernel and the render kernel with its fused quantise-and-store).  `value` is
+tone-samples per second with the tone state resident on the device; `e2e` repeats the step
+through the public API from host arrays (set_tones + set_chirps, then rendering straight into
+pinned host memory).  The CPU oracle is timed on the host cores on a bounded window of the same
+workload (`cpu_baseline`); `--impl reference` times only that oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "tone-samples/s and max real-time tones at 280 MS/s; p50/p99 chunk latency at ≤1 LSB"
+UNIT = "tone-samples/s"
+# Paper (Playback pathway, Quadro RTX 6000): 1000 tones chirped for 35 ms at 280 MS/s computed in
+# 610 ms, i.e. 9.8e9 / 0.61 tone-samples/s.  Context, another machine.
+PAPER_TONE_SAMPLES_PER_S = 9.8e9 / 0.610
+# SFU peak used as the roofline denominator of the render kernel: 16 sine results per clock per SM
+# x 152 SMs x 2070 MHz maximum SM clock.
+SFU_SIN_PER_CLK_SM = 16
+N_SM = 152
+SM_MAX_MHZ = 2070.0
+# DRAM traffic of one render launch (2^18-sample chunk, 1000 chirping tones) from the ncu capture
+# summarised in profiles/; None until a capture of the current kernel exists.
+RENDER_TRAFFIC_BYTES = None
+
+CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+                "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+def workload():
+    from paper_2403_15582_gb300 import workloads as wl
+    return wl.chirp_1000(seed=0)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(CLOCK_FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(CLOCK_FIELDS):
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            for name, v in zip(names, s[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        pw = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples),
+                "power_w_max": max(pw) if pw else None}
+
+
+def oracle_window_rate(wk, seconds: float, n0: int | None = None):
+    """Time the CPU oracle (all host cores) on a window of the workload sized for ~`seconds`."""
+    import oracle
+    oracle.build()
+    w = oracle.make_waveform(wk.fs, wk.freq_hz, wk.amp, wk.phase_rad, wk.chirps, grid_log2=wk.grid_log2)
+    nthreads = os.cpu_count() or 1
+    start = wk.n_samples // 2 if n0 is None else n0
+    probe = 4096
+    t0 = time.perf_counter()
+    oracle.render(w, start, probe, nthreads=nthreads)
+    dt = max(time.perf_counter() - t0, 1e-6)
+    n = int(min(max(probe, probe * seconds / dt), wk.n_samples - start))
+    t0 = time.perf_counter()
+    oracle.render(w, start, n, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    used = oracle.render.last_threads
+    return {"value": wk.K * n / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": f"{wk.K} tones x {n} samples from sample {start} (FP64 direct sum, 192-bit chirp cascade)",
+            "seconds": dt}
+
+
+def run_reference(args, wk):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    w = oracle.make_waveform(wk.fs, wk.freq_hz, wk.amp, wk.phase_rad, wk.chirps, grid_log2=wk.grid_log2)
+    nthreads = os.cpu_count() or 1
+    start = wk.n_samples // 2
+    t0 = time.perf_counter()
+    oracle.render(w, start, 4096, nthreads=nthreads)
+    rate = 4096 * wk.K / max(time.perf_counter() - t0, 1e-6)
+    per_step = int(min(max(4096, rate * 2.0 / wk.K), wk.n_samples - start))   # ~2 s per step
+    for _ in range(args.warmup):
+        oracle.render(w, start, per_step, nthreads=nthreads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.render(w, start, per_step, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    value = wk.K * per_step * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": value / PAPER_TONE_SAMPLES_PER_S,
+            "dtype": "f64", "data": "synthetic", "config": config(wk, args),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.render.last_threads, "kind": "oracle",
+                             "sample": f"{wk.K} tones x {per_step} samples per step from sample {start}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config(wk, args):
+    return {"workload": "chirp-1000tone-35ms-280MSps", "tones": wk.K, "samples": wk.n_samples, "chunk": wk.chunk,
+            "fs_hz": wk.fs, "profiles": "linear (even tones) / minimum-jerk (odd tones)",
+            "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{args.gpus}"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wk = workload()
+    if args.impl == "reference":
+        return run_reference(args, wk)
+
+    import numpy as np
+    import torch
+    import paper_2403_15582_gb300 as awg
+    from paper_2403_15582_gb300 import build as awg_build
+    awg_build.build()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist = dist_
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    N, chunk, K = wk.n_samples, wk.chunk, wk.K
+    tone, f0, f1, dur, prof, start = wk.chirp_arrays()
+    synth = awg.Synth(wk.fs)
+    synth.set_tones(wk.freq_hz, wk.amp, wk.phase_rad)
+    synth.set_chirps(tone, f0, f1, dur, prof, start)
+    out = torch.empty(N, dtype=torch.int16, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step_device():
+        synth.seek(0)
+        for c0 in range(0, N, chunk):
+            synth.render(min(chunk, N - c0), out[c0:], stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step_device()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    synth.profile_begin()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step_device()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    prep_ms, render_ms, launches = synth.profile_end()
+    sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    work_per_step = K * N
+    value = world * work_per_step * args.steps / (total_ms * 1e-3)
+    status = synth.device_status()
+
+    # e2e through the public API from host arrays into pinned host memory
+    out_host = torch.empty(N, dtype=torch.int16, pin_memory=True)
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        synth.set_tones(wk.freq_hz, wk.amp, wk.phase_rad)
+        synth.set_chirps(tone, f0, f1, dur, prof, start)
+        synth.seek(0)
+        for c0 in range(0, N, chunk):
+            synth.render(min(chunk, N - c0), out_host[c0:], stream)
+        stream.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = sum(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * work_per_step * args.steps / (e2e_total * 1e-3)
+    h2d = K * (2 * 64 + 208)     # tone records twice (set_tones, set_chirps) + chirp records
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (render): one SFU sine per tone-sample
+    chunk_sizes = [min(chunk, N - c0) for c0 in range(0, N, chunk)] * args.steps
+    render_total_s = float(np.sum(render_ms)) * 1e-3
+    achieved = K * float(np.sum(chunk_sizes)) / render_total_s / 1e12
+    peak = SFU_SIN_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12
+    chunk_lat = np.asarray(prep_ms) + np.asarray(render_ms)
+    clocks = sampler.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_TONE_SAMPLES_PER_S, "dtype": "f32", "data": "synthetic",
+        "config": config(wk, args),
+        "max_realtime_tones_280MSps": value / world / 280e6,
+        "output_msps": value / world / K / 1e6,
+        "chunk_latency_ms": {"p50": float(np.percentile(chunk_lat, 50)), "p99": float(np.percentile(chunk_lat, 99)),
+                             "playback_ms": 1e3 * chunk / wk.fs},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tsin/s",
+                     "frac": achieved / peak, "traffic": RENDER_TRAFFIC_BYTES,
+                     "kernel": "render_kernel", "peak_source": "16 SFU sin/clk/SM x 152 SMs x 2070 MHz"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 2 * N},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "device_status": status,
+        "kernel_ms_per_step": {"prep": float(np.sum(prep_ms)) / args.steps,
+                               "render": float(np.sum(render_ms)) / args.steps},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = oracle_window_rate(wk, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

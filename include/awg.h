@@ -1,0 +1,183 @@
+/*
+ * awg.h -- C ABI of a GB300 (sm_103a) multi-tone waveform synthesiser.
+ *
+ * It computes x[n] = sum_k A_k sin(phi_k(n)) (additive synthesis, Sec. II Eq. main and the
+ * dynamic form Eq. dynamicandstatic of Tu & Subhankar, "Fast real-time arbitrary waveform
+ * generation using graphic processing units") for static tones and tones chirped along linear
+ * or minimum-jerk frequency ramps (Eq. freqchirp), and writes scaled int16 DAC samples (and,
+ * on request, the FP32 sum) chunk by chunk.
+ *
+ * Phase model.  A tone's phase is an integer word Phi in units of 2^-64 turn.  Static tones:
+ * Phi(n) = Phi_ref + n*F (mod 2^64).  A chirp over samples n_s..n_s+L follows a degree <= 6
+ * polynomial held as seven 2^128-scaled forward differences (192-bit words); its phase words
+ * are exact integers, the same ones a sequential 192-bit accumulator cascade produces, so
+ * there is no drift over arbitrarily long streams.  After the chirp the tone is static at the
+ * end frequency, continuing from the phase reached at n_s+L (Eq. freqchirp case 2).
+ *
+ * Conventions for every call below:
+ *  - Return value: AWG_OK (0) or a negative AWG_E* code; awg_last_error() then returns a
+ *    thread-local message.  A failed call leaves the handle unchanged.
+ *  - Host arrays passed in are read during the call only (copied); the caller keeps ownership.
+ *  - `out` pointers are caller-owned device memory, or pinned host memory that is mapped into
+ *    the device address space (cudaHostAlloc with cudaHostAllocMapped, or any pinned memory on
+ *    a system with unified addressing); they are written asynchronously on `stream`.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - One handle must not be used from two host threads at once, and the renders of one handle
+ *    must be issued to one stream (or ordered by the caller).
+ *  - Sample indices are absolute (int64, counted from 0 at creation).
+ */
+#ifndef AWG_H
+#define AWG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct awg awg_t;
+
+enum {
+  AWG_OK = 0,
+  AWG_EINVAL = -1,    /* bad argument: see awg_last_error() */
+  AWG_ENOMEM = -2,    /* device or pinned-host allocation failed, or a fixed capacity is full */
+  AWG_ECUDA = -3,     /* a CUDA runtime call failed */
+  AWG_ETIMEOUT = -4,  /* a bounded wait in a kernel gave up (status word set on the device) */
+  AWG_EDEADLINE = -5, /* admission refused: the request cannot meet its deadline */
+  AWG_ESTATE = -6     /* call not valid in the handle's current state */
+};
+
+enum { AWG_PROFILE_LINEAR = 0, AWG_PROFILE_MINJERK = 1 };
+
+/* Version of this ABI (major*10000 + minor*100 + patch). */
+int awg_version(void);
+
+/* Message describing the last failing call on this host thread ("" if none). */
+const char* awg_last_error(void);
+
+/* ------------------------------------------------------------------------------------------
+ * Host-only set-up arithmetic (no GPU involved).  These are the exact rules the library uses
+ * internally; they are exported so that callers and tests can reproduce the words.
+ * ---------------------------------------------------------------------------------------- */
+
+/* Frequency word F = rint(f/fs * 2^64) mod 2^64 (IEEE double quotient, ties to even).
+ * Tone frequency of Eq. main as a per-sample phase step.  EINVAL if fs is not finite and > 0,
+ * or f is not finite, or f < 0 or f >= fs (a tone above fs/2 is rendered as its alias). */
+int awg_freq_word(double f_hz, double fs_hz, uint64_t* out_word);
+
+/* Phase word Phi0 = rint(frac(theta / 2pi) * 2^64) mod 2^64 (theta_j of Eq. main).
+ * EINVAL if theta is not finite. */
+int awg_phase_word(double theta_rad, uint64_t* out_word);
+
+/* Grid word of Eq. freqapprox: j = rint(f/fs * 2^log2_len), F = j << (64 - log2_len), so that
+ * the tone completes exactly j cycles in 2^log2_len samples.  1 <= log2_len <= 40.
+ * out_j may be NULL. */
+int awg_grid_word(double f_hz, double fs_hz, int32_t log2_len, uint64_t* out_word, int64_t* out_j);
+
+/* Chirp length L = rint(duration * fs) samples; the chirp spans m = 0..L (Eq. freqchirp case 1,
+ * 0 <= i <= T f_s).  EINVAL unless 1 <= L <= 2^28 - 1. */
+int awg_chirp_length(double duration_s, double fs_hz, int64_t* out_L);
+
+/* The seven 192-bit forward-difference words d_0..d_6 of a chirp from word F_start to word F_end
+ * over L samples (profile AWG_PROFILE_LINEAR or AWG_PROFILE_MINJERK).  With P(m) the chirp phase
+ * in words relative to its start (min-jerk: P(m) = F_start m + D (5 m^4 L^2 - 6 m^5 L + 2 m^6) /
+ * (2 L^5), Eq. freqchirp; linear: P(m) = F_start m + D m^2 / (2L), D = F_end - F_start as a
+ * signed integer), d_k = rint_half_even(Delta^k P(0) * 2^128) mod 2^192 for k >= 1 and
+ * d_0 = 2^127.  out: 21 uint64, little-endian limbs, d_0 first. */
+int awg_chirp_coeffs(uint64_t F_start, uint64_t F_end, int64_t L, int32_t profile, uint64_t* out21);
+
+/* ------------------------------------------------------------------------------------------
+ * Synthesiser handle (device-resident tone and chirp state).
+ * ---------------------------------------------------------------------------------------- */
+
+/* Create a handle for sample rate fs (Hz) on the current CUDA device.  NULL on error. */
+awg_t* awg_create(double sample_rate_hz);
+
+/* Release the handle and its device memory (waits for its in-flight work). NULL is allowed. */
+void awg_destroy(awg_t* h);
+
+/* Replace the tone set: n tones with frequency (Hz, in [0, fs)), amplitude (finite) and initial
+ * phase (rad, the phase at sample 0).  Clears all chirps.  n = 0 is allowed (silence).
+ * Full scale returns to its default (sum |A|) unless set explicitly afterwards. */
+int awg_set_tones(awg_t* h, const double* freq_hz, const double* amp, const double* phase_rad, int32_t n);
+
+/* As awg_set_tones, with each frequency snapped to the f_s / 2^log2_len grid (Eq. freqapprox),
+ * so that the record of 2^log2_len samples is exactly periodic. */
+int awg_set_tones_grid(awg_t* h, const double* freq_hz, int32_t log2_len, const double* amp,
+                       const double* phase_rad, int32_t n);
+
+/* Schedule n chirps.  Chirp i moves tone[i] from f_start[i] to f_end[i] (Hz, each in [0, fs))
+ * over duration[i] seconds (L = rint(duration fs) samples, 1 <= L < 2^28) with the given
+ * profile, starting at absolute sample start_sample[i] from the tone's phase at that sample
+ * (a start frequency that differs from the tone's current frequency is a frequency step).
+ * A tone holds one chirp at a time: a new chirp on a tone is accepted once the render cursor
+ * has passed that tone's previous chirp (previous n_s + L < cursor); the previous chirp's end
+ * state then becomes the tone's static state.  Every chirp must start at or after the cursor,
+ * and one call may hold at most one chirp per tone.
+ * EINVAL on any violation (nothing is applied); ENOMEM if device memory runs out. */
+int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, const double* f_end_hz,
+                   const double* duration_s, const int32_t* profile, const int64_t* start_sample,
+                   int32_t n);
+
+/* Full-scale value FS that maps to int16 code 32767 (q = clamp(rint(x * 32767/FS), +-32767)).
+ * fs_value <= 0 restores the default sum |A_k|, which can never clip. */
+int awg_set_full_scale(awg_t* h, double fs_value);
+
+/* Current full-scale value. */
+double awg_full_scale(const awg_t* h);
+
+/* Move the render cursor to an absolute sample (>= 0).  Rendering depends only on absolute
+ * indices and the current tone and chirp state, so seeking back reproduces earlier output bit
+ * for bit as long as no chirp set since then has folded an earlier chirp of the same tone. */
+int awg_seek(awg_t* h, int64_t sample);
+
+/* The render cursor (next sample awg_render writes), or -1 for NULL. */
+int64_t awg_cursor(const awg_t* h);
+
+/* Render samples cursor .. cursor+n-1 as int16 codes into out[0..n) on `stream`, then advance
+ * the cursor by n.  Asynchronous.  Output is a function of the absolute sample index and the
+ * tone set only: render(a) followed by render(b) equals render(a+b) bit for bit. */
+int awg_render(awg_t* h, int64_t n, int16_t* out, void* stream);
+
+/* As awg_render, also writing the FP32 sum x[n] (unscaled) to out_f32 (out_q may be NULL). */
+int awg_render_f32(awg_t* h, int64_t n, float* out_f32, int16_t* out_q, void* stream);
+
+/* Phase words Phi_k(sample) of the first n tones (n <= tone count), computed on the device by the
+ * exact closed form (192-bit, the function that seeds every render tile) and copied to
+ * out_host.  Synchronous. */
+int awg_phase_words(awg_t* h, int64_t sample, uint64_t* out_host, int32_t n);
+
+/* Per-sample 32-bit phases (units of 2^-32 turn, plus the 2^8 rounding offset of the sine
+ * argument) that the render kernel feeds to the sine for tone `tone` at samples
+ * cursor-independent [n0, n0+count), count <= 2^20; out_host receives count uint32.  For
+ * checking the in-tile phase approximation against exact words.  Synchronous. */
+int awg_render_phases(awg_t* h, int32_t tone, int64_t n0, int32_t count, uint32_t* out_host);
+
+/* Tile split used for this handle's tone count: tones are summed in this many partial sums per
+ * tile (thread-block cluster size).  For information. */
+int32_t awg_tone_split(const awg_t* h);
+
+/* Sum of the device time (ms) of the last render's kernels, recorded with CUDA events; it is
+ * valid once that render has completed (e.g. after synchronising its stream).  -1 if none. */
+float awg_last_render_ms(awg_t* h);
+
+/* Profiling mode: while on, every render records CUDA events on its stream before its chirp
+ * set-up kernel, between the kernels and after the render kernel.  awg_profile_begin clears the
+ * record.  awg_profile_end waits for the last recorded event, writes per render call the device
+ * time (ms) of the set-up kernel(s) and of the render kernel into prep_ms[i] / render_ms[i] for
+ * i < cap (either may be NULL), stores the number of kernels launched in *launches (may be NULL),
+ * stops recording and returns the number of render calls recorded (or a negative AWG_E* code). */
+int awg_profile_begin(awg_t* h);
+int awg_profile_end(awg_t* h, float* prep_ms, float* render_ms, int32_t cap, int64_t* launches);
+
+/* Device-side status word of the handle: 0, or the AWG_E* code a kernel raised (for instance
+ * AWG_ETIMEOUT when a bounded wait on an mbarrier gave up).  Reading it synchronises.  Clears
+ * the word. */
+int awg_device_status(awg_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AWG_H */

@@ -1,0 +1,15 @@
+"""GB300 (sm_103a) multi-tone additive synthesis: Python binding of the C ABI in include/awg.h.
+
+The binding marshals arguments only; every step of the synthesis runs in the CUDA library
+(libawg.so, built in-tree by ``paper_2403_15582_gb300.build``).  There is no CPU fallback: if the
+library is missing, importing the binding's entry points raises.
+"""
+from __future__ import annotations
+
+from .binding import (AWG_EDEADLINE, AWG_EINVAL, AWG_ENOMEM, AWG_ECUDA, AWG_ESTATE, AWG_ETIMEOUT, AWG_OK,
+                      PROFILE_LINEAR, PROFILE_MINJERK, AwgError, Synth, chirp_coeffs, chirp_length, freq_word,
+                      grid_word, lib, phase_word)
+
+__all__ = ["Synth", "AwgError", "lib", "freq_word", "phase_word", "grid_word", "chirp_length", "chirp_coeffs",
+           "PROFILE_LINEAR", "PROFILE_MINJERK", "AWG_OK", "AWG_EINVAL", "AWG_ENOMEM", "AWG_ECUDA", "AWG_ETIMEOUT",
+           "AWG_EDEADLINE", "AWG_ESTATE"]

@@ -1,0 +1,239 @@
+"""ctypes binding of libawg.so (include/awg.h).  Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libawg.so")
+
+AWG_OK, AWG_EINVAL, AWG_ENOMEM, AWG_ECUDA, AWG_ETIMEOUT, AWG_EDEADLINE, AWG_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PROFILE_LINEAR, PROFILE_MINJERK = 0, 1
+
+# (name, restype, argtypes) of every symbol declared in include/awg.h
+P, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+SIGNATURES = [
+    ("awg_version", ctypes.c_int, []),
+    ("awg_last_error", ctypes.c_char_p, []),
+    ("awg_freq_word", ctypes.c_int, [dbl, dbl, P]),
+    ("awg_phase_word", ctypes.c_int, [dbl, P]),
+    ("awg_grid_word", ctypes.c_int, [dbl, dbl, i32, P, P]),
+    ("awg_chirp_length", ctypes.c_int, [dbl, dbl, P]),
+    ("awg_chirp_coeffs", ctypes.c_int, [u64, u64, i64, i32, P]),
+    ("awg_create", P, [dbl]),
+    ("awg_destroy", None, [P]),
+    ("awg_set_tones", ctypes.c_int, [P, P, P, P, i32]),
+    ("awg_set_tones_grid", ctypes.c_int, [P, P, i32, P, P, i32]),
+    ("awg_set_chirps", ctypes.c_int, [P, P, P, P, P, P, P, i32]),
+    ("awg_set_full_scale", ctypes.c_int, [P, dbl]),
+    ("awg_full_scale", dbl, [P]),
+    ("awg_seek", ctypes.c_int, [P, i64]),
+    ("awg_cursor", i64, [P]),
+    ("awg_render", ctypes.c_int, [P, i64, P, P]),
+    ("awg_render_f32", ctypes.c_int, [P, i64, P, P, P]),
+    ("awg_phase_words", ctypes.c_int, [P, i64, P, i32]),
+    ("awg_render_phases", ctypes.c_int, [P, i32, i64, i32, P]),
+    ("awg_tone_split", i32, [P]),
+    ("awg_last_render_ms", ctypes.c_float, [P]),
+    ("awg_profile_begin", ctypes.c_int, [P]),
+    ("awg_profile_end", ctypes.c_int, [P, P, P, i32, P]),
+    ("awg_device_status", ctypes.c_int, [P]),
+]
+
+_lib = None
+
+
+class AwgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"awg error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libawg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2403_15582_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != AWG_OK:
+        raise AwgError(code, lib().awg_last_error().decode())
+    return code
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def freq_word(f_hz: float, fs: float) -> int:
+    out = np.zeros(1, dtype=np.uint64)
+    _check(lib().awg_freq_word(float(f_hz), float(fs), _p(out)))
+    return int(out[0])
+
+
+def phase_word(theta: float) -> int:
+    out = np.zeros(1, dtype=np.uint64)
+    _check(lib().awg_phase_word(float(theta), _p(out)))
+    return int(out[0])
+
+
+def grid_word(f_hz: float, fs: float, log2_len: int):
+    out = np.zeros(1, dtype=np.uint64)
+    j = np.zeros(1, dtype=np.int64)
+    _check(lib().awg_grid_word(float(f_hz), float(fs), int(log2_len), _p(out), _p(j)))
+    return int(out[0]), int(j[0])
+
+
+def chirp_length(duration: float, fs: float) -> int:
+    out = np.zeros(1, dtype=np.int64)
+    _check(lib().awg_chirp_length(float(duration), float(fs), _p(out)))
+    return int(out[0])
+
+
+def chirp_coeffs(F_start: int, F_end: int, L: int, profile: int) -> list[int]:
+    out = np.zeros(21, dtype=np.uint64)
+    _check(lib().awg_chirp_coeffs(int(F_start), int(F_end), int(L), int(profile), _p(out)))
+    return [int(out[3 * k]) | (int(out[3 * k + 1]) << 64) | (int(out[3 * k + 2]) << 128) for k in range(7)]
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _ptr(t):
+    if t is None:
+        return ctypes.c_void_p(0)
+    if hasattr(t, "data_ptr"):
+        return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(int(t))
+
+
+class Synth:
+    """One synthesiser handle (awg_t*).  Outputs are torch tensors (device or pinned host)."""
+
+    def __init__(self, sample_rate: float):
+        h = lib().awg_create(float(sample_rate))
+        if not h:
+            raise AwgError(AWG_ECUDA, lib().awg_last_error().decode())
+        self._h = ctypes.c_void_p(h)
+        self.fs = float(sample_rate)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().awg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def set_tones(self, freq_hz, amp, phase_rad, grid_log2: int | None = None):
+        f, a, ph = _f64(freq_hz), _f64(amp), _f64(phase_rad)
+        if grid_log2:
+            _check(lib().awg_set_tones_grid(self._h, _p(f), int(grid_log2), _p(a), _p(ph), int(f.size)))
+        else:
+            _check(lib().awg_set_tones(self._h, _p(f), _p(a), _p(ph), int(f.size)))
+
+    def set_chirps(self, tone, f_start, f_end, duration, profile, start_sample):
+        t = np.ascontiguousarray(np.asarray(tone, dtype=np.int32))
+        f0, f1, du = _f64(f_start), _f64(f_end), _f64(duration)
+        pr = np.ascontiguousarray(np.asarray(profile, dtype=np.int32))
+        st = np.ascontiguousarray(np.asarray(start_sample, dtype=np.int64))
+        _check(lib().awg_set_chirps(self._h, _p(t), _p(f0), _p(f1), _p(du), _p(pr), _p(st), int(t.size)))
+
+    def set_chirp_list(self, chirps):
+        if not chirps:
+            return
+        self.set_chirps([c["tone"] for c in chirps], [c["f_start"] for c in chirps], [c["f_end"] for c in chirps],
+                        [c["duration"] for c in chirps], [c["profile"] for c in chirps],
+                        [c.get("start_sample", 0) for c in chirps])
+
+    def set_full_scale(self, v: float):
+        _check(lib().awg_set_full_scale(self._h, float(v)))
+
+    @property
+    def full_scale(self) -> float:
+        return float(lib().awg_full_scale(self._h))
+
+    def seek(self, sample: int):
+        _check(lib().awg_seek(self._h, int(sample)))
+
+    @property
+    def cursor(self) -> int:
+        return int(lib().awg_cursor(self._h))
+
+    @property
+    def tone_split(self) -> int:
+        return int(lib().awg_tone_split(self._h))
+
+    def render(self, n: int, out, stream=None):
+        _check(lib().awg_render(self._h, int(n), _ptr(out), _stream_ptr(stream)))
+
+    def render_f32(self, n: int, out_f32, out_q=None, stream=None):
+        _check(lib().awg_render_f32(self._h, int(n), _ptr(out_f32), _ptr(out_q), _stream_ptr(stream)))
+
+    def phase_words(self, sample: int, n: int) -> np.ndarray:
+        out = np.zeros(n, dtype=np.uint64)
+        _check(lib().awg_phase_words(self._h, int(sample), _p(out), int(n)))
+        return out
+
+    def render_phases(self, tone: int, n0: int, count: int) -> np.ndarray:
+        out = np.zeros(count, dtype=np.uint32)
+        _check(lib().awg_render_phases(self._h, int(tone), int(n0), int(count), _p(out)))
+        return out
+
+    def last_render_ms(self) -> float:
+        return float(lib().awg_last_render_ms(self._h))
+
+    def profile_begin(self):
+        _check(lib().awg_profile_begin(self._h))
+
+    def profile_end(self, cap: int = 1 << 16):
+        """-> (prep_ms array, render_ms array, kernel launches) of the render calls since begin."""
+        prep = np.zeros(cap, dtype=np.float32)
+        rend = np.zeros(cap, dtype=np.float32)
+        launches = np.zeros(1, dtype=np.int64)
+        n = lib().awg_profile_end(self._h, _p(prep), _p(rend), int(cap), _p(launches))
+        if n < 0:
+            _check(n)
+        n = min(n, cap)
+        return prep[:n].copy(), rend[:n].copy(), int(launches[0])
+
+    def device_status(self) -> int:
+        v = lib().awg_device_status(self._h)
+        return int(v)

@@ -1,0 +1,880 @@
+// Host side of the C ABI (include/awg.h): tone and chirp set-up in exact integer arithmetic,
+// device-resident state, and kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/awg.h"
+#include "awg_internal.h"
+
+using awgk::ChirpRec;
+using awgk::TileRec;
+using awgk::ToneRec;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(AWG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+typedef unsigned __int128 u128;
+typedef __int128 s128;
+
+// ------------------------------------------------------------------------------------------
+// 192-bit words (mod 2^192) and a small unsigned bigint for exact set-up
+// ------------------------------------------------------------------------------------------
+struct W192 {
+  uint64_t w[3];
+};
+
+W192 w_add(W192 a, W192 b) {
+  W192 r;
+  u128 c = 0;
+  for (int i = 0; i < 3; ++i) {
+    c += (u128)a.w[i] + b.w[i];
+    r.w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+  return r;
+}
+W192 w_neg(W192 a) {
+  W192 r;
+  u128 c = 1;
+  for (int i = 0; i < 3; ++i) {
+    c += (u128)(~a.w[i]);
+    r.w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+  return r;
+}
+W192 w_mul(W192 a, W192 b) {
+  W192 r = {{0, 0, 0}};
+  for (int i = 0; i < 3; ++i) {
+    u128 c = 0;
+    for (int j = 0; i + j < 3; ++j) {
+      c += (u128)a.w[i] * b.w[j] + r.w[i + j];
+      r.w[i + j] = (uint64_t)c;
+      c >>= 64;
+    }
+  }
+  return r;
+}
+W192 w_from_u64(uint64_t v) { return W192{{v, 0, 0}}; }
+W192 w_from_s64(int64_t v) {
+  uint64_t s = (uint64_t)(v >> 63);
+  return W192{{(uint64_t)v, s, s}};
+}
+
+// Unsigned little-endian multi-limb integer (up to 8 limbs).
+struct Big {
+  uint64_t l[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+Big big_from_u128(u128 v) {
+  Big b;
+  b.l[0] = (uint64_t)v;
+  b.l[1] = (uint64_t)(v >> 64);
+  return b;
+}
+Big big_mul_u128(const Big& a, u128 m) {   // a * m, m < 2^128
+  Big r;
+  uint64_t m0 = (uint64_t)m, m1 = (uint64_t)(m >> 64);
+  for (int part = 0; part < 2; ++part) {
+    uint64_t mm = part ? m1 : m0;
+    if (!mm) continue;
+    u128 c = 0;
+    for (int i = 0; i + part < 8; ++i) {
+      c += (u128)a.l[i] * mm + r.l[i + part];
+      r.l[i + part] = (uint64_t)c;
+      c >>= 64;
+    }
+  }
+  return r;
+}
+Big big_shl(const Big& a, int s) {   // s < 512
+  Big r;
+  int q = s / 64, b = s % 64;
+  for (int i = 7; i >= 0; --i) {
+    uint64_t v = 0;
+    if (i - q >= 0) v = a.l[i - q] << b;
+    if (b && i - q - 1 >= 0) v |= a.l[i - q - 1] >> (64 - b);
+    r.l[i] = v;
+  }
+  return r;
+}
+uint64_t big_divmod_u64(Big& a, uint64_t d) {   // a /= d, returns remainder
+  u128 rem = 0;
+  for (int i = 7; i >= 0; --i) {
+    u128 cur = (rem << 64) | a.l[i];
+    a.l[i] = (uint64_t)(cur / d);
+    rem = cur % d;
+  }
+  return (uint64_t)rem;
+}
+Big big_add(const Big& a, const Big& b) {
+  Big r;
+  u128 c = 0;
+  for (int i = 0; i < 8; ++i) {
+    c += (u128)a.l[i] + b.l[i];
+    r.l[i] = (uint64_t)c;
+    c >>= 64;
+  }
+  return r;
+}
+int big_cmp(const Big& a, const Big& b) {
+  for (int i = 7; i >= 0; --i) {
+    if (a.l[i] != b.l[i]) return a.l[i] < b.l[i] ? -1 : 1;
+  }
+  return 0;
+}
+
+// Delta^k [m^p] at m = 0 = sum_j (-1)^(k-j) C(k,j) j^p  (k! S(p,k), Stirling numbers of the 2nd kind)
+s128 power_difference(int p, int k) {
+  s128 s = 0;
+  s128 binom = 1;   // C(k, j)
+  for (int j = 0; j <= k; ++j) {
+    if (j > 0) binom = binom * (k - j + 1) / j;
+    s128 pw = 1;
+    for (int e = 0; e < p; ++e) pw *= j;
+    s += (((k - j) & 1) ? -1 : 1) * binom * pw;
+  }
+  return s;
+}
+
+// round_half_even( sign * mag * 2^127 / L^pw ), returned mod 2^192
+W192 rounded_quotient(bool negative, const Big& mag, uint64_t L, int pw) {
+  Big num = big_shl(mag, 127);
+  // num = q L^pw + R with R = r1 + r2 L + ... (remainders of the successive divisions)
+  Big q = num;
+  uint64_t rem[5] = {0, 0, 0, 0, 0};
+  for (int i = 0; i < pw; ++i) rem[i] = big_divmod_u64(q, L);
+  Big R;
+  Big Lpow = big_from_u128(1);
+  for (int i = 0; i < pw; ++i) {
+    R = big_add(R, big_mul_u128(Lpow, rem[i]));
+    Lpow = big_mul_u128(Lpow, L);
+  }
+  Big twoR = big_shl(R, 1);
+  int c = big_cmp(twoR, Lpow);
+  if (c > 0 || (c == 0 && (q.l[0] & 1))) q = big_add(q, big_from_u128(1));
+  W192 r = {{q.l[0], q.l[1], q.l[2]}};
+  return negative ? w_neg(r) : r;
+}
+
+// C(m, k) for 0 <= m < 2^28 as an exact 192-bit value (the product of k factors < 2^168)
+W192 binom_w(int64_t m, int k) {
+  if (k == 0) return w_from_u64(1);
+  if (m < k) return w_from_u64(0);
+  Big p = big_from_u128(1);
+  for (int i = 0; i < k; ++i) p = big_mul_u128(p, (u128)(m - i));
+  uint64_t fact = 1;
+  for (int i = 2; i <= k; ++i) fact *= (uint64_t)i;
+  big_divmod_u64(p, fact);
+  return W192{{p.l[0], p.l[1], p.l[2]}};
+}
+
+W192 w_inverse_odd(uint64_t o) {   // o^-1 mod 2^192 by Newton's iteration
+  W192 x = w_from_u64(o);           // correct to 3 bits for odd o
+  W192 two = w_from_u64(2);
+  for (int it = 0; it < 8; ++it) x = w_mul(x, w_add(two, w_neg(w_mul(w_from_u64(o), x))));
+  return x;
+}
+
+// ------------------------------------------------------------------------------------------
+// set-up rules (a1, a2)
+// ------------------------------------------------------------------------------------------
+bool is_fin(double v) { return std::isfinite(v); }
+
+int freq_word_impl(double f, double fs, uint64_t* out) {
+  if (!(is_fin(fs) && fs > 0)) return fail(AWG_EINVAL, "sample rate must be finite and > 0");
+  if (!is_fin(f) || f < 0 || f >= fs) return fail(AWG_EINVAL, "tone frequency must lie in [0, fs)");
+  double r = std::ldexp(f / fs, 64);
+  double w = std::rint(r);
+  *out = (w >= 18446744073709551616.0) ? 0 : (uint64_t)w;
+  return AWG_OK;
+}
+
+int phase_word_impl(double theta, uint64_t* out) {
+  if (!is_fin(theta)) return fail(AWG_EINVAL, "phase must be finite");
+  double t = theta / (2.0 * M_PI);
+  double frac = t - std::floor(t);
+  double w = std::rint(std::ldexp(frac, 64));
+  *out = (w >= 18446744073709551616.0) ? 0 : (uint64_t)w;
+  return AWG_OK;
+}
+
+int chirp_length_impl(double dur, double fs, int64_t* L) {
+  if (!(is_fin(fs) && fs > 0)) return fail(AWG_EINVAL, "sample rate must be finite and > 0");
+  if (!is_fin(dur) || dur <= 0) return fail(AWG_EINVAL, "chirp duration must be finite and > 0");
+  double l = std::rint(dur * fs);
+  if (!(l >= 1 && l <= (double)((1 << 28) - 1))) return fail(AWG_EINVAL, "chirp length must be 1 .. 2^28-1 samples");
+  *L = (int64_t)l;
+  return AWG_OK;
+}
+
+// d_k, k = 0..6 (see awg.h).  With D = F_end - F_start:
+//   min-jerk  P(m) = F_start m + D (5 L^2 m^4 - 6 L m^5 + 2 m^6) / (2 L^5)
+//   linear    P(m) = F_start m + D m^2 / (2 L)
+// Delta^k P(0) = F_start [k = 1] + D N_k / (2 L^pw) with N_k built from Delta^k[m^p](0).
+int chirp_coeffs_impl(uint64_t F0, uint64_t F1, int64_t L, int profile, W192 d[7]) {
+  if (L < 1 || L > (1 << 28) - 1) return fail(AWG_EINVAL, "chirp length must be 1 .. 2^28-1 samples");
+  if (profile != AWG_PROFILE_LINEAR && profile != AWG_PROFILE_MINJERK) return fail(AWG_EINVAL, "unknown chirp profile");
+  const s128 D = (s128)F1 - (s128)F0;
+  d[0] = W192{{0, 1ull << 63, 0}};   // 2^127: rounding offset of the top 64 bits
+  for (int k = 1; k <= 6; ++k) {
+    s128 N;
+    int pw;
+    if (profile == AWG_PROFILE_MINJERK) {
+      N = 5 * (s128)L * L * power_difference(4, k) - 6 * (s128)L * power_difference(5, k) + 2 * power_difference(6, k);
+      pw = 5;
+    } else {
+      N = power_difference(2, k);
+      pw = 1;
+    }
+    W192 v = {{0, 0, 0}};
+    if (N != 0 && D != 0) {
+      bool neg = (N < 0) != (D < 0);
+      u128 aD = (u128)(D < 0 ? -D : D);
+      u128 aN = (u128)(N < 0 ? -N : N);
+      Big mag = big_mul_u128(big_from_u128(aD), aN);
+      v = rounded_quotient(neg, mag, (uint64_t)L, pw);
+    }
+    if (k == 1) v = w_add(v, W192{{0, 0, F0}});   // F_start * 2^128
+    d[k] = v;
+  }
+  return AWG_OK;
+}
+
+// top64 of sum_k d_k C(m, k): the chirp phase in words at offset m (d_0 holds the rounding offset)
+uint64_t chirp_offset_word(const W192 d[7], int64_t m) {
+  W192 s = {{0, 0, 0}};
+  for (int k = 0; k < 7; ++k) s = w_add(s, w_mul(d[k], binom_w(m, k)));
+  return s.w[2];
+}
+
+// Chirps whose neglected 4th..6th-order phase terms over one 32-sample run could exceed 64 units
+// of 2^-32 turn are rendered with the exact per-sample closed form instead.
+bool needs_exact(uint64_t F0, uint64_t F1, int64_t L, int profile) {
+  if (profile == AWG_PROFILE_LINEAR) return false;
+  double D = std::fabs((double)F1 - (double)F0);
+  double l = (double)L;
+  double bound = 31465.0 * 60.0 * D / (l * l * l) + 169911.0 * 360.0 * D / (l * l * l * l) +
+                 736281.0 * 720.0 * D / (l * l * l * l * l);
+  return bound > 64.0 * 4294967296.0;
+}
+
+int pow2_split(int K) {
+  int need = (K + 63) / 64;
+  int s = 1;
+  while (s < need && s < awgk::MAX_SPLIT) s <<= 1;
+  return s;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// handle
+// ==========================================================================================
+struct awg {
+  double fs = 0;
+  int device = 0;
+  int32_t K = 0;
+  std::vector<ToneRec> tones;
+  std::vector<double> amp;
+  std::vector<ChirpRec> chirps;       // slot pool (tone < 0: free)
+  std::vector<int32_t> free_slots;
+  ToneRec* d_tones = nullptr;
+  size_t cap_tones = 0;
+  ChirpRec* d_chirps = nullptr;
+  int32_t* d_act = nullptr;
+  size_t cap_chirps = 0;
+  TileRec* d_recs = nullptr;
+  size_t cap_recs = 0;
+  int32_t* d_status = nullptr;
+  uint64_t* d_words = nullptr;
+  size_t cap_words = 0;
+  uint32_t* d_trace = nullptr;
+  size_t cap_trace = 0;
+  int64_t cursor = 0;
+  double full_scale = 0;
+  bool fs_explicit = false;
+  int split = 1;
+  cudaStream_t priv = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
+  bool timed = false, have_done = false;
+  bool profiling = false;
+  std::vector<cudaEvent_t> prof_ev;   // 3 per recorded render call
+  size_t prof_calls = 0;
+  int64_t prof_launches = 0;
+  int64_t W[7][7];
+  uint64_t inv_odd[3][3];
+};
+
+namespace {
+
+void fill_constants(awg_t* h) {
+  // W[q][i] = Delta^q_j C(j RUN, i) at j = 0
+  for (int q = 0; q < 7; ++q)
+    for (int i = 0; i < 7; ++i) {
+      s128 s = 0, bq = 1;
+      for (int l = 0; l <= q; ++l) {
+        if (l > 0) bq = bq * (q - l + 1) / l;
+        s128 c = 1;   // C(l RUN, i)
+        int64_t m = (int64_t)l * awgk::RUN;
+        if (i > m) c = 0;
+        else
+          for (int t = 0; t < i; ++t) c = c * (m - t) / (t + 1);
+        s += (((q - l) & 1) ? -1 : 1) * bq * c;
+      }
+      h->W[q][i] = (int64_t)s;
+    }
+  const uint64_t odd[3] = {3, 15, 45};
+  for (int i = 0; i < 3; ++i) {
+    W192 x = w_inverse_odd(odd[i]);
+    for (int j = 0; j < 3; ++j) h->inv_odd[i][j] = x.w[j];
+  }
+}
+
+int wait_idle(awg_t* h) {
+  if (h->have_done) {
+    cudaError_t e = cudaEventSynchronize(h->ev_done);
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the last render");
+  }
+  return AWG_OK;
+}
+
+template <class T>
+int ensure(T** ptr, size_t* cap, size_t need, awg_t* h, const char* what) {
+  if (need <= *cap) return AWG_OK;
+  int st = wait_idle(h);
+  if (st) return st;
+  size_t ncap = std::max(need, *cap * 2);
+  T* p = nullptr;
+  cudaError_t e = cudaMalloc((void**)&p, ncap * sizeof(T));
+  if (e != cudaSuccess) return fail(AWG_ENOMEM, std::string("cudaMalloc ") + what);
+  if (*ptr) cudaFree(*ptr);
+  *ptr = p;
+  *cap = ncap;
+  return AWG_OK;
+}
+
+int upload_tones(awg_t* h) {
+  int st = ensure(&h->d_tones, &h->cap_tones, std::max<size_t>(1, h->tones.size()), h, "tones");
+  if (st) return st;
+  if (!h->tones.empty()) {
+    cudaError_t e = cudaMemcpy(h->d_tones, h->tones.data(), h->tones.size() * sizeof(ToneRec), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload tones");
+  }
+  return AWG_OK;
+}
+
+int upload_chirps(awg_t* h) {
+  size_t n = std::max<size_t>(1, h->chirps.size());
+  if (n > h->cap_chirps) {
+    int st = wait_idle(h);
+    if (st) return st;
+    size_t ncap = std::max(n, h->cap_chirps * 2);
+    ChirpRec* p = nullptr;
+    int32_t* q = nullptr;
+    if (cudaMalloc((void**)&p, ncap * sizeof(ChirpRec)) != cudaSuccess) return fail(AWG_ENOMEM, "cudaMalloc chirps");
+    if (cudaMalloc((void**)&q, ncap * sizeof(int32_t)) != cudaSuccess) {
+      cudaFree(p);
+      return fail(AWG_ENOMEM, "cudaMalloc chirp map");
+    }
+    if (h->d_chirps) cudaFree(h->d_chirps);
+    if (h->d_act) cudaFree(h->d_act);
+    h->d_chirps = p;
+    h->d_act = q;
+    h->cap_chirps = ncap;
+  }
+  if (!h->chirps.empty()) {
+    cudaError_t e = cudaMemcpy(h->d_chirps, h->chirps.data(), h->chirps.size() * sizeof(ChirpRec), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "upload chirps");
+  }
+  return AWG_OK;
+}
+
+double default_full_scale(const awg_t* h) {
+  double s = 0;
+  for (double a : h->amp) s += std::fabs(a);
+  return s;
+}
+
+int set_tones_common(awg_t* h, const double* f, const double* amp, const double* ph, int32_t n, int32_t log2_len) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (n < 0) return fail(AWG_EINVAL, "tone count must be >= 0");
+  if (n > 0 && (!f || !amp || !ph)) return fail(AWG_EINVAL, "null tone array");
+  std::vector<ToneRec> tones((size_t)n);
+  std::vector<double> a((size_t)n);
+  for (int32_t k = 0; k < n; ++k) {
+    uint64_t F, P;
+    int st;
+    if (log2_len > 0) {
+      int64_t j;
+      st = awg_grid_word(f[k], h->fs, log2_len, &F, &j);
+    } else {
+      st = freq_word_impl(f[k], h->fs, &F);
+    }
+    if (st) return st;
+    if (!is_fin(amp[k])) return fail(AWG_EINVAL, "amplitude must be finite");
+    st = phase_word_impl(ph[k], &P);
+    if (st) return st;
+    ToneRec& t = tones[(size_t)k];
+    std::memset(&t, 0, sizeof(t));
+    t.phi_ref = P;
+    t.F = F;
+    t.n_s = awgk::NO_CHIRP;
+    t.n_e = awgk::NO_CHIRP;
+    t.A = (float)amp[k];
+    t.slot = -1;
+    a[(size_t)k] = amp[k];
+  }
+  int st = wait_idle(h);
+  if (st) return st;
+  h->tones.swap(tones);
+  h->amp.swap(a);
+  h->K = n;
+  h->chirps.clear();
+  h->free_slots.clear();
+  h->fs_explicit = false;
+  h->full_scale = default_full_scale(h);
+  h->split = pow2_split(n);
+  st = upload_tones(h);
+  if (st) return st;
+  return upload_chirps(h);
+}
+
+int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (n < 0) return fail(AWG_EINVAL, "sample count must be >= 0");
+  if (n == 0) return AWG_OK;
+  if (!out_f && !out_q) return fail(AWG_EINVAL, "no output buffer");
+  if (h->cursor > INT64_MAX - n) return fail(AWG_EINVAL, "sample index overflow");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t c = h->cursor;
+  const int64_t tile0 = c / awgk::TILE;
+  const int64_t tile_last = (c + n - 1) / awgk::TILE;
+  const int64_t n_tiles64 = tile_last - tile0 + 1;
+  if (n_tiles64 > (int64_t)(INT32_MAX / awgk::MAX_SPLIT)) return fail(AWG_EINVAL, "render window too long");
+  const int32_t n_tiles = (int32_t)n_tiles64;
+  const int64_t span0 = tile0 * awgk::TILE, span1 = (tile_last + 1) * awgk::TILE - 1;
+
+  std::vector<int32_t> active;
+  for (size_t sl = 0; sl < h->chirps.size(); ++sl) {
+    const ChirpRec& cr = h->chirps[sl];
+    if (cr.tone < 0 || (cr.flags & awgk::TONE_EXACT)) continue;
+    const int64_t ne = cr.n_s + cr.L;
+    if (cr.n_s <= span1 && ne >= span0) active.push_back((int32_t)sl);
+  }
+  int st = ensure(&h->d_recs, &h->cap_recs, std::max<size_t>(1, active.size() * (size_t)n_tiles), h, "tile records");
+  if (st) return st;
+
+  cudaError_t e;
+  cudaEvent_t pe[3] = {nullptr, nullptr, nullptr};
+  if (h->profiling) {
+    while (h->prof_ev.size() < 3 * (h->prof_calls + 1)) {
+      cudaEvent_t ev;
+      if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "profiling event");
+      h->prof_ev.push_back(ev);
+    }
+    for (int i = 0; i < 3; ++i) pe[i] = h->prof_ev[3 * h->prof_calls + (size_t)i];
+    if ((e = cudaEventRecord(pe[0], s)) != cudaSuccess) return cuda_fail(e, "event");
+  }
+  int64_t launches = 0;
+  if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
+  for (size_t b = 0; b < active.size(); b += awgk::MAX_ACTIVE_PER_LAUNCH) {
+    awgk::PrepArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.chirps = h->d_chirps;
+    pa.recs = h->d_recs;
+    pa.act_of_slot = h->d_act;
+    pa.tile0 = tile0;
+    pa.n_tiles = n_tiles;
+    pa.n_active = (int32_t)std::min<size_t>(awgk::MAX_ACTIVE_PER_LAUNCH, active.size() - b);
+    pa.act_base = (int32_t)b;
+    std::memcpy(pa.W, h->W, sizeof(pa.W));
+    std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
+    for (int i = 0; i < pa.n_active; ++i) pa.slots[i] = active[b + (size_t)i];
+    if ((e = awgk::launch_prep(pa, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+    ++launches;
+  }
+  if (pe[1] && (e = cudaEventRecord(pe[1], s)) != cudaSuccess) return cuda_fail(e, "event");
+  awgk::RenderArgs ra;
+  std::memset(&ra, 0, sizeof(ra));
+  ra.tones = h->d_tones;
+  ra.chirps = h->d_chirps;
+  ra.recs = h->d_recs;
+  ra.act_of_slot = h->d_act;
+  ra.K = h->K;
+  ra.split = h->split;
+  ra.tile0 = tile0;
+  ra.n_tiles = n_tiles;
+  ra.win_start = c;
+  ra.win_end = c + n;
+  ra.out_q = out_q;
+  ra.out_f = out_f;
+  ra.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
+  ra.status = h->d_status;
+  std::memcpy(ra.inv_odd, h->inv_odd, sizeof(ra.inv_odd));
+  if ((e = awgk::launch_render(ra, s)) != cudaSuccess) return cuda_fail(e, "render launch");
+  ++launches;
+  if (pe[2]) {
+    if ((e = cudaEventRecord(pe[2], s)) != cudaSuccess) return cuda_fail(e, "event");
+    ++h->prof_calls;
+    h->prof_launches += launches;
+  }
+  if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
+  if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
+  h->timed = true;
+  h->have_done = true;
+  h->cursor = c + n;
+  return AWG_OK;
+}
+
+}  // namespace
+
+// ==========================================================================================
+// C ABI
+// ==========================================================================================
+extern "C" {
+
+int awg_version(void) { return 10000; }
+
+const char* awg_last_error(void) { return g_err.c_str(); }
+
+int awg_freq_word(double f_hz, double fs_hz, uint64_t* out_word) {
+  if (!out_word) return fail(AWG_EINVAL, "null output");
+  return freq_word_impl(f_hz, fs_hz, out_word);
+}
+
+int awg_phase_word(double theta_rad, uint64_t* out_word) {
+  if (!out_word) return fail(AWG_EINVAL, "null output");
+  return phase_word_impl(theta_rad, out_word);
+}
+
+int awg_grid_word(double f_hz, double fs_hz, int32_t log2_len, uint64_t* out_word, int64_t* out_j) {
+  if (!out_word) return fail(AWG_EINVAL, "null output");
+  if (!(is_fin(fs_hz) && fs_hz > 0)) return fail(AWG_EINVAL, "sample rate must be finite and > 0");
+  if (log2_len < 1 || log2_len > 40) return fail(AWG_EINVAL, "log2_len must be 1..40");
+  if (!is_fin(f_hz) || f_hz < 0 || f_hz >= fs_hz) return fail(AWG_EINVAL, "tone frequency must lie in [0, fs)");
+  double j = std::rint(std::ldexp(f_hz / fs_hz, log2_len));
+  int64_t ji = (int64_t)j;
+  *out_word = ((uint64_t)ji) << (64 - log2_len);
+  if (out_j) *out_j = ji;
+  return AWG_OK;
+}
+
+int awg_chirp_length(double duration_s, double fs_hz, int64_t* out_L) {
+  if (!out_L) return fail(AWG_EINVAL, "null output");
+  return chirp_length_impl(duration_s, fs_hz, out_L);
+}
+
+int awg_chirp_coeffs(uint64_t F_start, uint64_t F_end, int64_t L, int32_t profile, uint64_t* out21) {
+  if (!out21) return fail(AWG_EINVAL, "null output");
+  W192 d[7];
+  int st = chirp_coeffs_impl(F_start, F_end, L, profile, d);
+  if (st) return st;
+  for (int k = 0; k < 7; ++k)
+    for (int j = 0; j < 3; ++j) out21[3 * k + j] = d[k].w[j];
+  return AWG_OK;
+}
+
+awg_t* awg_create(double sample_rate_hz) {
+  if (!(is_fin(sample_rate_hz) && sample_rate_hz > 0)) {
+    fail(AWG_EINVAL, "sample rate must be finite and > 0");
+    return nullptr;
+  }
+  awg_t* h = new awg();
+  h->fs = sample_rate_hz;
+  fill_constants(h);
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = awgk::render_setup_attributes();
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_status, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cuda_fail(e, "awg_create");
+    awg_destroy(h);
+    return nullptr;
+  }
+  if (upload_tones(h) || upload_chirps(h)) {
+    awg_destroy(h);
+    return nullptr;
+  }
+  return h;
+}
+
+void awg_destroy(awg_t* h) {
+  if (!h) return;
+  if (h->have_done) cudaEventSynchronize(h->ev_done);
+  if (h->priv) cudaStreamSynchronize(h->priv);
+  cudaFree(h->d_tones);
+  cudaFree(h->d_chirps);
+  cudaFree(h->d_act);
+  cudaFree(h->d_recs);
+  cudaFree(h->d_status);
+  cudaFree(h->d_words);
+  cudaFree(h->d_trace);
+  for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ev_done) cudaEventDestroy(h->ev_done);
+  if (h->priv) cudaStreamDestroy(h->priv);
+  delete h;
+}
+
+int awg_set_tones(awg_t* h, const double* freq_hz, const double* amp, const double* phase_rad, int32_t n) {
+  return set_tones_common(h, freq_hz, amp, phase_rad, n, 0);
+}
+
+int awg_set_tones_grid(awg_t* h, const double* freq_hz, int32_t log2_len, const double* amp,
+                       const double* phase_rad, int32_t n) {
+  if (log2_len < 1 || log2_len > 40) return fail(AWG_EINVAL, "log2_len must be 1..40");
+  return set_tones_common(h, freq_hz, amp, phase_rad, n, log2_len);
+}
+
+int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, const double* f_end_hz,
+                   const double* duration_s, const int32_t* profile, const int64_t* start_sample, int32_t n) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (n < 0) return fail(AWG_EINVAL, "chirp count must be >= 0");
+  if (n == 0) return AWG_OK;
+  if (!tone || !f_start_hz || !f_end_hz || !duration_s || !profile || !start_sample)
+    return fail(AWG_EINVAL, "null chirp array");
+  struct Pending {
+    int32_t tone;
+    uint64_t F0, F1;
+    int64_t L, ns;
+    int32_t profile;
+  };
+  std::vector<Pending> pend((size_t)n);
+  std::vector<char> seen((size_t)h->K, 0);
+  for (int32_t i = 0; i < n; ++i) {
+    Pending& p = pend[(size_t)i];
+    p.tone = tone[i];
+    if (p.tone < 0 || p.tone >= h->K) return fail(AWG_EINVAL, "chirp tone index out of range");
+    if (seen[(size_t)p.tone]) return fail(AWG_EINVAL, "two chirps for one tone in one call");
+    seen[(size_t)p.tone] = 1;
+    int st = freq_word_impl(f_start_hz[i], h->fs, &p.F0);
+    if (st) return st;
+    st = freq_word_impl(f_end_hz[i], h->fs, &p.F1);
+    if (st) return st;
+    st = chirp_length_impl(duration_s[i], h->fs, &p.L);
+    if (st) return st;
+    p.profile = profile[i];
+    if (p.profile != AWG_PROFILE_LINEAR && p.profile != AWG_PROFILE_MINJERK) return fail(AWG_EINVAL, "unknown chirp profile");
+    p.ns = start_sample[i];
+    if (p.ns < h->cursor) return fail(AWG_EINVAL, "chirp starts before the render cursor");
+    if (p.ns > INT64_MAX / 2) return fail(AWG_EINVAL, "chirp start too large");
+    const ToneRec& t = h->tones[(size_t)p.tone];
+    if (t.slot >= 0 && t.n_e >= h->cursor) return fail(AWG_EINVAL, "tone already has a chirp that has not finished rendering");
+  }
+  int st = wait_idle(h);
+  if (st) return st;
+  for (const Pending& p : pend) {
+    ToneRec& t = h->tones[(size_t)p.tone];
+    if (t.slot >= 0) {   // fold the finished chirp into the static state
+      t.phi_ref = t.phi_post_ref;
+      t.F = t.F_end;
+      h->chirps[(size_t)t.slot].tone = -1;
+      h->free_slots.push_back(t.slot);
+      t.slot = -1;
+    }
+    W192 d[7];
+    st = chirp_coeffs_impl(p.F0, p.F1, p.L, p.profile, d);
+    if (st) return st;   // validated above; cannot fail
+    int32_t slot;
+    if (!h->free_slots.empty()) {
+      slot = h->free_slots.back();
+      h->free_slots.pop_back();
+    } else {
+      slot = (int32_t)h->chirps.size();
+      h->chirps.push_back(ChirpRec{});
+    }
+    ChirpRec& c = h->chirps[(size_t)slot];
+    std::memset(&c, 0, sizeof(c));
+    for (int k = 0; k < 7; ++k)
+      for (int j = 0; j < 3; ++j) c.d[3 * k + j] = d[k].w[j];
+    c.phi_start = t.phi_ref + (uint64_t)p.ns * t.F;
+    c.n_s = p.ns;
+    c.L = p.L;
+    c.tone = p.tone;
+    c.flags = needs_exact(p.F0, p.F1, p.L, p.profile) ? awgk::TONE_EXACT : 0;
+    const uint64_t phi_end = c.phi_start + chirp_offset_word(d, p.L);
+    t.slot = slot;
+    t.n_s = p.ns;
+    t.n_e = p.ns + p.L;
+    t.F_end = p.F1;
+    t.phi_post_ref = phi_end - (uint64_t)t.n_e * p.F1;
+    t.flags = c.flags;
+  }
+  st = upload_chirps(h);
+  if (st) return st;
+  return upload_tones(h);
+}
+
+int awg_set_full_scale(awg_t* h, double v) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (!is_fin(v)) return fail(AWG_EINVAL, "full scale must be finite");
+  if (v <= 0) {
+    h->fs_explicit = false;
+    h->full_scale = default_full_scale(h);
+  } else {
+    h->fs_explicit = true;
+    h->full_scale = v;
+  }
+  return AWG_OK;
+}
+
+double awg_full_scale(const awg_t* h) { return h ? h->full_scale : 0.0; }
+
+int awg_seek(awg_t* h, int64_t sample) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (sample < 0) return fail(AWG_EINVAL, "sample must be >= 0");
+  h->cursor = sample;
+  return AWG_OK;
+}
+
+int64_t awg_cursor(const awg_t* h) { return h ? h->cursor : -1; }
+
+int awg_render(awg_t* h, int64_t n, int16_t* out, void* stream) {
+  if (n > 0 && !out) return fail(AWG_EINVAL, "null output");
+  return render_impl(h, n, nullptr, out, stream);
+}
+
+int awg_render_f32(awg_t* h, int64_t n, float* out_f32, int16_t* out_q, void* stream) {
+  if (n > 0 && !out_f32) return fail(AWG_EINVAL, "null output");
+  return render_impl(h, n, out_f32, out_q, stream);
+}
+
+int awg_phase_words(awg_t* h, int64_t sample, uint64_t* out_host, int32_t n) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (n < 0 || n > h->K) return fail(AWG_EINVAL, "tone count out of range");
+  if (sample < 0) return fail(AWG_EINVAL, "sample must be >= 0");
+  if (n == 0) return AWG_OK;
+  if (!out_host) return fail(AWG_EINVAL, "null output");
+  int st = ensure(&h->d_words, &h->cap_words, (size_t)n, h, "phase words");
+  if (st) return st;
+  awgk::PhaseArgs pa;
+  pa.tones = h->d_tones;
+  pa.chirps = h->d_chirps;
+  pa.n = n;
+  pa.sample = sample;
+  pa.out = h->d_words;
+  std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
+  cudaError_t e = awgk::launch_phase_words(pa, h->priv);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, h->d_words, (size_t)n * 8, cudaMemcpyDeviceToHost, h->priv);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->priv);
+  if (e != cudaSuccess) return cuda_fail(e, "phase words");
+  return AWG_OK;
+}
+
+int awg_render_phases(awg_t* h, int32_t tone, int64_t n0, int32_t count, uint32_t* out_host) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (tone < 0 || tone >= h->K) return fail(AWG_EINVAL, "tone index out of range");
+  if (n0 < 0 || count < 0 || count > (1 << 20)) return fail(AWG_EINVAL, "bad sample range");
+  if (count == 0) return AWG_OK;
+  if (!out_host) return fail(AWG_EINVAL, "null output");
+  int st = wait_idle(h);
+  if (st) return st;
+  const int64_t tile0 = n0 / awgk::TILE, tile_last = (n0 + count - 1) / awgk::TILE;
+  const int32_t n_tiles = (int32_t)(tile_last - tile0 + 1);
+  const ToneRec& t = h->tones[(size_t)tone];
+  st = ensure(&h->d_recs, &h->cap_recs, (size_t)n_tiles, h, "tile records");
+  if (st) return st;
+  st = ensure(&h->d_trace, &h->cap_trace, (size_t)count, h, "trace");
+  if (st) return st;
+  cudaError_t e = cudaSuccess;
+  if (t.slot >= 0 && !(t.flags & awgk::TONE_EXACT)) {
+    awgk::PrepArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.chirps = h->d_chirps;
+    pa.recs = h->d_recs;
+    pa.act_of_slot = h->d_act;
+    pa.tile0 = tile0;
+    pa.n_tiles = n_tiles;
+    pa.n_active = 1;
+    pa.act_base = 0;
+    std::memcpy(pa.W, h->W, sizeof(pa.W));
+    std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
+    pa.slots[0] = t.slot;
+    e = awgk::launch_prep(pa, h->priv);
+  }
+  awgk::TraceArgs ta;
+  ta.tones = h->d_tones;
+  ta.chirps = h->d_chirps;
+  ta.recs = h->d_recs;
+  ta.act_of_slot = h->d_act;
+  ta.tone = tone;
+  ta.n0 = n0;
+  ta.count = count;
+  ta.tile0 = tile0;
+  ta.n_tiles = n_tiles;
+  ta.out = h->d_trace;
+  std::memcpy(ta.inv_odd, h->inv_odd, sizeof(ta.inv_odd));
+  if (e == cudaSuccess) e = awgk::launch_trace(ta, h->priv);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, h->d_trace, (size_t)count * 4, cudaMemcpyDeviceToHost, h->priv);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->priv);
+  if (e != cudaSuccess) return cuda_fail(e, "render phases");
+  return AWG_OK;
+}
+
+int32_t awg_tone_split(const awg_t* h) { return h ? h->split : 0; }
+
+float awg_last_render_ms(awg_t* h) {
+  if (!h || !h->timed) return -1.f;
+  float ms = -1.f;
+  if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) != cudaSuccess) return -1.f;
+  return ms;
+}
+
+int awg_profile_begin(awg_t* h) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  h->profiling = true;
+  h->prof_calls = 0;
+  h->prof_launches = 0;
+  return AWG_OK;
+}
+
+int awg_profile_end(awg_t* h, float* prep_ms, float* render_ms, int32_t cap, int64_t* launches) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (!h->profiling) return fail(AWG_ESTATE, "profiling was not started");
+  h->profiling = false;
+  if (launches) *launches = h->prof_launches;
+  const size_t n = h->prof_calls;
+  if (n == 0) return 0;
+  cudaError_t e = cudaEventSynchronize(h->prof_ev[3 * (n - 1) + 2]);
+  if (e != cudaSuccess) return cuda_fail(e, "profiling sync");
+  for (size_t i = 0; i < n && (int64_t)i < (int64_t)cap; ++i) {
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, h->prof_ev[3 * i], h->prof_ev[3 * i + 1]);
+    cudaEventElapsedTime(&b, h->prof_ev[3 * i + 1], h->prof_ev[3 * i + 2]);
+    if (prep_ms) prep_ms[i] = a;
+    if (render_ms) render_ms[i] = b;
+  }
+  return (int)std::min<size_t>(n, (size_t)INT32_MAX);
+}
+
+int awg_device_status(awg_t* h) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  int32_t v = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&v, h->d_status, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int32_t));
+  if (e != cudaSuccess) return cuda_fail(e, "device status");
+  return v;
+}
+
+}  // extern "C"

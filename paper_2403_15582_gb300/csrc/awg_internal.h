@@ -1,0 +1,121 @@
+// Internal layout shared by the host library (awg_host.cpp) and the kernels (awg_render.cu).
+// Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace awgk {
+
+// Work decomposition of the render kernel.  A thread owns RUN consecutive samples (one run)
+// and keeps their partial sums in registers; a CTA of NT threads owns one tile of TILE
+// consecutive samples; the tones of a tile are split over the CTAs of a thread-block cluster.
+// Runs and tiles are aligned to absolute sample indices, so a sample's value does not depend on
+// where a render window starts (chunk invariance).
+constexpr int RUN = 32;
+constexpr int NT = 128;
+constexpr int TILE = RUN * NT;     // 4096 samples
+constexpr int STAGE = 32;          // tones staged in shared memory at a time
+constexpr int MAX_SPLIT = 16;      // cluster size limit (non-portable 16 on sm_100-class parts)
+constexpr int MAX_ACTIVE_PER_LAUNCH = 1024;
+
+constexpr int64_t NO_CHIRP = INT64_MAX;
+
+// Per-tone record read by the render kernel.  64 bytes, 16-byte aligned (bulk-copied).
+struct alignas(16) ToneRec {
+  uint64_t phi_ref;       // static segment before the chirp (or the only one): Phi(n) = phi_ref + n F
+  uint64_t F;
+  uint64_t phi_post_ref;  // static segment after the chirp:  Phi(n) = phi_post_ref + n F_end
+  uint64_t F_end;
+  int64_t n_s;            // chirp covers samples [n_s, n_e]; NO_CHIRP if none
+  int64_t n_e;
+  float A;
+  int32_t slot;           // chirp slot, -1 if none
+  int32_t flags;          // TONE_EXACT: evaluate this chirp per sample with the exact closed form
+  int32_t pad;
+};
+static_assert(sizeof(ToneRec) == 64, "ToneRec layout");
+constexpr int32_t TONE_EXACT = 1;
+
+// Per-chirp record (one per live slot): the 192-bit forward-difference words.
+struct alignas(16) ChirpRec {
+  uint64_t d[21];         // d_0..d_6, 3 little-endian limbs each
+  uint64_t phi_start;     // Phi(n_s)
+  int64_t n_s;
+  int64_t L;
+  int32_t tone;
+  int32_t flags;
+  uint64_t pad;
+};
+static_assert(sizeof(ChirpRec) == 208, "ChirpRec layout");
+
+// Per (active chirp, tile) record: the chirp phase polynomial re-expressed at the tile start as
+// forward differences with stride RUN in the run index j (0 <= j < NT), for the phase and its
+// first three unit-stride differences.  Words (2^-64 turn), rounded.  B[0] is the phase word.
+struct alignas(16) TileRec {
+  uint64_t B[7];
+  uint64_t E[6];
+  uint64_t G[5];
+  uint64_t H[4];
+};
+static_assert(sizeof(TileRec) == 176, "TileRec layout");
+
+struct PrepArgs {
+  const ChirpRec* chirps;
+  TileRec* recs;          // [n_active][n_tiles]
+  int32_t* act_of_slot;   // slot -> active index (written here)
+  int64_t tile0;          // absolute index of the first tile
+  int32_t n_tiles;
+  int32_t n_active;
+  int32_t act_base;       // active index of slots[0]
+  int64_t W[7][7];        // W[q][i] = Delta^q_j C(j RUN, i) at j = 0
+  uint64_t inv_odd[3][3]; // inverses mod 2^192 of 3, 15, 45
+  int32_t slots[MAX_ACTIVE_PER_LAUNCH];
+};
+
+struct RenderArgs {
+  const ToneRec* tones;
+  const ChirpRec* chirps;
+  const TileRec* recs;
+  const int32_t* act_of_slot;
+  int32_t K;
+  int32_t split;          // CTAs per tile (cluster size)
+  int64_t tile0;
+  int32_t n_tiles;
+  int64_t win_start, win_end;   // [win_start, win_end) absolute samples written
+  int16_t* out_q;
+  float* out_f;
+  float scale;            // 32767 / FS
+  int32_t* status;
+  uint64_t inv_odd[3][3];
+};
+
+struct PhaseArgs {
+  const ToneRec* tones;
+  const ChirpRec* chirps;
+  int32_t n;
+  int64_t sample;
+  uint64_t* out;
+  uint64_t inv_odd[3][3];
+};
+
+struct TraceArgs {      // per-sample render phases of one tone (test hook)
+  const ToneRec* tones;
+  const ChirpRec* chirps;
+  const TileRec* recs;
+  const int32_t* act_of_slot;
+  int32_t tone;
+  int64_t n0;
+  int32_t count;
+  int64_t tile0;
+  int32_t n_tiles;
+  uint32_t* out;
+  uint64_t inv_odd[3][3];
+};
+
+cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
+cudaError_t launch_phase_words(const PhaseArgs& a, cudaStream_t s);
+cudaError_t launch_trace(const TraceArgs& a, cudaStream_t s);
+cudaError_t render_setup_attributes();
+
+}  // namespace awgk

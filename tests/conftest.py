@@ -17,3 +17,13 @@ def oracle():
     import oracle as o
     o.build()
     return o
+
+
+@pytest.fixture(scope="session")
+def awglib():
+    """The CUDA library, built in-tree if needed (nvcc cross-compiles without a GPU)."""
+    from paper_2403_15582_gb300 import build
+    build.build()
+    import paper_2403_15582_gb300 as awg
+    awg.lib()
+    return awg

@@ -1,0 +1,98 @@
+"""Host-side logic of the library, checked without a GPU: the exported symbols match the header,
+and the set-up words the library computes (its own exact-integer code) equal the oracle's
+(exact rationals), bit for bit."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_symbols():
+    src = open(os.path.join(ROOT, "include", "awg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(awg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol(awglib):
+    import ctypes
+    from paper_2403_15582_gb300 import binding
+    declared = _header_symbols()
+    assert len(declared) >= 20
+    lib = ctypes.CDLL(binding.LIB_PATH)
+    for name in declared:
+        assert hasattr(lib, name), name
+    bound = sorted(n for n, _, _ in binding.SIGNATURES)
+    assert bound == declared
+
+
+def test_version_and_error_string(awglib):
+    assert awglib.lib().awg_version() >= 10000
+    with pytest.raises(awglib.AwgError) as e:
+        awglib.freq_word(300e6, 280e6)
+    assert e.value.code == awglib.AWG_EINVAL
+    assert "fs" in awglib.lib().awg_last_error().decode()
+
+
+def test_freq_and_phase_words_match_oracle(awglib, oracle):
+    rng = np.random.default_rng(11)
+    for fs in (280e6, 50e6, 2.0**28, 1.0):
+        for f in np.concatenate([rng.uniform(0, fs, 300), [0.0, fs / 4, fs / 2, np.nextafter(fs, 0)]]):
+            assert awglib.freq_word(f, fs) == oracle.freq_word(f, fs)
+    for th in np.concatenate([rng.uniform(-100, 100, 300), [0.0, math.pi, -math.pi, 2 * math.pi, -1e-300]]):
+        assert awglib.phase_word(th) == oracle.phase_word(th)
+
+
+def test_grid_words_match_oracle(awglib, oracle):
+    rng = np.random.default_rng(12)
+    for lg in (12, 18, 24):
+        for f in rng.uniform(0, 280e6, 200):
+            w, j = awglib.grid_word(f, 280e6, lg)
+            assert j == oracle.grid_index(f, 280e6, lg)
+            assert w == oracle.grid_word(j, lg)
+
+
+def test_chirp_length_rule(awglib, oracle):
+    for dur in (35e-3, 1e-3, 0.1e-3, 2e-3, 1 / 280e6, 0.5 / 280e6 * 3):
+        assert awglib.chirp_length(dur, 280e6) == oracle.chirp_length(dur, 280e6)
+    for bad in (0.0, -1.0, float("nan"), 1e3, 0.4 / 280e6):
+        with pytest.raises(awglib.AwgError):
+            awglib.chirp_length(bad, 280e6)
+
+
+@pytest.mark.parametrize("profile", [0, 1])
+def test_chirp_coefficients_match_oracle_bitwise(awglib, oracle, profile):
+    rng = np.random.default_rng(13 + profile)
+    M = 1 << 64
+    cases = [(0, M - 1, 1), (M - 1, 0, 2), (123, 456, 3), (1 << 63, (1 << 63) + 1, 7), (0, M - 1, (1 << 28) - 1),
+             (M - 1, 0, (1 << 28) - 1), (5, 5, 1000)]
+    for _ in range(40):
+        cases.append((int(rng.integers(0, M, dtype=np.uint64)), int(rng.integers(0, M, dtype=np.uint64)),
+                      int(rng.integers(1, 1 << 28))))
+    for F0, F1, L in cases:
+        assert awglib.chirp_coeffs(F0, F1, L, profile) == oracle.chirp_coefficients(F0, F1, L, profile), (F0, F1, L)
+
+
+def test_chirp_coefficient_errors(awglib):
+    with pytest.raises(awglib.AwgError):
+        awglib.chirp_coeffs(1, 2, 0, 0)
+    with pytest.raises(awglib.AwgError):
+        awglib.chirp_coeffs(1, 2, 1 << 28, 1)
+    with pytest.raises(awglib.AwgError):
+        awglib.chirp_coeffs(1, 2, 100, 2)
+
+
+def test_bad_arguments_rejected_without_gpu(awglib):
+    L = awglib.lib()
+    assert L.awg_create(float("nan")) is None
+    assert L.awg_create(-1.0) is None
+    for f in (-1.0, float("inf"), float("nan"), 280e6):
+        with pytest.raises(awglib.AwgError):
+            awglib.freq_word(f, 280e6)
+    with pytest.raises(awglib.AwgError):
+        awglib.phase_word(float("nan"))
+    with pytest.raises(awglib.AwgError):
+        awglib.grid_word(1e6, 280e6, 0)

@@ -1,0 +1,318 @@
+"""GPU parity: the CUDA render path against the CPU oracle, called through the C ABI.
+
+Bars: phase words bit-exact; int16 codes within 1 LSB of the oracle's FP64 sum quantised in FP64;
+the FP32 sum within a bound derived from the arithmetic (per-tone sine/argument error plus FP32
+summation), written out in `fp32_bound`."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NTHREADS = os.cpu_count() or 1
+TWO64 = 1 << 64
+
+
+@pytest.fixture(scope="module")
+def awg(awglib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return awglib
+
+
+def synth_from(awg, wk):
+    s = awg.Synth(wk.fs)
+    s.set_tones(wk.freq_hz, wk.amp, wk.phase_rad, grid_log2=wk.grid_log2)
+    s.set_chirp_list(wk.chirps)
+    return s
+
+
+def oracle_from(oracle, wk):
+    return oracle.make_waveform(wk.fs, wk.freq_hz, wk.amp, wk.phase_rad, wk.chirps, grid_log2=wk.grid_log2)
+
+
+def render(s, n, f32=True):
+    q = torch.empty(max(n, 1), dtype=torch.int16, device="cuda")
+    if f32:
+        x = torch.empty(max(n, 1), dtype=torch.float32, device="cuda")
+        s.render_f32(n, x, q)
+        torch.cuda.synchronize()
+        return q[:n].cpu().numpy(), x[:n].cpu().numpy()
+    s.render(n, q)
+    torch.cuda.synchronize()
+    return q[:n].cpu().numpy(), None
+
+
+def fp32_bound(amps, split):
+    """|x_gpu - x_exact| bound: per tone <= 5e-6 |A| (SFU sine 2^-21.4, 23-bit argument, FP32
+    argument scaling, in-run phase cascade <= 2500 * 2^-32 turn), plus FP32 summation of
+    K/split + split terms (each rounding <= 2^-24 of the running sum, bounded by sum |A|)."""
+    K = len(amps)
+    S = sum(abs(a) for a in amps)
+    return S * (5e-6 + (K / max(split, 1) + split + 2) * 2.0**-24)
+
+
+def check(q, x, w, oracle, x_ref, split):
+    FS = w.full_scale()
+    q_ref = oracle.quantize(x_ref, FS)
+    dq = np.abs(q.astype(np.int32) - q_ref.astype(np.int32))
+    assert dq.max(initial=0) <= 1, f"max LSB error {dq.max()}"
+    if x is not None:
+        err = np.max(np.abs(x.astype(np.float64) - x_ref), initial=0.0)
+        assert err <= fp32_bound(w.A, split), (err, fp32_bound(w.A, split))
+    return float(np.mean(dq == 0)) if dq.size else 1.0
+
+
+def _sdiff32(a, b):
+    d = (np.asarray(a, dtype=np.int64) - np.asarray(b, dtype=np.int64)) % (1 << 32)
+    return np.where(d >= 1 << 31, d - (1 << 32), d)
+
+
+# ---------------------------------------------------------------------------------------------
+def test_static_100_full_record(awg, oracle):
+    """100 static tones, 2^20 samples: the whole record, FP32 and int16."""
+    from paper_2403_15582_gb300 import workloads as wl
+    wk = wl.static_100(seed=0)
+    s = synth_from(awg, wk)
+    w = oracle_from(oracle, wk)
+    q, x = render(s, wk.n_samples)
+    x_ref = oracle.render(w, 0, wk.n_samples, nthreads=NTHREADS)
+    frac = check(q, x, w, oracle, x_ref, s.tone_split)
+    assert frac > 0.9
+    assert s.device_status() == 0
+
+
+def test_phase_words_bit_exact(awg, oracle):
+    from paper_2403_15582_gb300 import workloads as wl
+    for seed in range(4):
+        wk = wl.tiny(seed=seed, K=9, n_samples=20000)
+        s = synth_from(awg, wk)
+        w = oracle_from(oracle, wk)
+        samples = {0, 1, 4095, 4096, 19999, 1 << 30, (1 << 40) + 3}
+        for c in wk.chirps:
+            L = oracle.chirp_length(c["duration"], wk.fs)
+            ns = c["start_sample"]
+            samples |= {max(ns - 1, 0), ns, ns + 1, ns + L // 2, ns + L - 1, ns + L, ns + L + 1}
+        for n in sorted(samples):
+            got = s.phase_words(n, w.K)
+            for k in range(w.K):
+                assert int(got[k]) == int(oracle.phase_words_at(w, k, [n])[0]), (seed, n, k)
+
+
+def test_phase_words_long_chirps(awg, oracle):
+    from paper_2403_15582_gb300 import workloads as wl
+    wk = wl.chirp_1000(seed=1, K=64)
+    s = synth_from(awg, wk)
+    w = oracle_from(oracle, wk)
+    rng = np.random.default_rng(0)
+    L = wk.n_samples
+    for n in [0, 1, L - 1, L, L + 1, L + 12345] + list(rng.integers(0, L, 12)):
+        got = s.phase_words(int(n), w.K)
+        ref = [int(oracle.phase_words_at(w, k, [int(n)])[0]) for k in range(w.K)]
+        assert [int(g) for g in got] == ref, n
+
+
+@pytest.mark.parametrize("dur_ms", [0.1, 0.5, 2.0, 35.0])
+def test_render_phase_cascade_within_bound(awg, oracle, dur_ms):
+    """The 32-bit phases the kernel feeds to the sine stay within the stated bound of the exact
+    words: 2500 units of 2^-32 turn for minimum-jerk runs (g, h rounding over 31 steps), 300 for
+    linear, 20 for static segments."""
+    fs = 280e6
+    L = int(round(dur_ms * 1e-3 * fs))
+    f = [90e6, 100e6, 120e6, 60e6]
+    s = awg.Synth(fs)
+    s.set_tones(f, [1, 1, 1, 1], [0.1, 0.2, 0.3, 0.4])
+    ns = 5000
+    chirps = [dict(tone=0, f_start=90e6, f_end=179e6, duration=L / fs, profile=1, start_sample=ns),
+              dict(tone=1, f_start=100e6, f_end=1e6, duration=L / fs, profile=0, start_sample=ns + 17),
+              dict(tone=2, f_start=125e6, f_end=80e6, duration=L / fs, profile=1, start_sample=ns + 4096)]
+    s.set_chirp_list(chirps)
+    w = oracle.make_waveform(fs, f, [1, 1, 1, 1], [0.1, 0.2, 0.3, 0.4], chirps)
+    for n0 in (0, ns + L // 2 - 30000, ns + L - 20000):
+        n0 = max(n0, 0)
+        cnt = 60000
+        idx = np.arange(n0, n0 + cnt, dtype=np.int64)
+        for k, bound in ((0, 2500), (1, 300), (2, 2500), (3, 20)):
+            got = s.render_phases(k, n0, cnt)
+            words = oracle.phase_words_at(w, k, idx)
+            ref = ((words.astype(object) + (1 << 40)) >> 32) % (1 << 32)
+            d = np.abs(_sdiff32(got.astype(np.int64), np.array(ref, dtype=np.int64)))
+            assert d.max() <= bound, (dur_ms, n0, k, int(d.max()))
+
+
+def test_tiny_waveforms_all_samples(awg, oracle):
+    from paper_2403_15582_gb300 import workloads as wl
+    for seed in range(6):
+        wk = wl.tiny(seed=seed, K=5, n_samples=9000 + 777 * seed)
+        s = synth_from(awg, wk)
+        w = oracle_from(oracle, wk)
+        q, x = render(s, wk.n_samples)
+        x_ref = oracle.render(w, 0, wk.n_samples)
+        check(q, x, w, oracle, x_ref, s.tone_split)
+
+
+def test_chirp_1000_windows(awg, oracle):
+    """1000 chirping tones (35 ms at 280 MS/s): windows at the start, the middle and across the
+    chirp end, with ragged lengths; each compared sample by sample with the oracle."""
+    from paper_2403_15582_gb300 import workloads as wl
+    wk = wl.chirp_1000(seed=0)
+    s = synth_from(awg, wk)
+    w = oracle_from(oracle, wk)
+    L = wk.n_samples
+    for n0, cnt in ((0, 3 * 4096 + 123), (L // 2 - 4000, 9001), (L - 6000, 12345)):
+        s.seek(n0)
+        q, x = render(s, cnt)
+        x_ref = oracle.render(w, n0, cnt, nthreads=NTHREADS)
+        check(q, x, w, oracle, x_ref, s.tone_split)
+
+
+def test_chirp_1000_full_record_sampled(awg, oracle):
+    """The full 9.8M-sample record rendered in 2^18-sample chunks, as the benchmark does, checked
+    at sampled indices with the oracle's closed form."""
+    from paper_2403_15582_gb300 import workloads as wl
+    wk = wl.chirp_1000(seed=0)
+    s = synth_from(awg, wk)
+    w = oracle_from(oracle, wk)
+    N = wk.n_samples
+    q = torch.empty(N, dtype=torch.int16, device="cuda")
+    for c0 in range(0, N, wk.chunk):
+        s.render(min(wk.chunk, N - c0), q[c0:])
+    torch.cuda.synchronize()
+    qh = q.cpu().numpy()
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([rng.integers(0, N, 700), [0, 1, N - 1, wk.chunk - 1, wk.chunk]]))
+    x_ref = oracle.render_at(w, idx, nthreads=NTHREADS)
+    q_ref = oracle.quantize(x_ref, w.full_scale())
+    assert np.max(np.abs(qh[idx].astype(np.int32) - q_ref)) <= 1
+    assert s.device_status() == 0
+
+
+def test_chunk_invariance_bit_exact(awg, oracle):
+    from paper_2403_15582_gb300 import workloads as wl
+    wk = wl.tiny(seed=7, K=40, n_samples=30000)
+    s = synth_from(awg, wk)
+    q1, x1 = render(s, 30000)
+    s.seek(0)
+    parts = [1, 4095, 4097, 7, 11800, 30000 - 1 - 4095 - 4097 - 7 - 11800]
+    qs, xs = [], []
+    for p in parts:
+        q, x = render(s, p)
+        qs.append(q)
+        xs.append(x)
+    assert np.array_equal(np.concatenate(qs), q1)
+    assert np.array_equal(np.concatenate(xs), x1)
+    assert s.cursor == 30000
+
+
+@pytest.mark.parametrize("K", [1, 63, 64, 65, 129, 1000, 2000])
+def test_tone_split_sizes(awg, oracle, K):
+    rng = np.random.default_rng(K)
+    f = rng.uniform(0, 280e6, K)
+    a = rng.uniform(-1, 1, K)
+    th = rng.uniform(0, 6.3, K)
+    s = awg.Synth(280e6)
+    s.set_tones(f, a, th)
+    w = oracle.make_waveform(280e6, f, a, th)
+    s.seek(12345)
+    q, x = render(s, 5000)
+    check(q, x, w, oracle, oracle.render(w, 12345, 5000, nthreads=NTHREADS), s.tone_split)
+
+
+def test_edge_cases(awg, oracle):
+    fs = 280e6
+    s = awg.Synth(fs)
+    # no tones: silence
+    s.set_tones([], [], [])
+    q, x = render(s, 5000)
+    assert not q.any() and not x.any()
+    # n = 0 is a no-op
+    s.render(0, None)
+    assert s.cursor == 5000
+    # DC, Nyquist, an aliased tone above fs/2, negative amplitude, far-out sample index
+    f = [0.0, fs / 2, 200e6, 13e6]
+    a = [0.25, 0.5, -0.75, 1.0]
+    th = [0.3, 1.1, 2.0, -0.5]
+    s.set_tones(f, a, th)
+    w = oracle.make_waveform(fs, f, a, th)
+    for n0 in (0, 7, (1 << 40) + 5):
+        s.seek(n0)
+        q, x = render(s, 4100)
+        check(q, x, w, oracle, oracle.render(w, n0, 4100), s.tone_split)
+    # explicit full scale that clips
+    s.set_full_scale(0.5)
+    s.seek(0)
+    q, _ = render(s, 2000, f32=False)
+    assert q.max() <= 32767 and q.min() >= -32767
+    ref = oracle.quantize(oracle.render(w, 0, 2000), 0.5)
+    assert np.max(np.abs(q.astype(np.int32) - ref)) <= 1
+
+
+def test_exact_path_for_very_fast_chirps(awg, oracle):
+    """Chirps so short that the in-run cubic cascade would not be accurate use the exact
+    per-sample closed form; output still within 1 LSB."""
+    fs = 280e6
+    f = [50e6, 70e6, 90e6]
+    s = awg.Synth(fs)
+    s.set_tones(f, [1, 1, 1], [0, 1, 2])
+    chirps = [dict(tone=0, f_start=50e6, f_end=130e6, duration=300 / fs, profile=1, start_sample=100),
+              dict(tone=1, f_start=70e6, f_end=10e6, duration=2 / fs, profile=1, start_sample=4090),
+              dict(tone=2, f_start=90e6, f_end=95e6, duration=1 / fs, profile=0, start_sample=33)]
+    s.set_chirp_list(chirps)
+    w = oracle.make_waveform(fs, f, [1, 1, 1], [0, 1, 2], chirps)
+    q, x = render(s, 9000)
+    check(q, x, w, oracle, oracle.render(w, 0, 9000), s.tone_split)
+
+
+def test_chirp_sequence_on_one_tone(awg, oracle):
+    """A second chirp on a tone, set after the first has been rendered, continues from the first
+    chirp's end state."""
+    fs = 280e6
+    s = awg.Synth(fs)
+    s.set_tones([80e6, 100e6], [0.5, 0.5], [0.0, 1.0])
+    c1 = dict(tone=0, f_start=80e6, f_end=120e6, duration=5000 / fs, profile=1, start_sample=1000)
+    s.set_chirp_list([c1])
+    q1, x1 = render(s, 10000)
+    c2 = dict(tone=0, f_start=120e6, f_end=60e6, duration=3000 / fs, profile=0, start_sample=12000)
+    s.set_chirp_list([c2])
+    q2, x2 = render(s, 10000)
+    # oracle: second chirp applied to the folded state of the first
+    w = oracle.make_waveform(fs, [80e6, 100e6], [0.5, 0.5], [0.0, 1.0], [c1])
+    x_ref1 = oracle.render(w, 0, 10000)
+    Fe = w.F_end[0]
+    end = oracle.chirp_end_word(w, 0)
+    n_e = c1["start_sample"] + w.L[0]
+    w.F[0] = Fe
+    w.phi_ref[0] = (end - n_e * Fe) % TWO64
+    L2 = oracle.chirp_length(c2["duration"], fs)
+    w.has_chirp[0], w.n_s[0], w.L[0] = 1, c2["start_sample"], L2
+    w.d[0] = oracle.chirp_coefficients(oracle.freq_word(120e6, fs), oracle.freq_word(60e6, fs), L2, 0)
+    w.F_end[0] = oracle.freq_word(60e6, fs)
+    x_ref2 = oracle.render(w, 10000, 10000)
+    check(q1, x1, w, oracle, x_ref1, s.tone_split)
+    check(q2, x2, w, oracle, x_ref2, s.tone_split)
+
+
+def test_set_chirps_validation(awg):
+    fs = 280e6
+    s = awg.Synth(fs)
+    s.set_tones([80e6, 90e6], [1, 1], [0, 0])
+    s.set_chirps([0], [80e6], [90e6], [1e-3], [1], [100])
+    bad = [
+        dict(tone=[5], f0=[80e6], f1=[90e6], d=[1e-3], p=[0], st=[0]),          # tone out of range
+        dict(tone=[1, 1], f0=[80e6] * 2, f1=[90e6] * 2, d=[1e-3] * 2, p=[0, 0], st=[0, 10**6]),   # twice in one call
+        dict(tone=[0], f0=[80e6], f1=[90e6], d=[1e-3], p=[0], st=[10**7]),      # pending chirp on tone 0
+        dict(tone=[1], f0=[80e6], f1=[290e6], d=[1e-3], p=[0], st=[0]),         # f_end >= fs
+        dict(tone=[1], f0=[80e6], f1=[90e6], d=[0.0], p=[0], st=[0]),           # zero length
+        dict(tone=[1], f0=[80e6], f1=[90e6], d=[1e-3], p=[3], st=[0]),          # bad profile
+    ]
+    for b in bad:
+        with pytest.raises(awg.AwgError) as e:
+            s.set_chirps(b["tone"], b["f0"], b["f1"], b["d"], b["p"], b["st"])
+        assert e.value.code == awg.AWG_EINVAL
+    q = torch.empty(1000, dtype=torch.int16, device="cuda")
+    s.render(1000, q)
+    with pytest.raises(awg.AwgError):
+        s.set_chirps([1], [80e6], [90e6], [1e-3], [0], [10])     # starts before the cursor
