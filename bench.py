@@ -247,9 +247,9 @@ def main():
     for i in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        synth.seek(0)
         synth.set_tones(wk.freq_hz, wk.amp, wk.phase_rad)
         synth.set_chirps(tone, f0, f1, dur, prof, start)
-        synth.seek(0)
         for c0 in range(0, N, chunk):
             synth.render(min(chunk, N - c0), out_host[c0:], stream)
         stream.synchronize()
