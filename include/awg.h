@@ -171,6 +171,27 @@ float awg_last_render_ms(awg_t* h);
 int awg_profile_begin(awg_t* h);
 int awg_profile_end(awg_t* h, float* prep_ms, float* render_ms, int32_t cap, int64_t* launches);
 
+/* Limits of awg_render_noalloc: (chirps active in the window) x (4096-sample tiles the window
+ * touches) tile records, and chirp slots (tones that hold a chirp record). */
+#define AWG_NOALLOC_MAX_RECORDS 71493
+#define AWG_NOALLOC_MAX_SLOTS 16384
+
+/* As awg_render, but it allocates nothing: no cudaMalloc or cudaFree and, when it succeeds, no
+ * host heap either (a rejected call formats its message for awg_last_error).  For callers
+ * that cannot allocate while they stream: a real-time thread feeding a DAC must not stall in the
+ * device allocator (which can synchronise the whole device and take longer than a chunk's
+ * playback time), and some host applications give the library a fixed device-memory budget
+ * up front.  Such a caller creates the handle and sets its tones and chirps beforehand, then
+ * calls this for every chunk.  The chirp tile records and their slot map go to a fixed 12 MiB
+ * scratch array compiled into the library, which every GPU that loads the library holds until
+ * the process exits.  The first call on a device looks up that array's device address, so make
+ * it before any stream capture.  AWG_ENOMEM (with a message) when the window needs more than
+ * AWG_NOALLOC_MAX_RECORDS records or a chirp slot index reaches AWG_NOALLOC_MAX_SLOTS.  All calls
+ * in the process share the scratch: each call writes every record it reads, so nothing needs to
+ * start at zero, but calls whose kernels overlap on the GPU (other streams, other handles) race
+ * -- issue them in order on one stream.  The paper has no counterpart to this entry point. */
+int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream);
+
 /* Device-side status word of the handle: 0, or the AWG_E* code a kernel raised (for instance
  * AWG_ETIMEOUT when a bounded wait on an mbarrier gave up).  Reading it synchronises.  Clears
  * the word. */

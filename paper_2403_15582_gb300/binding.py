@@ -37,6 +37,7 @@ SIGNATURES = [
     ("awg_render_phases", ctypes.c_int, [P, i32, i64, i32, P]),
     ("awg_tone_split", i32, [P]),
     ("awg_last_render_ms", ctypes.c_float, [P]),
+    ("awg_render_noalloc", ctypes.c_int, [P, i64, P, P]),
     ("awg_profile_begin", ctypes.c_int, [P]),
     ("awg_profile_end", ctypes.c_int, [P, P, P, i32, P]),
     ("awg_device_status", ctypes.c_int, [P]),
@@ -203,6 +204,9 @@ class Synth:
 
     def render(self, n: int, out, stream=None):
         _check(lib().awg_render(self._h, int(n), _ptr(out), _stream_ptr(stream)))
+
+    def render_noalloc(self, n: int, out, stream=None):
+        _check(lib().awg_render_noalloc(self._h, int(n), _ptr(out), _stream_ptr(stream)))
 
     def render_f32(self, n: int, out_f32, out_q=None, stream=None):
         _check(lib().awg_render_f32(self._h, int(n), _ptr(out_f32), _ptr(out_q), _stream_ptr(stream)))

@@ -840,6 +840,90 @@ float awg_last_render_ms(awg_t* h) {
   return ms;
 }
 
+int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (n < 0) return fail(AWG_EINVAL, "sample count must be >= 0");
+  if (n == 0) return AWG_OK;
+  if (!out) return fail(AWG_EINVAL, "null output");
+  if (h->cursor > INT64_MAX - n) return fail(AWG_EINVAL, "sample index overflow");
+  int cur = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (cur != h->device) return fail(AWG_EINVAL, "call on the device the handle was created on");
+  TileRec* recs = nullptr;
+  int32_t* act = nullptr;
+  if ((e = awgk::noalloc_scratch(cur, &recs, &act)) != cudaSuccess) return cuda_fail(e, "fixed scratch lookup");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t c = h->cursor;
+  const int64_t tile0 = c / awgk::TILE;
+  const int64_t tile_last = (c + n - 1) / awgk::TILE;
+  const int64_t n_tiles = tile_last - tile0 + 1;
+  const int64_t span0 = tile0 * awgk::TILE, span1 = (tile_last + 1) * awgk::TILE - 1;
+  auto is_active = [&](const ChirpRec& cr) {
+    return cr.tone >= 0 && !(cr.flags & awgk::TONE_EXACT) && cr.n_s <= span1 && cr.n_s + cr.L >= span0;
+  };
+  int64_t n_active = 0;
+  for (size_t sl = 0; sl < h->chirps.size(); ++sl) {
+    if (!is_active(h->chirps[sl])) continue;
+    if ((int64_t)sl >= awgk::NOALLOC_MAX_SLOTS)
+      return fail(AWG_ENOMEM, "chirp slot index beyond the fixed scratch's slot map (AWG_NOALLOC_MAX_SLOTS)");
+    ++n_active;
+  }
+  if (n_active * n_tiles > (int64_t)awgk::NOALLOC_MAX_RECORDS)
+    return fail(AWG_ENOMEM, "window needs " + std::to_string(n_active * n_tiles) +
+                                " chirp tile records; the fixed scratch holds " +
+                                std::to_string(awgk::NOALLOC_MAX_RECORDS) + " (AWG_NOALLOC_MAX_RECORDS)");
+  if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
+  awgk::PrepArgs pa;
+  std::memset(&pa, 0, sizeof(pa));
+  pa.chirps = h->d_chirps;
+  pa.recs = recs;
+  pa.act_of_slot = act;
+  pa.tile0 = tile0;
+  pa.n_tiles = (int32_t)n_tiles;
+  std::memcpy(pa.W, h->W, sizeof(pa.W));
+  std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
+  int32_t batch_base = 0;
+  for (size_t sl = 0; sl < h->chirps.size(); ++sl) {
+    if (!is_active(h->chirps[sl])) continue;
+    pa.slots[pa.n_active++] = (int32_t)sl;
+    if (pa.n_active == awgk::MAX_ACTIVE_PER_LAUNCH) {
+      pa.act_base = batch_base;
+      if ((e = awgk::launch_prep(pa, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+      batch_base += pa.n_active;
+      pa.n_active = 0;
+    }
+  }
+  if (pa.n_active > 0) {
+    pa.act_base = batch_base;
+    if ((e = awgk::launch_prep(pa, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+  }
+  awgk::RenderArgs ra;
+  std::memset(&ra, 0, sizeof(ra));
+  ra.tones = h->d_tones;
+  ra.chirps = h->d_chirps;
+  ra.recs = recs;
+  ra.act_of_slot = act;
+  ra.K = h->K;
+  ra.split = h->split;
+  ra.tile0 = tile0;
+  ra.n_tiles = (int32_t)n_tiles;
+  ra.win_start = c;
+  ra.win_end = c + n;
+  ra.out_q = out;
+  ra.out_f = nullptr;
+  ra.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
+  ra.status = h->d_status;
+  std::memcpy(ra.inv_odd, h->inv_odd, sizeof(ra.inv_odd));
+  if ((e = awgk::launch_render(ra, s)) != cudaSuccess) return cuda_fail(e, "render launch");
+  if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
+  if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
+  h->timed = true;
+  h->have_done = true;
+  h->cursor = c + n;
+  return AWG_OK;
+}
+
 int awg_profile_begin(awg_t* h) {
   if (!h) return fail(AWG_EINVAL, "null handle");
   h->profiling = true;

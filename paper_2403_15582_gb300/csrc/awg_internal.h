@@ -118,4 +118,11 @@ cudaError_t launch_phase_words(const PhaseArgs& a, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, cudaStream_t s);
 cudaError_t render_setup_attributes();
 
+// Fixed scratch of the allocation-free render (awg_noalloc.cu): 12 MiB of tile records and a map
+// for 16384 chirp slots.  Looks up the arrays' device addresses on first use for `device`, which
+// must be the current device.
+constexpr size_t NOALLOC_MAX_RECORDS = (12u << 20) / sizeof(TileRec);   // 71493
+constexpr int32_t NOALLOC_MAX_SLOTS = 16384;
+cudaError_t noalloc_scratch(int device, TileRec** recs, int32_t** act);
+
 }  // namespace awgk
