@@ -162,8 +162,8 @@ int32_t awg_tone_split(const awg_t* h);
  * valid once that render has completed (e.g. after synchronising its stream).  -1 if none. */
 float awg_last_render_ms(awg_t* h);
 
-/* Profiling mode: while on, every render records CUDA events on its stream before its chirp
- * set-up kernel, between the kernels and after the render kernel.  awg_profile_begin clears the
+/* Profiling mode: while on, every render records CUDA events on its stream around its chirp
+ * set-up kernels and around its render kernel.  awg_profile_begin clears the
  * record.  awg_profile_end waits for the last recorded event, writes per render call the device
  * time (ms) of the set-up kernel(s) and of the render kernel into prep_ms[i] / render_ms[i] for
  * i < cap (either may be NULL), stores the number of kernels launched in *launches (may be NULL),

@@ -262,22 +262,22 @@ uint64_t chirp_offset_word(const W192 d[7], int64_t m) {
   return s.w[2];
 }
 
-// Chirps whose neglected 4th..6th-order phase terms over one 32-sample run could exceed 64 units
-// of 2^-32 turn are rendered with the exact per-sample closed form instead.
+// Chirps whose neglected 4th..6th-order phase terms over one 32-sample run could exceed 512 units
+// of 2^-32 turn (1.2e-7 turn) are rendered from a per-sample table of exact phases instead.
 bool needs_exact(uint64_t F0, uint64_t F1, int64_t L, int profile) {
   if (profile == AWG_PROFILE_LINEAR) return false;
   double D = std::fabs((double)F1 - (double)F0);
   double l = (double)L;
   double bound = 31465.0 * 60.0 * D / (l * l * l) + 169911.0 * 360.0 * D / (l * l * l * l) +
                  736281.0 * 720.0 * D / (l * l * l * l * l);
-  return bound > 64.0 * 4294967296.0;
+  return bound > 512.0 * 4294967296.0;
 }
 
-int pow2_split(int K) {
-  int need = (K + 63) / 64;
-  int s = 1;
-  while (s < need && s < awgk::MAX_SPLIT) s <<= 1;
-  return s;
+// Tone split per tile: about 96 tones per CTA, at most MAX_SPLIT CTAs per cluster.  A function of
+// the tone count only, so that every sample is summed in the same order whatever the window.
+int tone_split_for(int K) {
+  int s = (K + 95) / 96;
+  return std::max(1, std::min(s, awgk::MAX_SPLIT));
 }
 
 }  // namespace
@@ -298,13 +298,15 @@ struct awg {
   ChirpRec* d_chirps = nullptr;
   int32_t* d_act = nullptr;
   size_t cap_chirps = 0;
-  TileRec* d_recs = nullptr;
+  TileRec* d_recs = nullptr;          // chirp tile records of the current render window
   size_t cap_recs = 0;
   int32_t* d_status = nullptr;
   uint64_t* d_words = nullptr;
   size_t cap_words = 0;
   uint32_t* d_trace = nullptr;
   size_t cap_trace = 0;
+  uint32_t* d_tab = nullptr;           // exact per-sample phases of TONE_EXACT chirps
+  size_t cap_tab = 0;
   int64_t cursor = 0;
   double full_scale = 0;
   bool fs_explicit = false;
@@ -313,7 +315,7 @@ struct awg {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
   bool timed = false, have_done = false;
   bool profiling = false;
-  std::vector<cudaEvent_t> prof_ev;   // 3 per recorded render call
+  std::vector<cudaEvent_t> prof_ev;   // 4 per recorded render call
   size_t prof_calls = 0;
   int64_t prof_launches = 0;
   int64_t W[7][7];
@@ -448,10 +450,39 @@ int set_tones_common(awg_t* h, const double* f, const double* amp, const double*
   h->free_slots.clear();
   h->fs_explicit = false;
   h->full_scale = default_full_scale(h);
-  h->split = pow2_split(n);
+  h->split = tone_split_for(n);
   st = upload_tones(h);
   if (st) return st;
   return upload_chirps(h);
+}
+
+// Per-sample exact 32-bit phases for every live TONE_EXACT chirp (very short, fast chirps),
+// packed one after another; the tone records get their offsets.  Chirp records must already be
+// on the device.
+int build_exact_tables(awg_t* h) {
+  size_t total = 0;
+  for (const ChirpRec& c : h->chirps)
+    if (c.tone >= 0 && (c.flags & awgk::TONE_EXACT)) total += (size_t)c.L + 1;
+  if (total == 0) return AWG_OK;
+  int st = ensure(&h->d_tab, &h->cap_tab, total, h, "exact phase tables");
+  if (st) return st;
+  size_t off = 0;
+  for (size_t sl = 0; sl < h->chirps.size(); ++sl) {
+    const ChirpRec& c = h->chirps[sl];
+    if (c.tone < 0 || !(c.flags & awgk::TONE_EXACT)) continue;
+    awgk::TableArgs ta;
+    ta.chirps = h->d_chirps;
+    ta.slot = (int32_t)sl;
+    ta.out = h->d_tab + off;
+    std::memcpy(ta.inv_odd, h->inv_odd, sizeof(ta.inv_odd));
+    cudaError_t e = awgk::launch_exact_table(ta, c.L, h->priv);
+    if (e != cudaSuccess) return cuda_fail(e, "exact table launch");
+    h->tones[(size_t)c.tone].tab_off = (int32_t)off;
+    off += (size_t)c.L + 1;
+  }
+  cudaError_t e = cudaStreamSynchronize(h->priv);
+  if (e != cudaSuccess) return cuda_fail(e, "exact tables");
+  return AWG_OK;
 }
 
 int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream) {
@@ -479,19 +510,22 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream)
   int st = ensure(&h->d_recs, &h->cap_recs, std::max<size_t>(1, active.size() * (size_t)n_tiles), h, "tile records");
   if (st) return st;
 
+  // The chirp tile set-up runs in stream order right before the render.  (Running it on a second
+  // stream, overlapped with the previous render, takes SM slots from the render and pushes its
+  // grid into a second wave; measured slower.)
   cudaError_t e;
-  cudaEvent_t pe[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
   if (h->profiling) {
-    while (h->prof_ev.size() < 3 * (h->prof_calls + 1)) {
+    while (h->prof_ev.size() < 4 * (h->prof_calls + 1)) {
       cudaEvent_t ev;
       if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "profiling event");
       h->prof_ev.push_back(ev);
     }
-    for (int i = 0; i < 3; ++i) pe[i] = h->prof_ev[3 * h->prof_calls + (size_t)i];
-    if ((e = cudaEventRecord(pe[0], s)) != cudaSuccess) return cuda_fail(e, "event");
+    for (int i = 0; i < 4; ++i) pe[i] = h->prof_ev[4 * h->prof_calls + (size_t)i];
   }
   int64_t launches = 0;
   if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
+  if (pe[0] && (e = cudaEventRecord(pe[0], s)) != cudaSuccess) return cuda_fail(e, "event");
   for (size_t b = 0; b < active.size(); b += awgk::MAX_ACTIVE_PER_LAUNCH) {
     awgk::PrepArgs pa;
     std::memset(&pa, 0, sizeof(pa));
@@ -509,9 +543,11 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream)
     ++launches;
   }
   if (pe[1] && (e = cudaEventRecord(pe[1], s)) != cudaSuccess) return cuda_fail(e, "event");
+  if (pe[2] && (e = cudaEventRecord(pe[2], s)) != cudaSuccess) return cuda_fail(e, "event");
   awgk::RenderArgs ra;
   std::memset(&ra, 0, sizeof(ra));
   ra.tones = h->d_tones;
+  ra.exact_tab = h->d_tab;
   ra.chirps = h->d_chirps;
   ra.recs = h->d_recs;
   ra.act_of_slot = h->d_act;
@@ -528,8 +564,8 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream)
   std::memcpy(ra.inv_odd, h->inv_odd, sizeof(ra.inv_odd));
   if ((e = awgk::launch_render(ra, s)) != cudaSuccess) return cuda_fail(e, "render launch");
   ++launches;
-  if (pe[2]) {
-    if ((e = cudaEventRecord(pe[2], s)) != cudaSuccess) return cuda_fail(e, "event");
+  if (pe[3]) {
+    if ((e = cudaEventRecord(pe[3], s)) != cudaSuccess) return cuda_fail(e, "event");
     ++h->prof_calls;
     h->prof_launches += launches;
   }
@@ -628,6 +664,7 @@ void awg_destroy(awg_t* h) {
   cudaFree(h->d_status);
   cudaFree(h->d_words);
   cudaFree(h->d_trace);
+  cudaFree(h->d_tab);
   for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -711,7 +748,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     c.n_s = p.ns;
     c.L = p.L;
     c.tone = p.tone;
-    c.flags = needs_exact(p.F0, p.F1, p.L, p.profile) ? awgk::TONE_EXACT : 0;
+    c.flags = (needs_exact(p.F0, p.F1, p.L, p.profile) ? awgk::TONE_EXACT : 0) |
+              (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0);
     const uint64_t phi_end = c.phi_start + chirp_offset_word(d, p.L);
     t.slot = slot;
     t.n_s = p.ns;
@@ -721,6 +759,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     t.flags = c.flags;
   }
   st = upload_chirps(h);
+  if (st) return st;
+  st = build_exact_tables(h);
   if (st) return st;
   return upload_tones(h);
 }
@@ -901,6 +941,7 @@ int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream) {
   awgk::RenderArgs ra;
   std::memset(&ra, 0, sizeof(ra));
   ra.tones = h->d_tones;
+  ra.exact_tab = h->d_tab;
   ra.chirps = h->d_chirps;
   ra.recs = recs;
   ra.act_of_slot = act;
@@ -939,12 +980,12 @@ int awg_profile_end(awg_t* h, float* prep_ms, float* render_ms, int32_t cap, int
   if (launches) *launches = h->prof_launches;
   const size_t n = h->prof_calls;
   if (n == 0) return 0;
-  cudaError_t e = cudaEventSynchronize(h->prof_ev[3 * (n - 1) + 2]);
+  cudaError_t e = cudaEventSynchronize(h->prof_ev[4 * (n - 1) + 3]);
   if (e != cudaSuccess) return cuda_fail(e, "profiling sync");
   for (size_t i = 0; i < n && (int64_t)i < (int64_t)cap; ++i) {
     float a = 0, b = 0;
-    cudaEventElapsedTime(&a, h->prof_ev[3 * i], h->prof_ev[3 * i + 1]);
-    cudaEventElapsedTime(&b, h->prof_ev[3 * i + 1], h->prof_ev[3 * i + 2]);
+    cudaEventElapsedTime(&a, h->prof_ev[4 * i], h->prof_ev[4 * i + 1]);
+    cudaEventElapsedTime(&b, h->prof_ev[4 * i + 2], h->prof_ev[4 * i + 3]);
     if (prep_ms) prep_ms[i] = a;
     if (render_ms) render_ms[i] = b;
   }

@@ -14,7 +14,7 @@ namespace awgk {
 constexpr int RUN = 32;
 constexpr int NT = 128;
 constexpr int TILE = RUN * NT;     // 4096 samples
-constexpr int STAGE = 32;          // tones staged in shared memory at a time
+constexpr int STAGE = 16;          // tones staged in shared memory at a time (double-buffered)
 constexpr int MAX_SPLIT = 16;      // cluster size limit (non-portable 16 on sm_100-class parts)
 constexpr int MAX_ACTIVE_PER_LAUNCH = 1024;
 
@@ -30,11 +30,12 @@ struct alignas(16) ToneRec {
   int64_t n_e;
   float A;
   int32_t slot;           // chirp slot, -1 if none
-  int32_t flags;          // TONE_EXACT: evaluate this chirp per sample with the exact closed form
-  int32_t pad;
+  int32_t flags;          // TONE_EXACT / TONE_LINEAR
+  int32_t tab_off;        // TONE_EXACT: offset of this chirp's per-sample phase table
 };
 static_assert(sizeof(ToneRec) == 64, "ToneRec layout");
-constexpr int32_t TONE_EXACT = 1;
+constexpr int32_t TONE_EXACT = 1;    // chirp read from a per-sample table of exact phases
+constexpr int32_t TONE_LINEAR = 2;   // linear chirp: differences of order >= 3 are exactly zero
 
 // Per-chirp record (one per live slot): the 192-bit forward-difference words.
 struct alignas(16) ChirpRec {
@@ -74,6 +75,7 @@ struct PrepArgs {
 
 struct RenderArgs {
   const ToneRec* tones;
+  const uint32_t* exact_tab;  // per-sample 32-bit phases of TONE_EXACT chirps
   const ChirpRec* chirps;
   const TileRec* recs;
   const int32_t* act_of_slot;
@@ -112,7 +114,15 @@ struct TraceArgs {      // per-sample render phases of one tone (test hook)
   uint64_t inv_odd[3][3];
 };
 
+struct TableArgs {      // exact per-sample 32-bit phases of one short chirp, m = 0..L
+  const ChirpRec* chirps;
+  int32_t slot;
+  uint32_t* out;          // L + 1 entries
+  uint64_t inv_odd[3][3];
+};
+
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
+cudaError_t launch_exact_table(const TableArgs& a, int64_t L, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
 cudaError_t launch_phase_words(const PhaseArgs& a, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, cudaStream_t s);

@@ -78,10 +78,6 @@ __device__ __forceinline__ U192 sar192(U192 a, int v) {
   return r;
 }
 
-// top 64 bits of a Q64.128 value, rounded to nearest
-__device__ __forceinline__ uint64_t round_top64(U192 a) {
-  return add192(a, U192{0, 1ull << 63, 0}).w2;
-}
 
 // C(m, j) for j = 0..6 and signed m (|m| < 2^30): the product of j consecutive integers is
 // below 2^180 in magnitude, so it is exact mod 2^192; dividing by j! = 2^v * odd is a
@@ -133,34 +129,57 @@ struct RunPoly {
   uint32_t p, f, g, h;
 };
 
-// C(j, q) for the run index j (0 <= j < NT), q = 0..6
-__device__ __forceinline__ void run_binomials(int j, uint64_t cj[7]) {
-  uint64_t u = (uint64_t)j;
-  cj[0] = 1;
-  cj[1] = u;
-  cj[2] = u * (u - 1) / 2;
-  cj[3] = cj[2] * (u - 2) / 3;
-  cj[4] = cj[3] * (u - 3) / 4;
-  cj[5] = cj[4] * (u - 4) / 5;
-  cj[6] = cj[5] * (u - 5) / 6;
-  // for j < q the product has a zero factor; the unsigned wrap of (u - i) is multiplied by it
-  if (j < 2) cj[2] = 0;
-  if (j < 3) cj[3] = 0;
-  if (j < 4) cj[4] = 0;
-  if (j < 5) cj[5] = 0;
-  if (j < 6) cj[6] = 0;
+// C(j, q) for the run index j (0 <= j < NT = 128): q <= 5 fit in 32 bits, C(j, 6) needs 33.
+struct RunBin {
+  uint32_t c1, c2, c3, c4, c5;
+  uint64_t c6;
+};
+
+__device__ __forceinline__ RunBin run_binomials(int j) {
+  RunBin b;
+  const uint64_t u = (uint64_t)j;
+  const uint64_t c2 = u * (u - 1) / 2, c3 = c2 * (u - 2) / 3, c4 = c3 * (u - 3) / 4, c5 = c4 * (u - 4) / 5;
+  b.c1 = (uint32_t)j;
+  b.c2 = (uint32_t)c2;
+  b.c3 = (uint32_t)c3;
+  b.c4 = (uint32_t)c4;
+  b.c5 = (uint32_t)c5;
+  b.c6 = c5 * (u - 5) / 6;
+  // a factor (u - i) is zero for j = i, so every product with q > j vanishes; j < q wraps (u - i)
+  // but the zero factor comes first, so the products above are already 0 for those j.
+  return b;
 }
 
-__device__ __forceinline__ RunPoly poly_state(const TileRec& rc, const uint64_t cj[7]) {
-  uint64_t p = rc.B[0], f = 0, g = 0, h = 0;
-#pragma unroll
-  for (int q = 1; q <= 6; ++q) p += rc.B[q] * cj[q];
-#pragma unroll
-  for (int q = 0; q <= 5; ++q) f += rc.E[q] * cj[q];
-#pragma unroll
-  for (int q = 0; q <= 4; ++q) g += rc.G[q] * cj[q];
-#pragma unroll
-  for (int q = 0; q <= 3; ++q) h += rc.H[q] * cj[q];
+// acc + x * c (mod 2^64) for a 32-bit c: one wide and one narrow integer multiply-add
+__device__ __forceinline__ uint64_t mac_u32(uint64_t acc, uint64_t x, uint32_t c) {
+  const uint64_t lo = (uint64_t)(uint32_t)x * c;
+  const uint32_t hi = (uint32_t)(x >> 32) * c;
+  return acc + lo + ((uint64_t)hi << 32);
+}
+
+__device__ __forceinline__ RunPoly pack_run(uint64_t p, uint64_t f, uint64_t g, uint64_t h);
+
+// (p, f, g, h) at run j from the stride-RUN records: p = sum_q B_q C(j,q), f = sum_q E_q C(j,q),
+// g = sum_q G_q C(j,q), h = sum_q H_q C(j,q), all mod 2^64.
+__device__ __forceinline__ RunPoly poly_state(const TileRec& rc, const RunBin& b, bool linear) {
+  if (linear) {   // B_q (q >= 3), E_q (q >= 2), G_q (q >= 1) and H are exactly zero
+    uint64_t p = mac_u32(mac_u32(rc.B[0], rc.B[1], b.c1), rc.B[2], b.c2);
+    uint64_t f = mac_u32(rc.E[0], rc.E[1], b.c1);
+    return pack_run(p, f, rc.G[0], 0);
+  }
+  uint64_t p = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.B[0], rc.B[1], b.c1), rc.B[2], b.c2), rc.B[3], b.c3), rc.B[4], b.c4),
+                       rc.B[5], b.c5) + rc.B[6] * b.c6;
+  asm volatile("" ::: "memory");   // evaluate the four polynomials one after another (registers)
+  uint64_t f = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.E[0], rc.E[1], b.c1), rc.E[2], b.c2), rc.E[3], b.c3), rc.E[4], b.c4),
+                       rc.E[5], b.c5);
+  asm volatile("" ::: "memory");
+  uint64_t g = mac_u32(mac_u32(mac_u32(mac_u32(rc.G[0], rc.G[1], b.c1), rc.G[2], b.c2), rc.G[3], b.c3), rc.G[4], b.c4);
+  asm volatile("" ::: "memory");
+  uint64_t h = mac_u32(mac_u32(mac_u32(rc.H[0], rc.H[1], b.c1), rc.H[2], b.c2), rc.H[3], b.c3);
+  return pack_run(p, f, g, h);
+}
+
+__device__ __forceinline__ RunPoly pack_run(uint64_t p, uint64_t f, uint64_t g, uint64_t h) {
   RunPoly r;
   r.p = (uint32_t)((p + P_OFFSET) >> 32);
   r.f = (uint32_t)((f + HALF32) >> 32);
@@ -184,7 +203,7 @@ __device__ __forceinline__ int classify_tile(const ToneRec& t, int64_t T0) {
 
 // The 32-bit phase the render feeds to the sine for sample r of run j (any segment).  The fast
 // loops below produce the same integers by stepping.
-__device__ uint32_t phase32_at(const ToneRec& t, const TileRec* rec, const ChirpRec* chirps, int64_t T0,
+__device__ __noinline__ uint32_t phase32_at(const ToneRec& t, const TileRec* rec, const ChirpRec* chirps, int64_t T0,
                                int j, int r, const uint64_t (*inv)[3]) {
   const int64_t n0 = T0 + (int64_t)j * RUN;
   const int64_t n = n0 + r;
@@ -192,17 +211,17 @@ __device__ uint32_t phase32_at(const ToneRec& t, const TileRec* rec, const Chirp
   if (t.slot < 0 || n < t.n_s) return static_p0(t.phi_ref, t.F, n0) + ur * static_f(t.F);
   if (n > t.n_e) return static_p0(t.phi_post_ref, t.F_end, n0) + ur * static_f(t.F_end);
   if (t.flags & TONE_EXACT) return (uint32_t)((exact_chirp_word(chirps[t.slot], n - t.n_s, inv) + P_OFFSET) >> 32);
-  uint64_t cj[7];
-  run_binomials(j, cj);
-  RunPoly s = poly_state(*rec, cj);
+  RunPoly s = poly_state(*rec, run_binomials(j), (t.flags & TONE_LINEAR) != 0);
   const uint32_t c2 = ur * (ur - 1) / 2, c3 = (r >= 3) ? ur * (ur - 1) * (ur - 2) / 6 : 0u;
   return s.p + ur * s.f + c2 * s.g + c3 * s.h;
 }
 
-// sin(2 pi p / 2^32): the top 23 bits of p, offset by half a turn, become the mantissa of a float
-// v in [1, 2); 2 pi (v - 3/2) lies in [-pi, pi) and is congruent to the phase.
-__device__ __forceinline__ float sin_turn(uint32_t p) {
-  const float v = __uint_as_float((p >> 9) ^ 0x3FC00000u);
+// sin(2 pi p / 2^32) for a phase already offset by half a turn (pc = p + 2^31): the top 23 bits
+// of pc become the mantissa of a float v in [1, 2); 2 pi (v - 3/2) lies in [-pi, pi) and is
+// congruent to the phase.  The half-turn offset is added once per run, not per sample.
+constexpr uint32_t HALF_TURN = 1u << 31;
+__device__ __forceinline__ float sin_centred(uint32_t pc) {
+  const float v = __uint_as_float((pc >> 9) + 0x3F800000u);
   return __sinf(fmaf(v, 6.28318530717958647692f, -9.42477796076937971538f));
 }
 
@@ -261,6 +280,97 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // ------------------------------------------------------------------------------------------
 // prep: per (active chirp, tile) stride-RUN forward differences at the tile start
 // ------------------------------------------------------------------------------------------
+// a * b mod 2^192 for a signed 64-bit b: a (b mod 2^64) - [b < 0] a 2^64
+__device__ __forceinline__ U192 mul192_s64(U192 a, int64_t bs) {
+  const uint64_t b = (uint64_t)bs;
+  unsigned __int128 p0 = (unsigned __int128)a.w0 * b;
+  unsigned __int128 p1 = (unsigned __int128)a.w1 * b + (uint64_t)(p0 >> 64);
+  U192 r;
+  r.w0 = (uint64_t)p0;
+  r.w1 = (uint64_t)p1;
+  r.w2 = a.w2 * b + (uint64_t)(p1 >> 64);
+  if (bs < 0) {
+    unsigned __int128 t = (unsigned __int128)r.w1 - a.w0;
+    r.w1 = (uint64_t)t;
+    r.w2 = r.w2 - a.w1 - (uint64_t)((t >> 64) & 1);
+  }
+  return r;
+}
+
+// C(m, j), j = 0..DEG, signed m, exact (see binomials())
+template <int DEG>
+__device__ __forceinline__ void binomials_deg(int64_t m, const uint64_t (*inv)[3], U192 c[DEG + 1]) {
+  U192 p = {1, 0, 0};
+  c[0] = p;
+#pragma unroll
+  for (int j = 1; j <= DEG; ++j) {
+    p = mul192_s64(p, m - (j - 1));
+    U192 q = p;
+    if (j == 3 || j == 4) q = mul192(q, U192{inv[0][0], inv[0][1], inv[0][2]});
+    if (j == 5) q = mul192(q, U192{inv[1][0], inv[1][1], inv[1][2]});
+    if (j == 6) q = mul192(q, U192{inv[2][0], inv[2][1], inv[2][2]});
+    const int v = (j == 2 || j == 3) ? 1 : (j == 4 || j == 5) ? 3 : (j == 6) ? 4 : 0;
+    c[j] = sar192(q, v);
+  }
+}
+
+// Upper 128 bits of a 192-bit value (units of 2^64 of the Q64.128 word, i.e. Q64.64).
+__device__ __forceinline__ unsigned __int128 hi128(U192 a) {
+  return ((unsigned __int128)a.w2 << 64) | a.w1;
+}
+// Q64.64 -> word, rounded to nearest (mod 2^64)
+__device__ __forceinline__ uint64_t round_q64(unsigned __int128 v) {
+  return (uint64_t)((v + ((unsigned __int128)1 << 63)) >> 64);
+}
+
+// DEG = 2 (linear chirps) or 6 (minimum-jerk).  The unit-stride differences at the tile start
+// are exact (192-bit); the stride-RUN transform that follows only needs the word-level result,
+// so it runs on the upper 128 bits (error < W 2^-64 word per term, below 2^-20 word).
+template <int DEG>
+__device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const PrepArgs& a, TileRec& out) {
+  U192 bin[DEG + 1];
+  binomials_deg<DEG>(m, a.inv_odd, bin);
+  U192 acc[DEG + 1];
+#pragma unroll
+  for (int k = 0; k <= DEG; ++k) {
+    U192 s = {0, 0, 0};
+#pragma unroll
+    for (int i = k; i <= DEG; ++i) s = add192(s, mul192(dword(c, i), bin[i - k]));
+    acc[k] = s;
+  }
+  unsigned __int128 h[DEG + 1];
+#pragma unroll
+  for (int k = 0; k <= DEG; ++k) h[k] = hi128(acc[k]);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    unsigned __int128 s = 0;
+#pragma unroll
+    for (int i = q; i <= DEG; ++i) s += h[i] * (unsigned __int128)(__int128)a.W[q][i];
+    out.B[q] = (q == 0) ? c.phi_start + acc[0].w2 : (q <= DEG ? round_q64(s) : 0);   // acc_0 holds 2^127
+  }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    unsigned __int128 s = 0;
+#pragma unroll
+    for (int i = q; i + 1 <= DEG; ++i) s += h[i + 1] * (unsigned __int128)(__int128)a.W[q][i];
+    out.E[q] = (q + 1 <= DEG) ? round_q64(s) : 0;
+  }
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    unsigned __int128 s = 0;
+#pragma unroll
+    for (int i = q; i + 2 <= DEG; ++i) s += h[i + 2] * (unsigned __int128)(__int128)a.W[q][i];
+    out.G[q] = (q + 2 <= DEG) ? round_q64(s) : 0;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    unsigned __int128 s = 0;
+#pragma unroll
+    for (int i = q; i + 3 <= DEG; ++i) s += h[i + 3] * (unsigned __int128)(__int128)a.W[q][i];
+    out.H[q] = (q + 3 <= DEG) ? round_q64(s) : 0;
+  }
+}
+
 __global__ void __launch_bounds__(128) prep_kernel(const __grid_constant__ PrepArgs a) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)a.n_active * a.n_tiles;
@@ -271,64 +381,95 @@ __global__ void __launch_bounds__(128) prep_kernel(const __grid_constant__ PrepA
   const ChirpRec& c = a.chirps[slot];
   if (t == 0) a.act_of_slot[slot] = a.act_base + ai;
   const int64_t T0 = (a.tile0 + t) * (int64_t)TILE;
-  const int64_t m = T0 - c.n_s;
-
-  U192 bin[7];
-  binomials(m, a.inv_odd, bin);
-  // unit-stride forward differences of the phase (Q64.128) at the tile start
-  U192 acc[7];
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    U192 s = {0, 0, 0};
-#pragma unroll
-    for (int i = k; i < 7; ++i) s = add192(s, mul192(dword(c, i), bin[i - k]));
-    acc[k] = s;
-  }
   TileRec out;
-  // B_q = sum_{i>=q} acc_i W[q][i]; E, G, H: the same for the first, second and third unit
-  // differences (acc shifted by 1, 2, 3).
-#pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    U192 s = {0, 0, 0};
-#pragma unroll
-    for (int i = q; i < 7; ++i) s = add192(s, mul192(acc[i], from_s64(a.W[q][i])));
-    out.B[q] = (q == 0) ? c.phi_start + s.w2 : round_top64(s);   // acc_0 already holds 2^127
-  }
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    U192 s = {0, 0, 0};
-#pragma unroll
-    for (int i = q; i < 6; ++i) s = add192(s, mul192(acc[i + 1], from_s64(a.W[q][i])));
-    out.E[q] = round_top64(s);
-  }
-#pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    U192 s = {0, 0, 0};
-#pragma unroll
-    for (int i = q; i < 5; ++i) s = add192(s, mul192(acc[i + 2], from_s64(a.W[q][i])));
-    out.G[q] = round_top64(s);
-  }
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    U192 s = {0, 0, 0};
-#pragma unroll
-    for (int i = q; i < 4; ++i) s = add192(s, mul192(acc[i + 3], from_s64(a.W[q][i])));
-    out.H[q] = round_top64(s);
-  }
+  if (c.flags & TONE_LINEAR) prep_one<2>(c, T0 - c.n_s, a, out);
+  else prep_one<6>(c, T0 - c.n_s, a, out);
   a.recs[(int64_t)(a.act_base + ai) * a.n_tiles + t] = out;
 }
 
 // ------------------------------------------------------------------------------------------
 // render
 // ------------------------------------------------------------------------------------------
-constexpr int RED_STRIDE = RUN + 1;   // conflict-free row stride of the per-thread partial sums
+// Per (tone, run) contribution of one staged tone, added into the thread's RUN partial sums.
+__device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, const RunBin& rb, float* col,
+                                         float (&acc)[RUN], int64_t T0, int64_t n0, const uint32_t* exact_tab) {
+  const float A = tr.A;
+  const int tcls = classify_tile(tr, T0);
+  int mode;   // 0 static before the chirp, 1 static after, 2 chirp polynomial, 3 general
+  if (tcls == TILE_PRE) {
+    mode = 0;
+  } else if (tcls == TILE_POST) {
+    mode = 1;
+  } else {
+    const int64_t last = n0 + RUN - 1;
+    if (last < tr.n_s) mode = 0;
+    else if (n0 > tr.n_e) mode = 1;
+    else if (n0 >= tr.n_s && last <= tr.n_e && !(tr.flags & TONE_EXACT)) mode = 2;
+    else mode = 3;
+  }
+  if (mode <= 1) {
+    const uint64_t phi = mode == 0 ? tr.phi_ref : tr.phi_post_ref;
+    const uint64_t F = mode == 0 ? tr.F : tr.F_end;
+    uint32_t p = static_p0(phi, F, n0) + HALF_TURN;
+    const uint32_t f = static_f(F);
+#pragma unroll
+    for (int r = 0; r < RUN; ++r) {
+      acc[r] = fmaf(A, sin_centred(p), acc[r]);
+      p += f;
+    }
+  } else if (mode == 2) {
+    const RunPoly st = poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0);
+    uint32_t p = st.p + HALF_TURN, f = st.f, g = st.g;
+    const uint32_t h = st.h;
+#pragma unroll
+    for (int r = 0; r < RUN; ++r) {
+      acc[r] = fmaf(A, sin_centred(p), acc[r]);
+      p += f;
+      f += g;
+      g += h;
+    }
+  } else {
+    // a segment boundary inside this run, or a table chirp: choose the segment per sample; the
+    // sines go to the thread's column of the partial-sum buffer, then into the accumulators
+    const uint32_t p_pre = static_p0(tr.phi_ref, tr.F, n0), f_pre = static_f(tr.F);
+    const uint32_t p_post = static_p0(tr.phi_post_ref, tr.F_end, n0), f_post = static_f(tr.F_end);
+    const bool exact = (tr.flags & TONE_EXACT) != 0;
+    RunPoly st = {0, 0, 0, 0};
+    if (!exact) st = poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0);
+    const int64_t r1 = tr.n_s - n0, r2 = tr.n_e - n0;
+    uint32_t pp = st.p, ff = st.f, gg = st.g;
+    for (int r = 0; r < RUN; ++r) {
+      uint32_t ph;
+      if (r < r1) ph = p_pre + (uint32_t)r * f_pre;
+      else if (r > r2) ph = p_post + (uint32_t)r * f_post;
+      else ph = exact ? exact_tab[tr.tab_off + (int32_t)(r - r1)] : pp;
+      col[r * NT] = sin_centred(ph + HALF_TURN);
+      pp += ff;
+      ff += gg;
+      gg += st.h;
+    }
+#pragma unroll
+    for (int r = 0; r < RUN; ++r) acc[r] = fmaf(A, col[r * NT], acc[r]);
+  }
+}
 
-__global__ void __launch_bounds__(NT) render_kernel(const __grid_constant__ RenderArgs a) {
+// Per-stage tone descriptor, built by warp 0 once per (tone, tile) so that the other threads
+// skip the classification and the 64-bit phase set-up of static segments.
+struct alignas(16) Desc {
+  uint64_t p0;    // DESC_STATIC: phase word at the tile start of the segment covering the tile
+  uint64_t F;     // DESC_STATIC: its frequency word
+  float A;
+  int32_t kind;
+  int32_t pad[2];
+};
+enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3 };
+
+__global__ void __launch_bounds__(NT, 5) render_kernel(const __grid_constant__ RenderArgs a) {
   __shared__ alignas(16) ToneRec s_tone[2][STAGE];
-  __shared__ alignas(16) TileRec s_rec[STAGE];
-  __shared__ alignas(16) float s_red[NT * RED_STRIDE];
-  __shared__ alignas(16) int16_t s_q[TILE];
-  __shared__ alignas(8) uint64_t s_bar[3];
+  __shared__ alignas(16) TileRec s_rec[2][STAGE];
+  __shared__ alignas(16) Desc s_desc[2][STAGE];
+  __shared__ alignas(16) float s_red[RUN * NT];   // partial sums, [r][thread]
+  __shared__ alignas(8) uint64_t s_bar[4];        // tones[0], tones[1], records[0], records[1]
 
   cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x;
@@ -337,143 +478,166 @@ __global__ void __launch_bounds__(NT) render_kernel(const __grid_constant__ Rend
   const int tile = blockIdx.x / split;
   const int64_t T0 = (a.tile0 + tile) * (int64_t)TILE;
   const int64_t n0 = T0 + (int64_t)tid * RUN;
+  const uint32_t run_off = (uint32_t)(tid * RUN);
   const int k_begin = (int)((int64_t)a.K * crank / split);
   const int k_end = (int)((int64_t)a.K * (crank + 1) / split);
-  const int n_tones = k_end - k_begin;
-  const int n_stages = (n_tones + STAGE - 1) / STAGE;
-
-  uint64_t cj[7];
-  run_binomials(tid, cj);
+  const int n_stages = (k_end - k_begin + STAGE - 1) / STAGE;
 
   float acc[RUN];
 #pragma unroll
   for (int r = 0; r < RUN; ++r) acc[r] = 0.f;
 
   if (tid == 0) {
-    mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    mbar_init(&s_bar[2], 1);
+#pragma unroll
+    for (int b = 0; b < 4; ++b) mbar_init(&s_bar[b], 1);
     fence_mbar_init();
   }
   __syncthreads();
 
+  // thread 0 issues the tone copies and counts the issues per barrier (for a bounded drain)
+  uint32_t issued = 0;   // 8-bit issue count per barrier
   auto issue_tones = [&](int st) {
     const int kb = k_begin + st * STAGE;
-    const int cnt = min(STAGE, k_end - kb);
-    const uint32_t bytes = (uint32_t)cnt * (uint32_t)sizeof(ToneRec);
+    const uint32_t bytes = (uint32_t)min(STAGE, k_end - kb) * (uint32_t)sizeof(ToneRec);
     fence_proxy_async();
     mbar_arrive_expect_tx(&s_bar[st & 1], bytes);
     bulk_g2s(&s_tone[st & 1][0], a.tones + kb, bytes, &s_bar[st & 1]);
+    issued += 1u << (8 * (st & 1));
   };
-  if (tid == 0 && n_stages > 0) issue_tones(0);
-
-  int fail_stage = -1, fail_kind = 0;   // kind 1: tone copy wait gave up, 2: record wait gave up
-  for (int st = 0; st < n_stages; ++st) {
-    const int buf = st & 1;
+  // warp 0, once the stage's tones have landed: descriptors, and the records of tones that
+  // chirp inside this tile
+  auto prepare_stage = [&](int st) {
+    const int b = st & 1;
     const int cnt = min(STAGE, k_end - (k_begin + st * STAGE));
-    if (tid == 0 && st + 1 < n_stages) issue_tones(st + 1);
-    bool w = mbar_wait(&s_bar[buf], (uint32_t)((st >> 1) & 1));
-    if (!__syncthreads_and(w)) {
-      fail_stage = st;
-      fail_kind = 1;
-      break;
-    }
-    // chirp tile records for the tones of this stage that chirp inside this tile
-    if (tid < 32) {
-      bool need = false;
-      const TileRec* src = nullptr;
-      if (tid < cnt) {
-        const ToneRec& tr = s_tone[buf][tid];
-        if (classify_tile(tr, T0) == TILE_CHIRP && !(tr.flags & TONE_EXACT)) {
+    bool need = false;
+    const TileRec* src = nullptr;
+    if (tid < cnt) {
+      const ToneRec& tr = s_tone[b][tid];
+      Desc d;
+      d.A = tr.A;
+      d.pad[0] = d.pad[1] = 0;
+      const int tcls = classify_tile(tr, T0);
+      const bool exact = (tr.flags & TONE_EXACT) != 0;
+      if (tcls == TILE_PRE) {
+        d.kind = DESC_STATIC;
+        d.F = tr.F;
+        d.p0 = tr.phi_ref + (uint64_t)T0 * tr.F;
+      } else if (tcls == TILE_POST) {
+        d.kind = DESC_STATIC;
+        d.F = tr.F_end;
+        d.p0 = tr.phi_post_ref + (uint64_t)T0 * tr.F_end;
+      } else {
+        d.F = 0;
+        d.p0 = 0;
+        const bool inside = T0 >= tr.n_s && T0 + TILE - 1 <= tr.n_e;
+        d.kind = (inside && !exact) ? ((tr.flags & TONE_LINEAR) ? DESC_LINEAR : DESC_MINJERK) : DESC_MIXED;
+        if (!exact) {
           need = true;
           src = a.recs + (int64_t)a.act_of_slot[tr.slot] * a.n_tiles + tile;
         }
       }
-      const unsigned mask = __ballot_sync(0xffffffffu, need);
-      if (tid == 0) {
-        fence_proxy_async();
-        mbar_arrive_expect_tx(&s_bar[2], (uint32_t)__popc(mask) * (uint32_t)sizeof(TileRec));
-      }
-      __syncwarp();
-      if (need) bulk_g2s(&s_rec[tid], src, (uint32_t)sizeof(TileRec), &s_bar[2]);
+      s_desc[b][tid] = d;
     }
-    w = mbar_wait(&s_bar[2], (uint32_t)(st & 1));
-    if (!__syncthreads_and(w)) {
+    const unsigned mask = __ballot_sync(0xffffffffu, need);
+    if (tid == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&s_bar[2 + b], (uint32_t)__popc(mask) * (uint32_t)sizeof(TileRec));
+      issued += 1u << (8 * (2 + b));
+    }
+    __syncwarp();
+    if (need) bulk_g2s(&s_rec[b][tid], src, (uint32_t)sizeof(TileRec), &s_bar[2 + b]);
+  };
+
+  bool ok = true;
+  if (n_stages > 0) {
+    if (tid == 0) {
+      issue_tones(0);
+      if (n_stages > 1) issue_tones(1);
+    }
+    if (tid < 32) {
+      ok &= mbar_wait(&s_bar[0], 0);
+      prepare_stage(0);
+    }
+    __syncthreads();   // stage-0 descriptors visible
+  }
+  int fail_stage = -1;
+  const RunBin rb = run_binomials(tid);
+  for (int st = 0; st < n_stages; ++st) {
+    const int b = st & 1;
+    const uint32_t par = (uint32_t)((st >> 1) & 1);
+    if (tid < 32 && st + 1 < n_stages) {
+      ok &= mbar_wait(&s_bar[(st + 1) & 1], (uint32_t)(((st + 1) >> 1) & 1));
+      prepare_stage(st + 1);
+    }
+    ok &= mbar_wait(&s_bar[b], par);
+    ok &= mbar_wait(&s_bar[2 + b], par);
+    if (ok) {
+      const int cnt = min(STAGE, k_end - (k_begin + st * STAGE));
+      for (int i = 0; i < cnt; ++i) {
+        const Desc& d = s_desc[b][i];
+        const int kind = d.kind;
+        const float A = d.A;
+        if (kind == DESC_STATIC) {
+          uint32_t p = (uint32_t)((mac_u32(d.p0 + P_OFFSET, d.F, run_off)) >> 32) + HALF_TURN;
+          const uint32_t f = static_f(d.F);
+#pragma unroll
+          for (int r = 0; r < RUN; ++r) {
+            acc[r] = fmaf(A, sin_centred(p), acc[r]);
+            p += f;
+          }
+        } else if (kind == DESC_LINEAR) {
+          const RunPoly q = poly_state(s_rec[b][i], rb, true);
+          uint32_t p = q.p + HALF_TURN, f = q.f;
+          const uint32_t g = q.g;
+#pragma unroll
+          for (int r = 0; r < RUN; ++r) {
+            acc[r] = fmaf(A, sin_centred(p), acc[r]);
+            p += f;
+            f += g;
+          }
+        } else if (kind == DESC_MINJERK) {
+          const RunPoly q = poly_state(s_rec[b][i], rb, false);
+          uint32_t p = q.p + HALF_TURN, f = q.f, g = q.g;
+          const uint32_t h = q.h;
+#pragma unroll
+          for (int r = 0; r < RUN; ++r) {
+            acc[r] = fmaf(A, sin_centred(p), acc[r]);
+            p += f;
+            f += g;
+            g += h;
+          }
+        } else {
+          tone_run(s_tone[b][i], &s_rec[b][i], rb, &s_red[tid], acc, T0, n0, a.exact_tab);
+        }
+      }
+    }
+    if (!__syncthreads_and(ok)) {   // stage buffers free, next stage's descriptors visible
       fail_stage = st;
-      fail_kind = 2;
       break;
     }
-
-    for (int i = 0; i < cnt; ++i) {
-      const ToneRec& tr = s_tone[buf][i];
-      const float A = tr.A;
-      const int tcls = classify_tile(tr, T0);
-      int mode;   // 0 static pre, 1 static post, 2 poly, 3 general
-      if (tcls == TILE_PRE) {
-        mode = 0;
-      } else if (tcls == TILE_POST) {
-        mode = 1;
-      } else {
-        const int64_t last = n0 + RUN - 1;
-        if (last < tr.n_s) mode = 0;
-        else if (n0 > tr.n_e) mode = 1;
-        else if (n0 >= tr.n_s && last <= tr.n_e && !(tr.flags & TONE_EXACT)) mode = 2;
-        else mode = 3;
-      }
-      if (mode <= 1) {
-        const uint64_t phi = mode == 0 ? tr.phi_ref : tr.phi_post_ref;
-        const uint64_t F = mode == 0 ? tr.F : tr.F_end;
-        uint32_t p = static_p0(phi, F, n0);
-        const uint32_t f = static_f(F);
-#pragma unroll
-        for (int r = 0; r < RUN; ++r) {
-          acc[r] = fmaf(A, sin_turn(p), acc[r]);
-          p += f;
-        }
-      } else if (mode == 2) {
-        RunPoly s = poly_state(s_rec[i], cj);
-        uint32_t p = s.p, f = s.f, g = s.g;
-        const uint32_t h = s.h;
-#pragma unroll
-        for (int r = 0; r < RUN; ++r) {
-          acc[r] = fmaf(A, sin_turn(p), acc[r]);
-          p += f;
-          f += g;
-          g += h;
-        }
-      } else {
-        float* row = &s_red[tid * RED_STRIDE];
-        for (int r = 0; r < RUN; ++r)
-          row[r] = sin_turn(phase32_at(tr, &s_rec[i], a.chirps, T0, tid, r, a.inv_odd));
-#pragma unroll
-        for (int r = 0; r < RUN; ++r) acc[r] = fmaf(A, row[r], acc[r]);
-      }
-    }
-    __syncthreads();   // stage buffers and records are reused by the next stage
+    if (tid == 0 && st + 2 < n_stages) issue_tones(st + 2);
   }
   if (fail_stage >= 0) {
-    // report, then let the copies still in flight land (bounded) before shared memory goes away
+    // report, then let every copy still in flight land (bounded) before shared memory goes away
     if (tid == 0) {
       atomicExch(a.status, STATUS_TIMEOUT);
-      const int st = fail_stage;
-      if (fail_kind == 1) (void)mbar_wait(&s_bar[st & 1], (uint32_t)((st >> 1) & 1));
-      if (st + 1 < n_stages) (void)mbar_wait(&s_bar[(st + 1) & 1], (uint32_t)(((st + 1) >> 1) & 1));
-      if (fail_kind == 2) (void)mbar_wait(&s_bar[2], (uint32_t)(st & 1));
+      for (int bb = 0; bb < 4; ++bb) {
+        const uint32_t cnt_b = (issued >> (8 * bb)) & 0xffu;
+        if (cnt_b > 0) (void)mbar_wait(&s_bar[bb], (cnt_b - 1) & 1u);
+      }
     }
     __syncthreads();
   }
 
-  // partial sums -> shared memory, then cluster-wide reduction in rank order
-  {
-    float* row = &s_red[tid * RED_STRIDE];
+  // partial sums -> shared memory ([r][thread]), then the cluster-wide sum in rank order
 #pragma unroll
-    for (int r = 0; r < RUN; ++r) row[r] = acc[r];
-  }
+  for (int r = 0; r < RUN; ++r) s_red[r * NT + tid] = acc[r];
   cluster.sync();
 
-  const int slice = TILE / split;          // samples reduced and stored by this CTA
-  const int per = slice / NT;              // per thread (32 / split, >= 2)
-  const int s_first = crank * slice + tid * per;
+  // this CTA reduces and stores samples [lo, hi) of the tile; thread t takes `per` consecutive ones
+  const int lo = (int)((int64_t)TILE * crank / split), hi = (int)((int64_t)TILE * (crank + 1) / split);
+  const int per = (hi - lo + NT - 1) / NT;
+  const int s_first = lo + tid * per;
   float xs[RUN];
 #pragma unroll
   for (int u = 0; u < RUN; ++u) xs[u] = 0.f;
@@ -481,32 +645,24 @@ __global__ void __launch_bounds__(NT) render_kernel(const __grid_constant__ Rend
     const float* rem = cluster.map_shared_rank(s_red, c);
 #pragma unroll
     for (int u = 0; u < RUN; ++u) {
-      if (u < per) {
-        const int s = s_first + u;
-        xs[u] += rem[(s / RUN) * RED_STRIDE + (s % RUN)];
-      }
+      const int sidx = s_first + u;
+      if (u < per && sidx < hi) xs[u] += rem[(sidx % RUN) * NT + sidx / RUN];
     }
   }
-  cluster.sync();   // remote reads done; shared memory may be reused
+  cluster.sync();   // remote reads done before any CTA of the cluster exits
 
-  // scale, round half to even, clamp, stage, then coalesced stores of the window part
+  // scale, round half to even, clamp, store the window part
 #pragma unroll
   for (int u = 0; u < RUN; ++u) {
-    if (u < per) {
-      const int s = s_first + u - crank * slice;
-      float q = rintf(xs[u] * a.scale);
-      q = fminf(fmaxf(q, -32767.f), 32767.f);
-      s_q[s] = (int16_t)q;
-      if (a.out_f) s_red[s] = xs[u];
-    }
-  }
-  __syncthreads();
-  const int64_t base = T0 + (int64_t)crank * slice;
-  for (int i = tid; i < slice; i += NT) {
-    const int64_t n = base + i;
-    if (n >= a.win_start && n < a.win_end) {
-      if (a.out_q) a.out_q[n - a.win_start] = s_q[i];
-      if (a.out_f) a.out_f[n - a.win_start] = s_red[i];
+    const int sidx = s_first + u;
+    if (u < per && sidx < hi) {
+      const int64_t n = T0 + sidx;
+      if (n >= a.win_start && n < a.win_end) {
+        float q = rintf(xs[u] * a.scale);
+        q = fminf(fmaxf(q, -32767.f), 32767.f);
+        if (a.out_q) a.out_q[n - a.win_start] = (int16_t)q;
+        if (a.out_f) a.out_f[n - a.win_start] = xs[u];
+      }
     }
   }
 }
@@ -516,6 +672,13 @@ __global__ void phase_words_kernel(const __grid_constant__ PhaseArgs a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= a.n) return;
   a.out[k] = exact_word(a.tones[k], a.chirps, a.sample, a.inv_odd);
+}
+
+// Exact per-sample 32-bit phases of a short chirp (TONE_EXACT), m = 0..L.
+__global__ void exact_table_kernel(const __grid_constant__ TableArgs a, int64_t L) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m > L) return;
+  a.out[m] = (uint32_t)((exact_chirp_word(a.chirps[a.slot], m, a.inv_odd) + P_OFFSET) >> 32);
 }
 
 // The render's per-sample 32-bit phases of one tone (test hook).
@@ -563,6 +726,12 @@ cudaError_t launch_render(const RenderArgs& a, cudaStream_t s) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, render_kernel, a);
+}
+
+cudaError_t launch_exact_table(const TableArgs& a, int64_t L, cudaStream_t s) {
+  const int64_t n = L + 1;
+  exact_table_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(a, L);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_phase_words(const PhaseArgs& a, cudaStream_t s) {
