@@ -37,9 +37,9 @@ PAPER_TONE_SAMPLES_PER_S = 9.8e9 / 0.610
 SFU_SIN_PER_CLK_SM = 16
 N_SM = 152
 SM_MAX_MHZ = 2070.0
-# DRAM traffic of one render launch (2^18-sample chunk, 1000 chirping tones) from the ncu capture
-# summarised in profiles/; None until a capture of the current kernel exists.
-RENDER_TRAFFIC_BYTES = None
+# DRAM traffic (read + write) of one render launch (2^18-sample chunk, 1000 chirping tones) from
+# the ncu capture summarised in profiles/render_kernel_chirp1000_chunk2e18.md (cold cache).
+RENDER_TRAFFIC_BYTES = 11.419136e6
 
 CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
                 "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
