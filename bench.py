@@ -157,6 +157,26 @@ def run_reference(args, wk):
     return 0
 
 
+def stream_leg(awg, fs: float, stream, seconds: float = 1.0, n_slots: int = 4, prefill: int = 2):
+    """Continuous stream of 10,000 tones whose groups of 100 ramp in turn (1 ms linear ramps),
+    2^20-sample chunks through the pinned ring with a real-time host sink: underruns and chunk
+    latency."""
+    from paper_2403_15582_gb300 import workloads as wl
+    from paper_2403_15582_gb300.stream import run_stream
+    wk = wl.stream_rotating(seed=0, fs=fs, seconds=seconds)
+    synth = awg.Synth(fs)
+    synth.set_tones(wk.freq_hz, wk.amp, wk.phase_rad)
+    ring = awg.Ring(synth, wk.chunk, n_slots)
+    n_chunks = -(-wk.n_samples // wk.chunk)
+    st = run_stream(synth, ring, wk.chirps, n_chunks, stream, prefill=prefill)
+    ring.close()
+    synth.close()
+    return {"tones": wk.K, "fs_hz": fs, "chunk": wk.chunk, "chunks": int(st["played"]), "underruns": int(st["underruns"]),
+            "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"]},
+            "min_lead_ms": st["lead_min_ms"], "playback_ms": st["chunk_playback_ms"], "slots": n_slots,
+            "required_tone_samples_per_s": wk.K * fs}
+
+
 def config(wk, args):
     return {"workload": "chirp-1000tone-35ms-280MSps", "tones": wk.K, "samples": wk.n_samples, "chunk": wk.chunk,
             "fs_hz": wk.fs, "profiles": "linear (even tones) / minimum-jerk (odd tones)",
@@ -171,6 +191,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-stream", action="store_true")
     args = ap.parse_args()
     wk = workload()
     if args.impl == "reference":
@@ -294,6 +315,8 @@ def main():
         "kernel_ms_per_step": {"prep": float(np.sum(prep_ms)) / args.steps,
                                "render": float(np.sum(render_ms)) / args.steps},
     }
+    if not args.no_stream:
+        line["stream"] = {f"{int(fs_/1e6)}MSps": stream_leg(awg, fs_, stream) for fs_ in (280e6, 50e6)}
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_window_rate(wk, args.cpu_seconds)
     print(json.dumps(line), flush=True)

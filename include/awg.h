@@ -127,6 +127,9 @@ int awg_set_full_scale(awg_t* h, double fs_value);
 /* Current full-scale value. */
 double awg_full_scale(const awg_t* h);
 
+/* Sample rate the handle was created with (Hz), 0 for NULL. */
+double awg_sample_rate(const awg_t* h);
+
 /* Move the render cursor to an absolute sample (>= 0).  Rendering depends only on absolute
  * indices and the current tone and chirp state, so seeking back reproduces earlier output bit
  * for bit as long as no chirp set since then has folded an earlier chirp of the same tone. */
@@ -196,6 +199,51 @@ int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream);
  * AWG_ETIMEOUT when a bounded wait on an mbarrier gave up).  Reading it synchronises.  Clears
  * the word. */
 int awg_device_status(awg_t* h);
+
+/* ------------------------------------------------------------------------------------------
+ * Streaming ring (the Streaming pathway, Sec. IV-B, with the DAC card replaced by a host sink).
+ * n_slots chunk slots of int16 samples live in pinned, device-mapped host memory; awg_ring_push
+ * renders the handle's next chunk straight into the next slot; a sink thread plays chunk c at
+ * t_start + c * chunk / fs (t_start: when the first `prefill` chunks are complete), reading every
+ * sample of the slot, and frees the slot.  A chunk that is not complete at its play time is an
+ * underrun (the card's FIFO would have run dry).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct awg_ring awg_ring_t;
+
+typedef struct {
+  int64_t played;            /* chunks played */
+  int64_t underruns;         /* chunks that were not complete at their play time */
+  double latency_p50_ms;     /* GPU completion minus push time (host clock), per chunk */
+  double latency_p99_ms;
+  double latency_max_ms;
+  double lead_min_ms;        /* play time minus GPU completion: the smallest margin seen */
+  double lead_p50_ms;
+  double chunk_playback_ms;  /* chunk / fs */
+  uint64_t checksum;         /* FNV-style hash over every played sample, in play order */
+} awg_ring_stats_t;
+
+/* Ring of n_slots (2..1024) chunks of `chunk` samples (1..2^30) fed by handle h.  NULL on error. */
+awg_ring_t* awg_ring_create(awg_t* h, int64_t chunk, int32_t n_slots);
+
+/* Stop the sink (if running), wait for outstanding renders and free the ring.  NULL is allowed. */
+void awg_ring_destroy(awg_ring_t* r);
+
+/* Render the handle's next chunk into the next slot on `stream` (asynchronously) and hand it to
+ * the sink.  Waits up to timeout_ms while that slot still holds a chunk the sink has not played;
+ * AWG_ETIMEOUT if it stays occupied.  Advances the handle's cursor by one chunk. */
+int awg_ring_push(awg_ring_t* r, void* stream, int32_t timeout_ms);
+
+/* Start the sink thread: it waits for `prefill` (1..n_slots) chunks, then plays n_chunks chunks
+ * (n_chunks < 0: until awg_ring_finish).  If capture is non-NULL, the played samples are also
+ * copied there in play order, up to capture_samples. */
+int awg_ring_start(awg_ring_t* r, int32_t prefill, int64_t n_chunks, int16_t* capture, int64_t capture_samples);
+
+/* Wait up to timeout_ms for the sink to play its n_chunks, stop it, and fill *out (may be NULL).
+ * AWG_ETIMEOUT if the chunks were not all played, or the sink gave up waiting for a chunk. */
+int awg_ring_finish(awg_ring_t* r, int32_t timeout_ms, awg_ring_stats_t* out);
+
+/* Host pointer to the samples of slot i (NULL if out of range). */
+const int16_t* awg_ring_slot(const awg_ring_t* r, int32_t i);
 
 #ifdef __cplusplus
 }

@@ -329,3 +329,36 @@ def chirp_end_word(w: Waveform, k: int) -> int:
     """Phi at the last chirp sample m = L (the post-chirp anchor of Eq. freqchirp case 2)."""
     F, phi, hc, ns, L, d, Fe = _tone_args(w, k)
     return int(lib().oracle_chirp_end_word(F, phi, ns, L, _p(d)))
+
+
+def make_waveform_window(fs: float, freq_hz, amp, phase_rad, chirps, n0: int, N: int) -> Waveform:
+    """Waveform state for the window [n0, n0+N) when tones chirp several times.
+
+    Each tone's chirps are applied in time order; a chirp that ends before n0 is folded into the
+    tone's static state (the tone continues at f_end from the phase reached at the chirp's end,
+    Eq. freqchirp case 2), and the chirp overlapping the window (at most one per tone) is kept."""
+    w = make_waveform(fs, freq_hz, amp, phase_rad)
+    by_tone = {}
+    for c in chirps:
+        by_tone.setdefault(int(c["tone"]), []).append(c)
+    for k, lst in by_tone.items():
+        lst.sort(key=lambda c: c.get("start_sample", 0))
+        for c in lst:
+            Fs_ = freq_word(c["f_start"], fs)
+            Fe_ = freq_word(c["f_end"], fs)
+            L = chirp_length(c["duration"], fs)
+            ns = int(c.get("start_sample", 0))
+            if ns >= n0 + N:
+                break
+            if w.has_chirp[k]:   # fold the previous chirp
+                end = chirp_end_word(w, k)
+                n_e = w.n_s[k] + w.L[k]
+                w.F[k] = w.F_end[k]
+                w.phi_ref[k] = (end - n_e * w.F_end[k]) % (1 << 64)
+                w.has_chirp[k] = 0
+            w.has_chirp[k], w.n_s[k], w.L[k] = 1, ns, L
+            w.d[k] = chirp_coefficients(Fs_, Fe_, L, int(c["profile"]))
+            w.F_end[k] = Fe_
+            if ns + L >= n0:
+                break
+    return w

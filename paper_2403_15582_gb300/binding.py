@@ -29,6 +29,13 @@ SIGNATURES = [
     ("awg_set_chirps", ctypes.c_int, [P, P, P, P, P, P, P, i32]),
     ("awg_set_full_scale", ctypes.c_int, [P, dbl]),
     ("awg_full_scale", dbl, [P]),
+    ("awg_sample_rate", dbl, [P]),
+    ("awg_ring_create", P, [P, i64, i32]),
+    ("awg_ring_destroy", None, [P]),
+    ("awg_ring_push", ctypes.c_int, [P, P, i32]),
+    ("awg_ring_start", ctypes.c_int, [P, i32, i64, P, i64]),
+    ("awg_ring_finish", ctypes.c_int, [P, i32, P]),
+    ("awg_ring_slot", P, [P, i32]),
     ("awg_seek", ctypes.c_int, [P, i64]),
     ("awg_cursor", i64, [P]),
     ("awg_render", ctypes.c_int, [P, i64, P, P]),
@@ -241,3 +248,56 @@ class Synth:
     def device_status(self) -> int:
         v = lib().awg_device_status(self._h)
         return int(v)
+
+
+class RingStats(ctypes.Structure):
+    _fields_ = [("played", ctypes.c_int64), ("underruns", ctypes.c_int64), ("latency_p50_ms", ctypes.c_double),
+                ("latency_p99_ms", ctypes.c_double), ("latency_max_ms", ctypes.c_double), ("lead_min_ms", ctypes.c_double),
+                ("lead_p50_ms", ctypes.c_double), ("chunk_playback_ms", ctypes.c_double), ("checksum", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Ring:
+    """Streaming ring of pinned host chunk slots fed by a Synth and drained by a sink thread."""
+
+    def __init__(self, synth: Synth, chunk: int, n_slots: int):
+        r = lib().awg_ring_create(synth.handle, int(chunk), int(n_slots))
+        if not r:
+            raise AwgError(AWG_EINVAL, lib().awg_last_error().decode())
+        self._r = ctypes.c_void_p(r)
+        self.synth = synth
+        self.chunk = int(chunk)
+        self.n_slots = int(n_slots)
+
+    def close(self):
+        if getattr(self, "_r", None):
+            lib().awg_ring_destroy(self._r)
+            self._r = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def push(self, stream=None, timeout_ms: int = 10000):
+        _check(lib().awg_ring_push(self._r, _stream_ptr(stream), int(timeout_ms)))
+
+    def start(self, prefill: int, n_chunks: int, capture: np.ndarray | None = None):
+        cap_p = _p(capture) if capture is not None else ctypes.c_void_p(0)
+        cap_n = int(capture.size) if capture is not None else 0
+        self._capture = capture
+        _check(lib().awg_ring_start(self._r, int(prefill), int(n_chunks), cap_p, cap_n))
+
+    def finish(self, timeout_ms: int = 60000) -> dict:
+        st = RingStats()
+        _check(lib().awg_ring_finish(self._r, int(timeout_ms), ctypes.byref(st)))
+        return st.as_dict()
+
+    def slot(self, i: int) -> np.ndarray:
+        ptr = lib().awg_ring_slot(self._r, int(i))
+        if not ptr:
+            raise AwgError(AWG_EINVAL, "slot index out of range")
+        return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_int16)), shape=(self.chunk,)).copy()

@@ -24,6 +24,14 @@ int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+
+}  // namespace
+
+namespace awgk {
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace awgk
+
+namespace {
 int cuda_fail(cudaError_t e, const char* what) {
   return fail(AWG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
@@ -406,6 +414,21 @@ int upload_chirps(awg_t* h) {
   return AWG_OK;
 }
 
+// Upload the records at the given (sorted, unique) indices, one copy per run of adjacent indices.
+template <class T>
+int upload_runs(T* dev, const std::vector<T>& host, const std::vector<int32_t>& idx, const char* what) {
+  size_t i = 0;
+  while (i < idx.size()) {
+    size_t j = i + 1;
+    while (j < idx.size() && idx[j] == idx[j - 1] + 1) ++j;
+    const size_t first = (size_t)idx[i], count = (size_t)(idx[j - 1] - idx[i] + 1);
+    cudaError_t e = cudaMemcpy(dev + first, host.data() + first, count * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    i = j;
+  }
+  return AWG_OK;
+}
+
 double default_full_scale(const awg_t* h) {
   double s = 0;
   for (double a : h->amp) s += std::fabs(a);
@@ -720,8 +743,11 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   }
   int st = wait_idle(h);
   if (st) return st;
+  const size_t slots_before = h->chirps.size();
+  std::vector<int32_t> changed_tones, changed_slots;
   for (const Pending& p : pend) {
     ToneRec& t = h->tones[(size_t)p.tone];
+    changed_tones.push_back(p.tone);
     if (t.slot >= 0) {   // fold the finished chirp into the static state
       t.phi_ref = t.phi_post_ref;
       t.F = t.F_end;
@@ -740,6 +766,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
       slot = (int32_t)h->chirps.size();
       h->chirps.push_back(ChirpRec{});
     }
+    changed_slots.push_back(slot);
     ChirpRec& c = h->chirps[(size_t)slot];
     std::memset(&c, 0, sizeof(c));
     for (int k = 0; k < 7; ++k)
@@ -758,11 +785,22 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     t.phi_post_ref = phi_end - (uint64_t)t.n_e * p.F1;
     t.flags = c.flags;
   }
-  st = upload_chirps(h);
+  // only the records that changed go to the device (the whole chirp array if it had to grow)
+  std::sort(changed_tones.begin(), changed_tones.end());
+  std::sort(changed_slots.begin(), changed_slots.end());
+  changed_slots.erase(std::unique(changed_slots.begin(), changed_slots.end()), changed_slots.end());
+  if (h->chirps.size() > h->cap_chirps || slots_before == 0) {
+    st = upload_chirps(h);
+  } else {
+    st = upload_runs(h->d_chirps, h->chirps, changed_slots, "upload chirps");
+  }
   if (st) return st;
   st = build_exact_tables(h);
   if (st) return st;
-  return upload_tones(h);
+  bool any_exact = false;
+  for (const ChirpRec& c : h->chirps) any_exact |= (c.tone >= 0 && (c.flags & awgk::TONE_EXACT));
+  if (any_exact) return upload_tones(h);   // table offsets may have moved for any exact tone
+  return upload_runs(h->d_tones, h->tones, changed_tones, "upload tones");
 }
 
 int awg_set_full_scale(awg_t* h, double v) {
@@ -779,6 +817,8 @@ int awg_set_full_scale(awg_t* h, double v) {
 }
 
 double awg_full_scale(const awg_t* h) { return h ? h->full_scale : 0.0; }
+
+double awg_sample_rate(const awg_t* h) { return h ? h->fs : 0.0; }
 
 int awg_seek(awg_t* h, int64_t sample) {
   if (!h) return fail(AWG_EINVAL, "null handle");

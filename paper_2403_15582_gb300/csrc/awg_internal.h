@@ -2,6 +2,7 @@
 // Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace awgk {
@@ -134,5 +135,8 @@ cudaError_t render_setup_attributes();
 constexpr size_t NOALLOC_MAX_RECORDS = (12u << 20) / sizeof(TileRec);   // 71493
 constexpr int32_t NOALLOC_MAX_SLOTS = 16384;
 cudaError_t noalloc_scratch(int device, TileRec** recs, int32_t** act);
+
+// Sets the message awg_last_error() returns on this thread; returns `code`.
+int set_error(int code, const std::string& msg);
 
 }  // namespace awgk

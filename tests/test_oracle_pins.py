@@ -362,3 +362,32 @@ def test_pins_catch_planted_mistakes(oracle, monkeypatch, mistake):
     err = _chirp_max_word_error(oracle, 2.0**28, 50331648.0, 83886080.0, 4096, profile, np.arange(0, 4200, 7), False)
     assert err > 1 << 40
     monkeypatch.setattr(oracle, "chirp_phase_poly", good)
+
+
+def test_repeated_chirps_fold_continuously(oracle):
+    """A tone chirped twice: inside and after the second chirp, the folded oracle state follows
+    the exact rational phase of Eq. freqchirp applied twice in a row (case 2 between them)."""
+    fs = 2.0**28
+    f0, f1, f2 = 50331648.0, 83886080.0, 16777216.0
+    L1, L2, n1, n2 = 4096, 2048, 100, 9000
+    chirps = [dict(tone=0, f_start=f0, f_end=f1, duration=L1 / fs, profile=1, start_sample=n1),
+              dict(tone=0, f_start=f1, f_end=f2, duration=L2 / fs, profile=0, start_sample=n2)]
+    Fr = Fraction(fs)
+    e0, e1, e2 = (Fraction(oracle.freq_word(x, fs)) * Fr / TWO64 for x in (f0, f1, f2))
+    th = 0.7
+    start1 = Fraction(oracle.phase_word(th), TWO64) + e0 * n1 / Fr
+    end1 = start1 + paper_chirp_turns(L1, Fr, e0, e1, L1, 1)
+
+    def exact_turns(n):
+        if n <= n1 + L1:
+            return start1 + paper_chirp_turns(n - n1, Fr, e0, e1, L1, 1)
+        if n < n2:
+            return end1 + e1 * (n - n1 - L1) / Fr
+        start2 = end1 + e1 * (n2 - n1 - L1) / Fr
+        return start2 + paper_chirp_turns(n - n2, Fr, e1, e2, L2, 0)
+
+    for n0 in (n2 - 50, n2 + 1000, n2 + L2 - 5):
+        w = oracle.make_waveform_window(fs, [f0], [1.0], [th], chirps, n0, 64)
+        words = oracle.phase_words_seq(w, 0, n0, 64)
+        for i, wd in enumerate(words):
+            assert abs(_sdiff(wd, round(exact_turns(n0 + i) * TWO64))) <= 3, (n0, i)
