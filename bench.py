@@ -177,6 +177,56 @@ def stream_leg(awg, fs: float, stream, seconds: float = 1.0, n_slots: int = 4, p
             "required_tone_samples_per_s": wk.K * fs}
 
 
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def table_leg(awg, stream, reps: int = 3):
+    """Periodic 10,000-tone table of 2^24 samples: split-precision tcgen05 GEMM (FP16 and BF16 hi+lo)
+    against the direct-sum render of the same record on the same GPU."""
+    import numpy as np
+    import torch
+    from paper_2403_15582_gb300 import workloads as wl
+    wk = wl.table_10000(seed=0)
+    lg = wk.grid_log2
+    N = 1 << lg
+    synth = awg.Synth(wk.fs)
+    synth.set_tones(wk.freq_hz, wk.amp, wk.phase_rad, grid_log2=lg)
+    q = torch.empty(N, dtype=torch.int16, device="cuda")
+    out = {"workload": f"table-{wk.K}tone-2^{lg}", "tone_samples": wk.K * N}
+    peaks, src = measured_peaks()
+    flops = 3 * 2.0 * (N // 256) * 256 * (2 * wk.K)          # three hi/lo products, 2K inner terms
+    for prec, name in ((1, "fp16"), (0, "bf16")):
+        synth.table_gemm(lg, prec, q, None, stream)          # warm-up
+        synth.profile_begin()
+        for _ in range(reps):
+            synth.table_gemm(lg, prec, q, None, stream)
+        torch.cuda.synchronize()
+        prep, gemm, _ = synth.profile_end()
+        g = float(np.median(gemm))
+        out[name] = {"gemm_ms": g, "operand_prep_ms": float(np.median(prep)),
+                     "tflops": flops / (g * 1e-3) / 1e12,
+                     "frac_of_bf16_peak": flops / (g * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                     "tone_samples_per_s": wk.K * N / (g * 1e-3)}
+    synth.profile_begin()
+    for _ in range(reps):
+        synth.seek(0)
+        synth.render(N, q, stream)
+    torch.cuda.synchronize()
+    prep, rend, _ = synth.profile_end()
+    d = float(np.median(prep + rend))
+    out["direct_ms"] = d
+    out["direct_tone_samples_per_s"] = wk.K * N / (d * 1e-3)
+    out["peak_source"] = f"{src} bf16 {peaks['bf16_tflops']} TFLOP/s (FP16 dense rate taken equal)"
+    synth.close()
+    return out
+
+
 def config(wk, args):
     return {"workload": "chirp-1000tone-35ms-280MSps", "tones": wk.K, "samples": wk.n_samples, "chunk": wk.chunk,
             "fs_hz": wk.fs, "profiles": "linear (even tones) / minimum-jerk (odd tones)",
@@ -192,6 +242,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--no-table", action="store_true")
     args = ap.parse_args()
     wk = workload()
     if args.impl == "reference":
@@ -315,6 +366,8 @@ def main():
         "kernel_ms_per_step": {"prep": float(np.sum(prep_ms)) / args.steps,
                                "render": float(np.sum(render_ms)) / args.steps},
     }
+    if not args.no_table:
+        line["table"] = table_leg(awg, stream)
     if not args.no_stream:
         line["stream"] = {f"{int(fs_/1e6)}MSps": stream_leg(awg, fs_, stream) for fs_ in (280e6, 50e6)}
     if not args.no_cpu_baseline and world == 1:

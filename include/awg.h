@@ -201,6 +201,23 @@ int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream);
 int awg_device_status(awg_t* h);
 
 /* ------------------------------------------------------------------------------------------
+ * Periodic table on tensor cores.
+ * ---------------------------------------------------------------------------------------- */
+enum { AWG_PREC_BF16 = 0, AWG_PREC_FP16 = 1 };
+
+/* The whole periodic record x[0 .. 2^log2_len) of the handle's tones as a split-precision GEMM:
+ * with n = n1 * 256 + n2, x = sum_k [A_k sin a_k(n1)] cos b_k(n2) + [A_k cos a_k(n1)] sin b_k(n2)
+ * (the angle-addition form of Eq. main), a_k, b_k from exact phase words; operands split into
+ * hi + lo halves of the chosen precision, products hi*hi + hi*lo + lo*hi accumulated in FP32 on
+ * tcgen05 tensor cores.  Requires every tone on the f_s / 2^log2_len grid (awg_set_tones_grid,
+ * Eq. freqapprox) and no chirps; 15 <= log2_len <= 30.  Writes int16 codes (full scale of the
+ * handle) to out_q and/or the FP32 sum to out_f (either may be NULL, not both), sample n at
+ * index n, asynchronously on `stream`.  The cursor is not used or moved.  Operand buffers
+ * (2 x 2^(log2_len-8) x 2K 16-bit values, 5.2 GB for 10,000 tones and 2^24 samples) are kept by
+ * the handle between calls. */
+int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q, float* out_f, void* stream);
+
+/* ------------------------------------------------------------------------------------------
  * Streaming ring (the Streaming pathway, Sec. IV-B, with the DAC card replaced by a host sink).
  * n_slots chunk slots of int16 samples live in pinned, device-mapped host memory; awg_ring_push
  * renders the handle's next chunk straight into the next slot; a sink thread plays chunk c at

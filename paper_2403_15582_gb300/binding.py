@@ -10,6 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libawg.so")
 
 AWG_OK, AWG_EINVAL, AWG_ENOMEM, AWG_ECUDA, AWG_ETIMEOUT, AWG_EDEADLINE, AWG_ESTATE = 0, -1, -2, -3, -4, -5, -6
+PREC_BF16, PREC_FP16 = 0, 1
 PROFILE_LINEAR, PROFILE_MINJERK = 0, 1
 
 # (name, restype, argtypes) of every symbol declared in include/awg.h
@@ -30,6 +31,7 @@ SIGNATURES = [
     ("awg_set_full_scale", ctypes.c_int, [P, dbl]),
     ("awg_full_scale", dbl, [P]),
     ("awg_sample_rate", dbl, [P]),
+    ("awg_table_gemm", ctypes.c_int, [P, i32, i32, P, P, P]),
     ("awg_ring_create", P, [P, i64, i32]),
     ("awg_ring_destroy", None, [P]),
     ("awg_ring_push", ctypes.c_int, [P, P, i32]),
@@ -211,6 +213,9 @@ class Synth:
 
     def render(self, n: int, out, stream=None):
         _check(lib().awg_render(self._h, int(n), _ptr(out), _stream_ptr(stream)))
+
+    def table_gemm(self, log2_len: int, precision: int, out_q=None, out_f=None, stream=None):
+        _check(lib().awg_table_gemm(self._h, int(log2_len), int(precision), _ptr(out_q), _ptr(out_f), _stream_ptr(stream)))
 
     def render_noalloc(self, n: int, out, stream=None):
         _check(lib().awg_render_noalloc(self._h, int(n), _ptr(out), _stream_ptr(stream)))

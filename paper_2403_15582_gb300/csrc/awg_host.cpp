@@ -315,6 +315,8 @@ struct awg {
   size_t cap_trace = 0;
   uint32_t* d_tab = nullptr;           // exact per-sample phases of TONE_EXACT chirps
   size_t cap_tab = 0;
+  uint16_t* d_gemm = nullptr;          // table GEMM operands: A hi, A lo, B hi, B lo
+  size_t cap_gemm = 0;
   int64_t cursor = 0;
   double full_scale = 0;
   bool fs_explicit = false;
@@ -688,6 +690,7 @@ void awg_destroy(awg_t* h) {
   cudaFree(h->d_words);
   cudaFree(h->d_trace);
   cudaFree(h->d_tab);
+  cudaFree(h->d_gemm);
   for (cudaEvent_t ev : h->prof_ev) cudaEventDestroy(ev);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
@@ -918,6 +921,65 @@ float awg_last_render_ms(awg_t* h) {
   float ms = -1.f;
   if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) != cudaSuccess) return -1.f;
   return ms;
+}
+
+int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q, float* out_f, void* stream) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (log2_len < 15 || log2_len > 30) return fail(AWG_EINVAL, "log2_len must be 15..30");
+  if (precision != AWG_PREC_BF16 && precision != AWG_PREC_FP16) return fail(AWG_EINVAL, "unknown precision");
+  if (!out_q && !out_f) return fail(AWG_EINVAL, "no output buffer");
+  const uint64_t grid_mask = (log2_len >= 64) ? 0 : ((1ull << (64 - log2_len)) - 1);
+  for (const ToneRec& t : h->tones) {
+    if (t.slot >= 0) return fail(AWG_EINVAL, "table GEMM needs static tones (a tone holds a chirp)");
+    if (t.F & grid_mask) return fail(AWG_EINVAL, "table GEMM needs every tone on the f_s / 2^log2_len grid");
+  }
+  const int64_t M = (int64_t)1 << (log2_len - 8);
+  const size_t Kp = awgk::table_kp(std::max(h->K, 1));
+  const size_t a_elems = (size_t)M * Kp, b_elems = (size_t)256 * Kp;
+  int st = ensure(&h->d_gemm, &h->cap_gemm, 2 * a_elems + 2 * b_elems, h, "table GEMM operands");
+  if (st) return st;
+  awgk::TableArgs2 t;
+  t.tones = h->d_tones;
+  t.K = h->K;
+  t.M = M;
+  t.nb_log2 = 8;
+  t.precision = precision;
+  t.a_hi = h->d_gemm;
+  t.a_lo = h->d_gemm + a_elems;
+  t.b_hi = h->d_gemm + 2 * a_elems;
+  t.b_lo = h->d_gemm + 2 * a_elems + b_elems;
+  t.out_q = out_q;
+  t.out_f = out_f;
+  t.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
+  t.status = h->d_status;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  if (h->profiling) {   // operand preparation and GEMM timed like a render's set-up and render
+    while (e == cudaSuccess && h->prof_ev.size() < 4 * (h->prof_calls + 1)) {
+      cudaEvent_t ev;
+      e = cudaEventCreate(&ev);
+      if (e == cudaSuccess) h->prof_ev.push_back(ev);
+    }
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) pe[i] = h->prof_ev[4 * h->prof_calls + (size_t)i];
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev0, s);
+  if (e == cudaSuccess && pe[0]) e = cudaEventRecord(pe[0], s);
+  if (e == cudaSuccess) e = awgk::launch_table_prep(t, s);
+  if (e == cudaSuccess && pe[1]) e = cudaEventRecord(pe[1], s);
+  if (e == cudaSuccess && pe[2]) e = cudaEventRecord(pe[2], s);
+  if (e == cudaSuccess) e = awgk::launch_table_gemm(t, s);
+  if (e == cudaSuccess && pe[3]) e = cudaEventRecord(pe[3], s);
+  if (e == cudaSuccess && pe[3]) {
+    ++h->prof_calls;
+    h->prof_launches += 3;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev1, s);
+  if (e == cudaSuccess) e = cudaEventRecord(h->ev_done, s);
+  if (e != cudaSuccess) return cuda_fail(e, "table GEMM");
+  h->timed = true;
+  h->have_done = true;
+  return AWG_OK;
 }
 
 int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream) {

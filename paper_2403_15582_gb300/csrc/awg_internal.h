@@ -136,6 +136,26 @@ constexpr size_t NOALLOC_MAX_RECORDS = (12u << 20) / sizeof(TileRec);   // 71493
 constexpr int32_t NOALLOC_MAX_SLOTS = 16384;
 cudaError_t noalloc_scratch(int device, TileRec** recs, int32_t** act);
 
+// Periodic-table GEMM (awg_table.cu).
+struct TableArgs2 {
+  const ToneRec* tones;
+  int32_t K;
+  int64_t M;              // rows: record length / 256
+  int32_t nb_log2;        // log2 of the columns (8: 256 samples per row)
+  int32_t precision;      // 0 BF16, 1 FP16 hi+lo operands
+  void* a_hi;             // M x Kp
+  void* a_lo;
+  void* b_hi;             // 256 x Kp
+  void* b_lo;
+  int16_t* out_q;
+  float* out_f;
+  float scale;
+  int32_t* status;
+};
+size_t table_kp(int K);  // padded inner dimension (2K rounded up to the K tile)
+cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s);   // operand halves
+cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s);   // tensor-core GEMM + epilogue
+
 // Sets the message awg_last_error() returns on this thread; returns `code`.
 int set_error(int code, const std::string& msg);
 

@@ -1,0 +1,425 @@
+// Periodic multi-tone table as a split-precision tensor-core GEMM (tcgen05, sm_103a).
+//
+// For tones on the f_s / 2^log2_len grid (Eq. freqapprox) the record of N = 2^log2_len samples is
+// periodic.  With n = n1 * NB + n2 (NB = 256) and the angle-addition identity,
+//   x[n] = sum_k A_k sin(a_k(n1) + b_k(n2))
+//        = sum_k [A_k sin a_k(n1)] cos b_k(n2) + [A_k cos a_k(n1)] sin b_k(n2),
+// a_k(n1) = 2 pi (Phi0_k + n1 NB F_k) / 2^64 and b_k(n2) = 2 pi n2 F_k / 2^64 from exact 64-bit
+// phase words.  That is a GEMM X[M = N/NB, NB] = Aop[M, 2K] * Bop[2K, NB].  Each operand is split
+// into hi + lo in BF16 (or FP16); the kernel accumulates hi*hi + hi*lo + lo*hi in FP32 in tensor
+// memory and quantises in the epilogue.
+//
+// Kernel structure: a cluster of S CTAs per 128-row tile of X splits the K dimension (fewer FP32
+// accumulations per chain); each CTA (192 threads) has
+//   warp 0   TMA producer: 2-stage ring of {A_hi, A_lo (128 x 64), B_hi, B_lo (256 x 64)} tiles,
+//            128-byte swizzle, mbarrier transaction counts
+//   warp 1   allocates 256 TMEM columns; lane 0 issues tcgen05.mma (M 128, N 256, K 16) x 3 passes
+//            x 4 k-steps per stage, commits each stage back to the producer
+//   warps 2-5 epilogue: tcgen05.ld 32x32b of both accumulators into a padded FP32 partial tile in
+//            shared memory; then the cluster sums the S partial tiles through distributed shared
+//            memory in rank order, and each CTA scales, rounds, clamps and stores its rows.
+// Every wait is bounded (about 2 s); on a timeout the CTA records AWG_ETIMEOUT, lets in-flight
+// copies and MMAs drain (bounded), frees its TMEM and exits.
+#include <cooperative_groups.h>
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "awg_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace awgk {
+
+namespace {
+
+constexpr int TM = 128;               // rows of X per CTA (UMMA M)
+constexpr int TN = 256;               // NB: columns of X (UMMA N)
+constexpr int TK = 64;                // K elements per stage (128 bytes of 16-bit values)
+constexpr int NSTAGE = 2;
+constexpr uint32_t A_TILE = TM * TK * 2;   // 16 KB
+constexpr uint32_t B_TILE = TN * TK * 2;   // 32 KB
+constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // 96 KB
+constexpr int STATUS_TIMEOUT = -4;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  while (!mbar_try(bar, parity))
+    if (now_ns() - t0 > 2000000000ull) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile with 128-byte rows, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;                 // version
+  d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+constexpr int PART_STRIDE = TN + 1;   // padded row of a partial tile (conflict-free column writes)
+
+struct TableGemmArgs {
+  int32_t n_kb;          // K blocks of TK (all CTAs of a cluster together)
+  int16_t* out_q;
+  float* out_f;
+  float scale;           // 32767 / FS
+  int32_t* status;
+  uint32_t idesc;
+};
+
+__global__ void __launch_bounds__(192, 1)
+    table_gemm_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
+                      const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+                      const __grid_constant__ TableGemmArgs a) {
+  extern __shared__ uint8_t dyn_smem[];
+  __shared__ alignas(8) uint64_t bars[2 * NSTAGE + 1];   // full[2], empty[2], done
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_fail;
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int split = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t base = (smem_u32(dyn_smem) + 1023u) & ~1023u;   // 1024-byte aligned stages
+  float* part = reinterpret_cast<float*>(dyn_smem + (base - smem_u32(dyn_smem)));   // reuses the stages
+  const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[NSTAGE]), done = smem_u32(&bars[2 * NSTAGE]);
+  const int row0 = (blockIdx.x / split) * TM;
+  const int kb0 = (int)((int64_t)a.n_kb * crank / split), kb1 = (int)((int64_t)a.n_kb * (crank + 1) / split);
+  const int n_kb = kb1 - kb0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {   // whole warp: 512 TMEM columns, two 128 x 256 FP32 accumulators
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)), "r"(2 * TN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int issued = 0;
+    for (int kb = 0; kb < n_kb; ++kb) {
+      const int s = kb % NSTAGE;
+      if (kb >= NSTAGE && !mbar_wait(empty0 + 8 * s, (uint32_t)(((kb / NSTAGE) - 1) & 1))) {
+        s_fail = 1;
+        break;
+      }
+      if (s_fail) break;
+      const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
+      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+      const int kx = (kb0 + kb) * TK;
+      tma_load_2d(st, &mA_hi, kx, row0, full0 + 8 * s);
+      tma_load_2d(st + A_TILE, &mA_lo, kx, row0, full0 + 8 * s);
+      tma_load_2d(st + 2 * A_TILE, &mB_hi, kx, 0, full0 + 8 * s);
+      tma_load_2d(st + 2 * A_TILE + B_TILE, &mB_lo, kx, 0, full0 + 8 * s);
+      issued = kb + 1;
+    }
+    if (s_fail) {   // let the copies already issued land (bounded) before the CTA exits
+      for (int kb = (issued > NSTAGE ? issued - NSTAGE : 0); kb < issued; ++kb)
+        (void)mbar_wait(full0 + 8 * (kb % NSTAGE), (uint32_t)((kb / NSTAGE) & 1));
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    bool ok = true;
+    for (int kb = 0; kb < n_kb && ok; ++kb) {
+      const int s = kb % NSTAGE;
+      if (!mbar_wait(full0 + 8 * s, (uint32_t)((kb / NSTAGE) & 1)) || s_fail) {
+        ok = false;
+        s_fail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
+      const uint32_t a_hi = st, a_lo = st + A_TILE, b_hi = st + 2 * A_TILE, b_lo = st + 2 * A_TILE + B_TILE;
+#pragma unroll
+      for (int j = 0; j < TK / 16; ++j) {   // K = 16 per instruction: +32 bytes inside the swizzle atom
+        const uint32_t off = 32u * (uint32_t)j;
+        const uint32_t first = (kb == 0 && j == 0) ? 0u : 1u;
+        // the large products and the small corrections accumulate separately, so the large
+        // accumulator takes one rounding per k-step instead of three
+        mma_f16(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), a.idesc, first);
+        mma_f16(tmem + TN, sw128_desc(a_hi + off), sw128_desc(b_lo + off), a.idesc, first);
+        mma_f16(tmem + TN, sw128_desc(a_lo + off), sw128_desc(b_hi + off), a.idesc, 1u);
+      }
+      mma_commit(empty0 + 8 * s);   // stage free once these MMAs have read it
+    }
+    mma_commit(done);               // all MMAs issued so far complete -> epilogue (also on abort)
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const bool ok = mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int lane_base = 32 * (warp % 4);          // TMEM lanes this warp may read
+    const int row = lane_base + lane;                // row of the tile = TMEM lane
+    const bool go = __all_sync(0xffffffffu, ok && !s_fail);   // warp-uniform: tcgen05.ld is .aligned
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // stage memory becomes the partial tile
+    if (go) {
+#pragma unroll 1
+      for (int c0 = 0; c0 < TN; c0 += 32) {
+        uint32_t v[32], w[32];
+        const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]), "=r"(w[7]),
+              "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]), "=r"(w[13]), "=r"(w[14]), "=r"(w[15]),
+              "=r"(w[16]), "=r"(w[17]), "=r"(w[18]), "=r"(w[19]), "=r"(w[20]), "=r"(w[21]), "=r"(w[22]), "=r"(w[23]),
+              "=r"(w[24]), "=r"(w[25]), "=r"(w[26]), "=r"(w[27]), "=r"(w[28]), "=r"(w[29]), "=r"(w[30]), "=r"(w[31])
+            : "r"(taddr + (uint32_t)TN));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = __float_as_uint(__uint_as_float(v[i]) + __uint_as_float(w[i]));
+#pragma unroll
+        for (int i = 0; i < 32; ++i) part[row * PART_STRIDE + c0 + i] = __uint_as_float(v[i]);
+      }
+    }
+    if (!ok) s_fail = 1;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && s_fail) atomicExch(a.status, STATUS_TIMEOUT);
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TN) : "memory");
+  }
+  cluster.sync();   // every partial tile of the cluster is in shared memory
+
+  // this CTA sums rows [r_lo, r_hi) of the S partial tiles in rank order, then quantises and stores
+  const int r_lo = TM * crank / split, r_hi = TM * (crank + 1) / split;
+  const int n_el = (r_hi - r_lo) * TN;
+  for (int e = threadIdx.x; e < n_el; e += blockDim.x) {
+    const int row = r_lo + e / TN, col = e % TN;
+    float x = 0.f;
+    for (int c = 0; c < split; ++c) x += cluster.map_shared_rank(part, c)[row * PART_STRIDE + col];
+    const int64_t n = (int64_t)(row0 + row) * TN + col;
+    if (a.out_q) a.out_q[n] = (int16_t)fminf(fmaxf(rintf(x * a.scale), -32767.f), 32767.f);
+    if (a.out_f) a.out_f[n] = x;
+  }
+  cluster.sync();   // remote reads done before any CTA of the cluster exits
+}
+
+// ---------------------------------------------------------------------------------------------
+// operand preparation
+// ---------------------------------------------------------------------------------------------
+// sin and cos of 2 pi w / 2^64 for a 64-bit phase word, accurate to a few 1e-8: sincospi of the
+// word's top bits (exactly representable), corrected to first order by the remaining bits.
+__device__ __forceinline__ void sincos_word(uint64_t w, float* s, float* c) {
+  const int32_t hi = (int32_t)(w >> 32);                 // half-turns x 2^31
+  const int32_t h1 = hi & ~0xFF;                         // <= 23 significant bits: exact in float
+  const float x1 = (float)h1 * 4.656612873077392578125e-10f;   // 2^-31
+  const float x2 = ((float)(hi - h1) + (float)(uint32_t)w * 2.3283064365386963e-10f) * 4.656612873077392578125e-10f;
+  float s1, c1;
+  sincospif(x1, &s1, &c1);
+  const float d = 3.14159265358979323846f * x2;
+  *s = fmaf(c1, d, s1);
+  *c = fmaf(-s1, d, c1);
+}
+
+template <typename T>
+__device__ __forceinline__ T to_half(float v);
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_half<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_half<__half>(float v) { return __float2half_rn(v); }
+template <typename T>
+__device__ __forceinline__ float from_half(T v);
+template <>
+__device__ __forceinline__ float from_half<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <>
+__device__ __forceinline__ float from_half<__half>(__half v) { return __half2float(v); }
+
+template <typename T>
+__device__ __forceinline__ void split_store(T* hi, T* lo, int64_t i, float v) {
+  const T h = to_half<T>(v);
+  hi[i] = h;
+  lo[i] = to_half<T>(v - from_half<T>(h));
+}
+
+// Aop[n1][2k] = A_k sin a_k(n1), Aop[n1][2k+1] = A_k cos a_k(n1); zero beyond 2K.
+template <typename T>
+__global__ void prep_a_kernel(const ToneRec* tones, int K, int64_t M, int64_t Kp, int NBlog2, T* hi, T* lo) {
+  const int64_t pairs = Kp / 2;
+  const int64_t total = M * pairs;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n1 = i / pairs, k = i - n1 * pairs;
+    float s = 0.f, c = 0.f, A = 0.f;
+    if (k < K) {
+      const ToneRec& t = tones[k];
+      const uint64_t w = t.phi_ref + (((uint64_t)n1 << NBlog2) * t.F);
+      sincos_word(w, &s, &c);
+      A = t.A;
+    }
+    split_store<T>(hi, lo, n1 * Kp + 2 * k, A * s);
+    split_store<T>(hi, lo, n1 * Kp + 2 * k + 1, A * c);
+  }
+}
+
+// Bt[n2][2k] = cos b_k(n2), Bt[n2][2k+1] = sin b_k(n2) (the B operand stored K-major).
+template <typename T>
+__global__ void prep_b_kernel(const ToneRec* tones, int K, int64_t Kp, T* hi, T* lo) {
+  const int64_t pairs = Kp / 2;
+  const int64_t total = (int64_t)TN * pairs;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n2 = i / pairs, k = i - n2 * pairs;
+    float s = 0.f, c = 0.f;
+    if (k < K) sincos_word((uint64_t)n2 * tones[k].F, &s, &c);
+    split_store<T>(hi, lo, n2 * Kp + 2 * k, c);
+    split_store<T>(hi, lo, n2 * Kp + 2 * k + 1, s);
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+cudaError_t encode_2d(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt, void* base, uint64_t inner,
+                      uint64_t outer, uint32_t box_inner, uint32_t box_outer) {
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {inner * 2};
+  const cuuint32_t box[2] = {box_inner, box_outer};
+  const cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+size_t table_kp(int K) { return (((size_t)2 * K + TK - 1) / TK) * TK; }
+
+cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s) {
+  const int64_t M = t.M;
+  const int64_t Kp = (int64_t)table_kp(t.K);
+  const bool bf16 = (t.precision == 0);
+  const int threads = 256;
+  const int blocks = 152 * 8;
+  if (bf16) {
+    prep_a_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(t.tones, t.K, M, Kp, t.nb_log2, (__nv_bfloat16*)t.a_hi,
+                                                           (__nv_bfloat16*)t.a_lo);
+    prep_b_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(t.tones, t.K, Kp, (__nv_bfloat16*)t.b_hi, (__nv_bfloat16*)t.b_lo);
+  } else {
+    prep_a_kernel<__half><<<blocks, threads, 0, s>>>(t.tones, t.K, M, Kp, t.nb_log2, (__half*)t.a_hi, (__half*)t.a_lo);
+    prep_b_kernel<__half><<<blocks, threads, 0, s>>>(t.tones, t.K, Kp, (__half*)t.b_hi, (__half*)t.b_lo);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
+  const int64_t M = t.M;
+  const int64_t Kp = (int64_t)table_kp(t.K);
+  const bool bf16 = (t.precision == 0);
+  cudaError_t e;
+  static EncodeTiledFn enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    enc = (EncodeTiledFn)fn;
+  }
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  if ((e = encode_2d(enc, &mAh, dt, t.a_hi, (uint64_t)Kp, (uint64_t)M, TK, TM)) != cudaSuccess) return e;
+  if ((e = encode_2d(enc, &mAl, dt, t.a_lo, (uint64_t)Kp, (uint64_t)M, TK, TM)) != cudaSuccess) return e;
+  if ((e = encode_2d(enc, &mBh, dt, t.b_hi, (uint64_t)Kp, (uint64_t)TN, TK, TN)) != cudaSuccess) return e;
+  if ((e = encode_2d(enc, &mBl, dt, t.b_lo, (uint64_t)Kp, (uint64_t)TN, TK, TN)) != cudaSuccess) return e;
+
+  TableGemmArgs ga;
+  ga.n_kb = (int32_t)(Kp / TK);
+  ga.out_q = t.out_q;
+  ga.out_f = t.out_f;
+  ga.scale = t.scale;
+  ga.status = t.status;
+  // instruction descriptor: FP32 accumulate, A/B BF16 (1) or FP16 (0), both K-major, N/8, M/16
+  const uint32_t fmt = bf16 ? 1u : 0u;
+  ga.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+  const size_t smem = (size_t)NSTAGE * STAGE_BYTES + 1024;
+  static_assert((size_t)TM * PART_STRIDE * 4 <= (size_t)NSTAGE * STAGE_BYTES, "partial tile fits in the stages");
+  e = cudaFuncSetAttribute(table_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  // K split over a cluster of up to 4 CTAs per 128-row tile
+  const unsigned split = (unsigned)(ga.n_kb < 4 ? ga.n_kb : 4);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(M / TM) * split, 1, 1);
+  cfg.blockDim = dim3(192, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = split;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, table_gemm_kernel, mAh, mAl, mBh, mBl, ga);
+}
+
+}  // namespace awgk
