@@ -173,6 +173,7 @@ def stream_leg(awg, fs: float, stream, seconds: float = 1.0, n_slots: int = 4, p
     synth.close()
     return {"tones": wk.K, "fs_hz": fs, "chunk": wk.chunk, "chunks": int(st["played"]), "underruns": int(st["underruns"]),
             "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"]},
+            "first_chunk_ms": {"p50": st["first_chunk_p50_ms"], "p99": st["first_chunk_p99_ms"]},
             "min_lead_ms": st["lead_min_ms"], "playback_ms": st["chunk_playback_ms"], "slots": n_slots,
             "required_tone_samples_per_s": wk.K * fs}
 
@@ -227,6 +228,41 @@ def table_leg(awg, stream, reps: int = 3):
     return out
 
 
+def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, capacity: float = 2.5e12):
+    """Served rearrangement stream: Poisson arrivals of requests (50-10,000 tones, up to 100 chirping
+    over 0.1-2 ms, 8 chunks of 2^16-2^20 samples) at rho x capacity / mean request work, submitted in
+    real time; admission by memory and deadline; continuous batching."""
+    import math
+    from paper_2403_15582_gb300 import workloads as wl
+    mean_K = (10000 - 50) / math.log(10000 / 50)
+    mean_chunk = sum(1 << e for e in range(16, 21)) / 5
+    rate = rho * capacity / (mean_K * mean_chunk * 8)
+    reqs = wl.served_requests(seed=0, rate_hz=rate, seconds=seconds, fs=fs)
+    srv = awg.Server(fs, 16 << 30, 256)
+    t0 = time.perf_counter()
+    ids = []
+    for r in reqs:
+        delay = r.arrival_s - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(srv.submit(r.freq_hz, r.amp, r.phase_rad, r.chunk, r.n_chunks, r.chirps))
+    srv.drain(120000)
+    st = srv.stats()
+    for rid in ids:
+        srv.release(rid)
+    srv.close()
+    return {"fs_hz": fs, "rho": rho, "assumed_capacity": capacity, "arrival_rate_hz": rate, "seconds": seconds,
+            "requests": st["submitted"], "admitted": st["admitted"], "rejected_deadline": st["rejected_deadline"],
+            "rejected_memory": st["rejected_memory"], "completed": st["completed"], "chunks": st["chunks"],
+            "deadline_misses": st["deadline_misses"],
+            "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"]},
+            "first_chunk_ms": {"p50": st["first_chunk_p50_ms"], "p99": st["first_chunk_p99_ms"]},
+            "samples_per_s": st["samples_per_s"], "tone_samples_per_s": st["tone_samples_per_s"],
+            "mean_batch": st["mean_batch"], "max_batch": st["max_batch"], "rounds": st["rounds"], "busy_fraction": st["busy_fraction"],
+            "est_throughput": st["est_throughput"],
+            "est_round_cost_ms": st["est_round_cost_ms"]}
+
+
 def config(wk, args):
     return {"workload": "chirp-1000tone-35ms-280MSps", "tones": wk.K, "samples": wk.n_samples, "chunk": wk.chunk,
             "fs_hz": wk.fs, "profiles": "linear (even tones) / minimum-jerk (odd tones)",
@@ -243,6 +279,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-table", action="store_true")
+    ap.add_argument("--no-served", action="store_true")
     args = ap.parse_args()
     wk = workload()
     if args.impl == "reference":
@@ -368,6 +405,8 @@ def main():
     }
     if not args.no_table:
         line["table"] = table_leg(awg, stream)
+    if not args.no_served:
+        line["served"] = {f"rho{r}": served_leg(awg, rho=r) for r in (0.5, 0.8)}
     if not args.no_stream:
         line["stream"] = {f"{int(fs_/1e6)}MSps": stream_leg(awg, fs_, stream) for fs_ in (280e6, 50e6)}
     if not args.no_cpu_baseline and world == 1:

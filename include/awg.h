@@ -262,6 +262,116 @@ int awg_ring_finish(awg_ring_t* r, int32_t timeout_ms, awg_ring_stats_t* out);
 /* Host pointer to the samples of slot i (NULL if out of range). */
 const int16_t* awg_ring_slot(const awg_ring_t* r, int32_t i);
 
+/* ------------------------------------------------------------------------------------------
+ * Served request stream with continuous batching.  A request is a waveform (a comb of tones, some
+ * of them chirped, as in the rearrangement of Sec. V-B) that asks for n_chunks consecutive chunks
+ * of `chunk` samples, played back at fs one after another (the chunked streaming of Sec. IV).
+ * Timing: chunk 0 is rendered as soon as the request is set up on the device; playback starts
+ * when it is complete (t_play; its latency from submission is reported as the first-chunk time).
+ * Chunk c >= 1 is released when chunk c-1 starts playing, t_play + (c-1) chunk/fs, and is due when
+ * chunk c-1 ends, t_play + c chunk/fs; a chunk completed after that is a deadline miss (an
+ * underrun of the player).
+ * Admission: a request is admitted while the device-memory budget and max_active allow and the
+ * real-time budget holds with it: rounds last about a quarter of the shortest chunk period of the
+ * active set, and the set's load fs * sum K must stay below 85 % of the tone-sample rate that
+ * rounds of that length leave after their fixed costs (a cost model fitted to the measured
+ * rounds).  A request that does not fit waits up to max_queue_ms (without blocking the requests
+ * behind it) and is then rejected; one that could never fit is rejected at once.
+ * Rounds: the scheduler keeps two rounds in flight; each round takes the released chunks of all
+ * active requests in earliest-deadline-first order, cuts the ones that do not fit the round's work
+ * budget into whole 4096-sample tiles, and renders them in one batched grid per tone-split size.
+ * A request's samples are the same as a standalone render of it (awg_render), whatever runs
+ * beside it and however its chunks are cut.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct awg_server awg_server_t;
+
+enum { AWG_REQ_QUEUED = 0, AWG_REQ_ACTIVE = 1, AWG_REQ_DONE = 2, AWG_REQ_REJECTED = 3 };
+
+typedef struct {
+  const double* freq_hz;            /* n_tones: as awg_set_tones */
+  const double* amp;
+  const double* phase_rad;
+  int32_t n_tones;
+  const int32_t* chirp_tone;        /* n_chirps: as awg_set_chirps (start samples relative to the
+                                       request's first sample) */
+  const double* chirp_f_start_hz;
+  const double* chirp_f_end_hz;
+  const double* chirp_duration_s;
+  const int32_t* chirp_profile;
+  const int64_t* chirp_start_sample;
+  int32_t n_chirps;
+  int64_t chunk;                    /* samples per chunk, 1 .. 2^26 */
+  int32_t n_chunks;
+  double full_scale;                /* <= 0: sum |A| */
+} awg_request_t;
+
+typedef struct {
+  int64_t submitted, admitted, rejected_deadline, rejected_memory, completed;
+  int64_t chunks, deadline_misses;  /* chunks rendered; of those, completed after their deadline */
+  double latency_p50_ms;            /* chunks c >= 1: completion minus release */
+  double latency_p99_ms;
+  double latency_max_ms;
+  double first_chunk_p50_ms;        /* chunk 0: completion minus submission (queue + set-up + render) */
+  double first_chunk_p99_ms;
+  int64_t rounds;
+  double mean_batch;                /* pieces (requests) per round */
+  int64_t max_batch;
+  double tone_samples_per_s;        /* over the span from the first round to the last */
+  double samples_per_s;
+  double busy_fraction;             /* device time of the rounds / that span */
+  double est_throughput;            /* cost model: static-tone samples/s of a busy device */
+  double est_round_cost_ms;         /* cost model: fixed device time of one round */
+} awg_server_stats_t;
+
+/* Server for sample rate fs on the current device, with a device-memory budget (bytes) for the
+ * requests' state and outputs, at most max_active concurrent requests, and at most max_queue_ms
+ * of waiting for admission.  NULL on error (see awg_last_error). */
+awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes, int32_t max_active,
+                                double max_queue_ms);
+
+/* Stop the scheduler, wait for in-flight work and free everything.  NULL is allowed. */
+void awg_server_destroy(awg_server_t* s);
+
+/* Queue a request (arrays are copied); returns its id (>= 0) or a negative AWG_E* code. */
+int64_t awg_server_submit(awg_server_t* s, const awg_request_t* req);
+
+/* State (AWG_REQ_*) and number of rendered chunks of request id. */
+int awg_server_poll(awg_server_t* s, int64_t id, int32_t* state, int32_t* chunks_done);
+
+/* Copy the first n_samples samples of a finished request to host memory (AWG_ESTATE if not done). */
+int awg_server_read(awg_server_t* s, int64_t id, int16_t* host_out, int64_t n_samples);
+
+/* Forget a finished or rejected request and free its output (done by the scheduler thread). */
+int awg_server_release(awg_server_t* s, int64_t id);
+
+/* Wait up to timeout_ms until no request is queued or active. */
+int awg_server_drain(awg_server_t* s, int32_t timeout_ms);
+
+/* Counters and latency percentiles so far. */
+int awg_server_stats(awg_server_t* s, awg_server_stats_t* out);
+
+/* Trace of the most recent rounds and chunk completions (the last 65,536 of each; times on the
+ * server clock, seconds since awg_server_create; device times mapped through an event recorded at
+ * creation).  Each call copies up to cap records, oldest first, and returns how many (or a
+ * negative AWG_E* code). */
+typedef struct {
+  double t_plan;                    /* host: planning started */
+  double t_issued;                  /* host: all launches of the round issued */
+  double t_start, t_done;           /* device: round start and end */
+  double work;                      /* tone-samples */
+  double first_due;                 /* earliest due time among the round's chunks (c >= 1) */
+  int32_t pieces, tiles;
+} awg_round_record_t;
+
+typedef struct {
+  int64_t id;                       /* request */
+  int32_t chunk, late;              /* late: completed after its due time */
+  double release, due, done;        /* chunk 0: release = set-up done, due = release + period */
+} awg_chunk_record_t;
+
+int32_t awg_server_trace_rounds(awg_server_t* s, awg_round_record_t* out, int32_t cap);
+int32_t awg_server_trace_chunks(awg_server_t* s, awg_chunk_record_t* out, int32_t cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -32,6 +32,16 @@ SIGNATURES = [
     ("awg_full_scale", dbl, [P]),
     ("awg_sample_rate", dbl, [P]),
     ("awg_table_gemm", ctypes.c_int, [P, i32, i32, P, P, P]),
+    ("awg_server_create", P, [dbl, i64, i32, dbl]),
+    ("awg_server_destroy", None, [P]),
+    ("awg_server_submit", i64, [P, P]),
+    ("awg_server_poll", ctypes.c_int, [P, i64, P, P]),
+    ("awg_server_read", ctypes.c_int, [P, i64, P, i64]),
+    ("awg_server_release", ctypes.c_int, [P, i64]),
+    ("awg_server_drain", ctypes.c_int, [P, i32]),
+    ("awg_server_stats", ctypes.c_int, [P, P]),
+    ("awg_server_trace_rounds", i32, [P, P, i32]),
+    ("awg_server_trace_chunks", i32, [P, P, i32]),
     ("awg_ring_create", P, [P, i64, i32]),
     ("awg_ring_destroy", None, [P]),
     ("awg_ring_push", ctypes.c_int, [P, P, i32]),
@@ -306,3 +316,106 @@ class Ring:
         if not ptr:
             raise AwgError(AWG_EINVAL, "slot index out of range")
         return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_int16)), shape=(self.chunk,)).copy()
+
+
+REQ_QUEUED, REQ_ACTIVE, REQ_DONE, REQ_REJECTED = 0, 1, 2, 3
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("freq_hz", P), ("amp", P), ("phase_rad", P), ("n_tones", i32), ("chirp_tone", P),
+                ("chirp_f_start_hz", P), ("chirp_f_end_hz", P), ("chirp_duration_s", P), ("chirp_profile", P),
+                ("chirp_start_sample", P), ("n_chirps", i32), ("chunk", i64), ("n_chunks", i32), ("full_scale", dbl)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", i64), ("admitted", i64), ("rejected_deadline", i64), ("rejected_memory", i64),
+                ("completed", i64), ("chunks", i64), ("deadline_misses", i64), ("latency_p50_ms", dbl),
+                ("latency_p99_ms", dbl), ("latency_max_ms", dbl), ("first_chunk_p50_ms", dbl),
+                ("first_chunk_p99_ms", dbl), ("rounds", i64), ("mean_batch", dbl), ("max_batch", i64),
+                ("tone_samples_per_s", dbl), ("samples_per_s", dbl), ("busy_fraction", dbl), ("est_throughput", dbl),
+                ("est_round_cost_ms", dbl)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Server:
+    """Served request stream (continuous batching) on the current device."""
+
+    def __init__(self, sample_rate: float, mem_budget_bytes: int = 8 << 30, max_active: int = 64,
+                 max_queue_ms: float = 5.0):
+        h = lib().awg_server_create(float(sample_rate), int(mem_budget_bytes), int(max_active), float(max_queue_ms))
+        if not h:
+            raise AwgError(AWG_EINVAL, lib().awg_last_error().decode())
+        self._s = ctypes.c_void_p(h)
+        self.fs = float(sample_rate)
+
+    def close(self):
+        if getattr(self, "_s", None):
+            lib().awg_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, freq_hz, amp, phase_rad, chunk: int, n_chunks: int, chirps=(), full_scale: float = 0.0) -> int:
+        f, a, th = _f64(freq_hz), _f64(amp), _f64(phase_rad)
+        ch = list(chirps)
+        ct = np.ascontiguousarray([c["tone"] for c in ch], dtype=np.int32)
+        c0 = _f64([c["f_start"] for c in ch])
+        c1 = _f64([c["f_end"] for c in ch])
+        cd = _f64([c["duration"] for c in ch])
+        cp = np.ascontiguousarray([c["profile"] for c in ch], dtype=np.int32)
+        cs = np.ascontiguousarray([c.get("start_sample", 0) for c in ch], dtype=np.int64)
+        q = _Request(_p(f).value, _p(a).value, _p(th).value, int(f.size), _p(ct).value, _p(c0).value, _p(c1).value,
+                     _p(cd).value, _p(cp).value, _p(cs).value, len(ch), int(chunk), int(n_chunks), float(full_scale))
+        rid = lib().awg_server_submit(self._s, ctypes.byref(q))
+        if rid < 0:
+            _check(int(rid))
+        return int(rid)
+
+    def poll(self, rid: int):
+        st = np.zeros(1, dtype=np.int32)
+        done = np.zeros(1, dtype=np.int32)
+        _check(lib().awg_server_poll(self._s, int(rid), _p(st), _p(done)))
+        return int(st[0]), int(done[0])
+
+    def read(self, rid: int, n_samples: int) -> np.ndarray:
+        out = np.zeros(n_samples, dtype=np.int16)
+        _check(lib().awg_server_read(self._s, int(rid), _p(out), int(n_samples)))
+        return out
+
+    def release(self, rid: int):
+        _check(lib().awg_server_release(self._s, int(rid)))
+
+    def drain(self, timeout_ms: int = 60000):
+        _check(lib().awg_server_drain(self._s, int(timeout_ms)))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().awg_server_stats(self._s, ctypes.byref(st)))
+        return st.as_dict()
+
+    ROUND_DTYPE = np.dtype([("t_plan", "f8"), ("t_issued", "f8"), ("t_start", "f8"), ("t_done", "f8"),
+                            ("work", "f8"), ("first_due", "f8"), ("pieces", "i4"), ("tiles", "i4")])
+    CHUNK_DTYPE = np.dtype([("id", "i8"), ("chunk", "i4"), ("late", "i4"), ("release", "f8"), ("due", "f8"),
+                            ("done", "f8")])
+
+    def trace_rounds(self, cap: int = 1 << 16) -> np.ndarray:
+        """The most recent rounds (structured array, ROUND_DTYPE)."""
+        out = np.zeros(cap, dtype=self.ROUND_DTYPE)
+        n = lib().awg_server_trace_rounds(self._s, out.ctypes.data, int(cap))
+        if n < 0:
+            _check(int(n))
+        return out[:n]
+
+    def trace_chunks(self, cap: int = 1 << 16) -> np.ndarray:
+        """The most recent chunk completions (structured array, CHUNK_DTYPE)."""
+        out = np.zeros(cap, dtype=self.CHUNK_DTYPE)
+        n = lib().awg_server_trace_chunks(self._s, out.ctypes.data, int(cap))
+        if n < 0:
+            _check(int(n))
+        return out[:n]

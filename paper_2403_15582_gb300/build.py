@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libawg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["awg_render.cu", "awg_table.cu", "awg_noalloc.cu", "awg_host.cpp", "awg_ring.cpp"]
+SOURCES = ["awg_render.cu", "awg_table.cu", "awg_noalloc.cu", "awg_host.cpp", "awg_ring.cpp", "awg_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -604,6 +604,79 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream)
 
 }  // namespace
 
+size_t awgk::render_recs_needed(const awg_t* h, int64_t n) {
+  if (!h || n <= 0) return 0;
+  const int64_t c = h->cursor;
+  const int64_t tile0 = c / awgk::TILE, tile_last = (c + n - 1) / awgk::TILE;
+  const int64_t span0 = tile0 * awgk::TILE, span1 = (tile_last + 1) * awgk::TILE - 1;
+  size_t active = 0;
+  for (const ChirpRec& cr : h->chirps)
+    if (cr.tone >= 0 && !(cr.flags & awgk::TONE_EXACT) && cr.n_s <= span1 && cr.n_s + cr.L >= span0) ++active;
+  return active * (size_t)(tile_last - tile0 + 1);
+}
+
+size_t awgk::render_slots(const awg_t* h) { return h ? h->chirps.size() : 0; }
+
+int awgk::prepare_render(awg_t* h, int64_t n, int16_t* out_q, float* out_f, cudaStream_t s, awgk::RenderArgs* ra,
+                         awgk::TileRec* recs, size_t recs_cap, int32_t* act, size_t* recs_need) {
+  if (!h || n <= 0 || (!out_q && !out_f) || !ra) return fail(AWG_EINVAL, "prepare_render: bad arguments");
+  const int64_t c = h->cursor;
+  const int64_t tile0 = c / awgk::TILE, tile_last = (c + n - 1) / awgk::TILE;
+  const int32_t n_tiles = (int32_t)(tile_last - tile0 + 1);
+  const int64_t span0 = tile0 * awgk::TILE, span1 = (tile_last + 1) * awgk::TILE - 1;
+  std::vector<int32_t> active;
+  for (size_t sl = 0; sl < h->chirps.size(); ++sl) {
+    const ChirpRec& cr = h->chirps[sl];
+    if (cr.tone < 0 || (cr.flags & awgk::TONE_EXACT)) continue;
+    if (cr.n_s <= span1 && cr.n_s + cr.L >= span0) active.push_back((int32_t)sl);
+  }
+  const size_t need = active.size() * (size_t)n_tiles;
+  if (recs_need) *recs_need = need;
+  if (recs || act) {
+    if (need > recs_cap || (!recs && need) || (!act && need)) return fail(AWG_ENOMEM, "prepare_render: arena too small");
+  } else {
+    int st = ensure(&h->d_recs, &h->cap_recs, std::max<size_t>(1, need), h, "tile records");
+    if (st) return st;
+    recs = h->d_recs;
+    act = h->d_act;
+  }
+  for (size_t b = 0; b < active.size(); b += awgk::MAX_ACTIVE_PER_LAUNCH) {
+    awgk::PrepArgs pa;
+    std::memset(&pa, 0, sizeof(pa));
+    pa.chirps = h->d_chirps;
+    pa.recs = recs;
+    pa.act_of_slot = act;
+    pa.tile0 = tile0;
+    pa.n_tiles = n_tiles;
+    pa.n_active = (int32_t)std::min<size_t>(awgk::MAX_ACTIVE_PER_LAUNCH, active.size() - b);
+    pa.act_base = (int32_t)b;
+    std::memcpy(pa.W, h->W, sizeof(pa.W));
+    std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
+    for (int i = 0; i < pa.n_active; ++i) pa.slots[i] = active[b + (size_t)i];
+    cudaError_t e = awgk::launch_prep(pa, s);
+    if (e != cudaSuccess) return cuda_fail(e, "prep launch");
+  }
+  std::memset(ra, 0, sizeof(*ra));
+  ra->tones = h->d_tones;
+  ra->exact_tab = h->d_tab;
+  ra->chirps = h->d_chirps;
+  ra->recs = recs;
+  ra->act_of_slot = act;
+  ra->K = h->K;
+  ra->split = h->split;
+  ra->tile0 = tile0;
+  ra->n_tiles = n_tiles;
+  ra->win_start = c;
+  ra->win_end = c + n;
+  ra->out_q = out_q;
+  ra->out_f = out_f;
+  ra->scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
+  ra->status = h->d_status;
+  std::memcpy(ra->inv_odd, h->inv_odd, sizeof(ra->inv_odd));
+  h->cursor = c + n;
+  return AWG_OK;
+}
+
 // ==========================================================================================
 // C ABI
 // ==========================================================================================

@@ -125,6 +125,8 @@ struct TableArgs {      // exact per-sample 32-bit phases of one short chirp, m 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_exact_table(const TableArgs& a, int64_t L, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
+// items[i] = (request index into reqs, window tile); every request has split == `split`.
+cudaError_t launch_render_batch(const RenderArgs* reqs, const int2* items, int n_items, int split, cudaStream_t s);
 cudaError_t launch_phase_words(const PhaseArgs& a, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, cudaStream_t s);
 cudaError_t render_setup_attributes();
@@ -155,6 +157,25 @@ struct TableArgs2 {
 size_t table_kp(int K);  // padded inner dimension (2K rounded up to the K tile)
 cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s);   // operand halves
 cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s);   // tensor-core GEMM + epilogue
+
+}  // namespace awgk
+
+struct awg;
+namespace awgk {
+// Everything awg_render does except the render launch: chirp tile set-up for the window
+// [cursor, cursor + n) on stream s, the render descriptor in *ra, and the cursor advance.  The
+// caller launches the render (e.g. batched with other handles') on the same stream.  The tile
+// records go to `recs` (recs_cap records) and the slot -> record map to `act` (render_slots(h)
+// entries) when they are given, so that windows of one handle can be in flight on several streams
+// at once; otherwise to the handle's own buffers.  *recs_need (if given) receives the number of
+// records the window needs; AWG_ENOMEM if recs_cap is short (the cursor is then unchanged).
+int prepare_render(struct awg* h, int64_t n, int16_t* out_q, float* out_f, cudaStream_t s, RenderArgs* ra,
+                   TileRec* recs = nullptr, size_t recs_cap = 0, int32_t* act = nullptr,
+                   size_t* recs_need = nullptr);
+// Tile records prepare_render needs for the window [cursor, cursor + n).
+size_t render_recs_needed(const struct awg* h, int64_t n);
+// Entries of the slot -> record map of h (its chirp slots).
+size_t render_slots(const struct awg* h);
 
 // Sets the message awg_last_error() returns on this thread; returns `code`.
 int set_error(int code, const std::string& msg);

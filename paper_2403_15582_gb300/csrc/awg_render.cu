@@ -464,7 +464,9 @@ struct alignas(16) Desc {
 };
 enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3 };
 
-__global__ void __launch_bounds__(NT, 5) render_kernel(const __grid_constant__ RenderArgs a) {
+// One CTA's share of one tile: tones [K crank / split, K (crank+1) / split) of window tile `tile`
+// of the render described by `a`, then the cluster-wide sum and the store of this CTA's slice.
+__device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile, const int crank, const int split) {
   __shared__ alignas(16) ToneRec s_tone[2][STAGE];
   __shared__ alignas(16) TileRec s_rec[2][STAGE];
   __shared__ alignas(16) Desc s_desc[2][STAGE];
@@ -473,9 +475,6 @@ __global__ void __launch_bounds__(NT, 5) render_kernel(const __grid_constant__ R
 
   cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x;
-  const int split = a.split;
-  const int crank = (int)cluster.block_rank();
-  const int tile = blockIdx.x / split;
   const int64_t T0 = (a.tile0 + tile) * (int64_t)TILE;
   const int64_t n0 = T0 + (int64_t)tid * RUN;
   const uint32_t run_off = (uint32_t)(tid * RUN);
@@ -667,6 +666,21 @@ __global__ void __launch_bounds__(NT, 5) render_kernel(const __grid_constant__ R
   }
 }
 
+__global__ void __launch_bounds__(NT, 5) render_kernel(const __grid_constant__ RenderArgs a) {
+  cg::cluster_group cluster = cg::this_cluster();
+  render_tile(a, blockIdx.x / a.split, (int)cluster.block_rank(), a.split);
+}
+
+// Several renders in one grid (continuous batching): cluster i renders window tile items[i].y of
+// request items[i].x; every request of the launch has the same tone split (= the cluster size).
+__global__ void __launch_bounds__(NT, 5) render_batch_kernel(const RenderArgs* __restrict__ reqs,
+                                                               const int2* __restrict__ items) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int split = (int)cluster.num_blocks();
+  const int2 it = items[blockIdx.x / split];
+  render_tile(reqs[it.x], it.y, (int)cluster.block_rank(), split);
+}
+
 // Exact phase words of the first n tones at one sample (test hook).
 __global__ void phase_words_kernel(const __grid_constant__ PhaseArgs a) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -700,7 +714,26 @@ __global__ void trace_kernel(const __grid_constant__ TraceArgs a) {
 }  // namespace
 
 cudaError_t render_setup_attributes() {
-  return cudaFuncSetAttribute(render_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(render_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+cudaError_t launch_render_batch(const RenderArgs* reqs, const int2* items, int n_items, int split, cudaStream_t s) {
+  if (n_items == 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_items * split), 1, 1);
+  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)split;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, render_batch_kernel, reqs, items);
 }
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {

@@ -1,0 +1,888 @@
+// Served request stream with continuous batching (C ABI in include/awg.h).
+//
+// A request is a tweezer-rearrangement waveform (Sec. V-B: a comb of static tones, some of them
+// chirped) that asks for n_chunks consecutive chunks of `chunk` samples.  Chunk c is released at
+// arrival + c * chunk / fs (when the previous chunk would start playing) and is due one playback
+// period later.  A scheduler thread admits requests while device memory and the real-time budget
+// allow, keeps each admitted request's tone and chirp state resident on the device (one handle
+// per request), and in every round renders all released chunks of all active requests in one
+// batched grid per tone-split size.  Each (request, tile) is computed exactly as a standalone
+// render of that request would compute it, so a result does not depend on its co-runners.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/awg.h"
+#include "awg_internal.h"
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Request {
+  int64_t id = 0;
+  // description (host copies)
+  std::vector<double> f, a, th, c_f0, c_f1, c_dur;
+  std::vector<int32_t> c_tone, c_prof;
+  std::vector<int64_t> c_start;
+  int64_t chunk = 0;
+  int32_t n_chunks = 0;
+  double full_scale = 0;
+  double t_arrival = 0;        // server clock, seconds
+  double period = 0;           // playback time of one chunk, s
+  // state
+  int32_t state = AWG_REQ_QUEUED;
+  awg_t* h = nullptr;
+  int16_t* d_out = nullptr;
+  size_t mem = 0, out_bytes = 0;
+  bool ready = false;          // set-up done: renderable
+  bool release_requested = false;
+  int32_t split = 1;
+  double weight = 0;           // device cost per sample, in static-tone units: K + n_chirps / 2
+  int32_t issue_chunk = 0;     // next piece to issue: chunk index and offset in it
+  int64_t issue_off = 0;
+  int32_t done_chunks = 0;     // chunks complete on the device
+  double t_ready = -1;         // set-up finished
+  double t_play = -1;          // chunk 0 complete: playback starts
+  double t_pieces = 0;         // latest completion among the pieces of the chunk being completed
+};
+
+// One round: pieces (a request's chunk, or a tile-aligned part of it) rendered by one batched
+// grid per tone-split size.
+struct Piece {
+  Request* r;
+  int32_t chunk;
+  int64_t off, n;
+  bool last;                   // completes its chunk
+};
+
+struct Round {
+  int set = 0;                 // staging buffers and events in use
+  std::vector<Piece> pieces;
+  double work = 0;             // tone-samples
+  double host_s = 0;           // host time to plan and issue
+  awg_round_record_t rec{};
+};
+
+// Fixed-capacity trace of the most recent records.
+template <class T>
+struct TraceRing {
+  static constexpr size_t CAP = 1u << 16;
+  std::vector<T> buf;
+  size_t n = 0;                // records written so far
+  void push(const T& x) {
+    if (buf.size() < CAP) buf.push_back(x);
+    else buf[n % CAP] = x;
+    ++n;
+  }
+  int32_t copy(T* out, int32_t cap) const {
+    const size_t have = std::min(n, CAP), take = std::min(have, (size_t)std::max(0, cap));
+    const size_t first = n - have + (have - take);   // skip the oldest when cap is short
+    for (size_t i = 0; i < take; ++i) out[i] = buf[(first + i) % CAP];
+    return (int32_t)take;
+  }
+};
+
+double percentile(std::vector<double> v, double q) {
+  if (v.empty()) return 0.0;
+  std::sort(v.begin(), v.end());
+  const double pos = q * (double)(v.size() - 1);
+  const size_t i = (size_t)pos;
+  const double f = pos - (double)i;
+  return i + 1 < v.size() ? v[i] * (1 - f) + v[i + 1] * f : v[i];
+}
+
+}  // namespace
+
+constexpr int NSETS = 3;       // rounds in flight, each on its own stream with its own buffers
+
+struct awg_server {
+  double fs = 0;
+  int64_t budget = 0;
+  int32_t max_active = 0;
+  double max_queue_s = 0;
+  int device = 0;
+  clk::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::atomic<int64_t> epoch{0};                  // bumped by submit / set-up done / release / stop
+  std::deque<Request*> pending;
+  std::vector<Request*> active;
+  std::map<int64_t, Request*> all;
+  int64_t next_id = 0;
+  int64_t used = 0;
+  std::thread sched, worker;
+  std::atomic<bool> stop{false};
+  std::deque<Request*> to_setup;                  // admitted, waiting for set-up (worker thread)
+  std::vector<awg_t*> idle_handles;               // pooled handles (state is replaced on reuse)
+  std::map<size_t, std::vector<int16_t*>> idle_out;   // pooled output buffers by byte size
+  // per set: stream, events, staging and device copies of the round's descriptors, tile records
+  cudaStream_t streams[NSETS] = {};
+  cudaEvent_t ev_ref = nullptr, ev_beg[NSETS] = {}, ev_end[NSETS] = {};
+  double t_ref = 0;                               // server clock when ev_ref completed
+  awgk::RenderArgs* h_reqs[NSETS] = {};
+  int2* h_items[NSETS] = {};
+  awgk::RenderArgs* d_reqs[NSETS] = {};
+  int2* d_items[NSETS] = {};
+  awgk::TileRec* d_arena[NSETS] = {};
+  int32_t* d_act[NSETS] = {};
+  size_t cap_reqs[NSETS] = {}, cap_items[NSETS] = {}, cap_arena[NSETS] = {}, cap_act[NSETS] = {};
+  std::deque<Round> flight;
+  int64_t round_seq = 0;
+  double queued_work = 0;      // tone-samples issued and not yet accounted complete
+  double busy_end = -1;        // end of the device's current busy interval (server clock)
+  // cost model (calibrated at creation): the device renders P static-tone samples/s when it is
+  // kept busy (updated from busy rounds within [0.6, 1.2] of the calibration); a round costs a_gpu
+  // more (descriptor copies, launches)
+  double P = 2.5e12, P_cal = 2.5e12;
+  double a_gpu = 20e-6;
+  double host_s = 30e-6;
+  // statistics
+  int64_t submitted = 0, admitted = 0, rej_deadline = 0, rej_memory = 0, completed = 0;
+  int64_t chunks = 0, misses = 0, rounds = 0, batched = 0, max_batch = 0;
+  std::vector<double> lat, ttfc;
+  TraceRing<awg_round_record_t> trace_rounds;
+  TraceRing<awg_chunk_record_t> trace_chunks;
+  double busy_s = 0, tone_samples = 0, samples = 0;
+  double first_t = -1, last_t = 0;
+  std::string error;
+};
+
+namespace {
+
+double now_s(const awg_server_t* s) { return std::chrono::duration<double>(clk::now() - s->t0).count(); }
+
+size_t footprint(const Request* r) {
+  const size_t tiles = (size_t)(r->chunk + 2 * awgk::TILE - 1) / awgk::TILE;
+  return (size_t)r->f.size() * sizeof(awgk::ToneRec) + r->c_tone.size() * sizeof(awgk::ChirpRec) +
+         r->c_tone.size() * tiles * sizeof(awgk::TileRec) + (size_t)r->n_chunks * (size_t)r->chunk * 2 + (64u << 10);
+}
+
+// Queue horizon for a set whose shortest chunk period is min_period: the scheduler issues work
+// only while the device has less than this much queued, so a newly released chunk starts within
+// about one horizon.
+double horizon(double min_period) { return std::min(2e-3, std::max(40e-6, min_period / 3.0)); }
+
+// Admission by the real-time budget (EDF density with release jitter): chunk i needs
+// C_i = K_i chunk_i / P of device time within its period T_i, of which the queue horizon H and the
+// round cost a_gpu are lost, so the set is accepted while sum C_i / (T_i - H - a_gpu) <= 0.85 and
+// one tile of the largest request fits in a horizon.  `extra` (may be null) is a candidate.
+bool fits_set(const awg_server_t* s, const std::vector<const Request*>& set) {
+  double min_period = 1e30, kmax = 0;
+  for (const Request* q : set) {
+    min_period = std::min(min_period, q->period);
+    kmax = std::max(kmax, (double)q->f.size());
+  }
+  if (set.empty()) return true;
+  const double H = horizon(min_period);
+  double density = 0;
+  for (const Request* q : set) {
+    const double window = q->period - H - s->a_gpu;
+    if (window <= 0) return false;
+    density += q->weight * (double)q->chunk / s->P / window;
+  }
+  return density <= 0.85 && kmax * awgk::TILE / s->P <= H;
+}
+
+bool fits_deadline(const awg_server_t* s, const Request* extra) {
+  std::vector<const Request*> set(s->active.begin(), s->active.end());
+  if (extra) set.push_back(extra);
+  return fits_set(s, set);
+}
+
+// Could `r` ever be admitted (alone, with an idle device)?
+bool fits_alone(const awg_server_t* s, const Request* r) { return fits_set(s, {r}); }
+
+bool start_request(awg_server_t* s, Request* r) {
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (!s->idle_handles.empty()) {
+      r->h = s->idle_handles.back();
+      s->idle_handles.pop_back();
+    }
+  }
+  if (!r->h) r->h = awg_create(s->fs);
+  if (!r->h) return false;
+  if (awg_seek(r->h, 0)) return false;
+  const int32_t K = (int32_t)r->f.size();
+  if (awg_set_tones(r->h, r->f.data(), r->a.data(), r->th.data(), K)) return false;
+  if (!r->c_tone.empty() &&
+      awg_set_chirps(r->h, r->c_tone.data(), r->c_f0.data(), r->c_f1.data(), r->c_dur.data(), r->c_prof.data(),
+                     r->c_start.data(), (int32_t)r->c_tone.size()))
+    return false;
+  if (awg_set_full_scale(r->h, r->full_scale)) return false;
+  r->split = awg_tone_split(r->h);
+  r->out_bytes = std::max<size_t>((size_t)r->n_chunks * (size_t)r->chunk * sizeof(int16_t), 16);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->idle_out.find(r->out_bytes);
+    if (it != s->idle_out.end() && !it->second.empty()) {
+      r->d_out = it->second.back();
+      it->second.pop_back();
+    }
+  }
+  if (!r->d_out && cudaMalloc((void**)&r->d_out, r->out_bytes) != cudaSuccess) return false;
+  return true;
+}
+
+// Handles go back to the pool instead of being destroyed (no device allocation in steady state).
+void recycle_handle(awg_server_t* s, Request* r) {
+  if (r->h) s->idle_handles.push_back(r->h);
+  r->h = nullptr;
+}
+
+void destroy_handle(Request* r) {
+  if (r->h) awg_destroy(r->h);
+  r->h = nullptr;
+}
+
+void bump(awg_server_t* s) {
+  s->epoch.fetch_add(1);
+  s->cv.notify_all();
+}
+
+// Set-up of admitted requests (handle, tone and chirp state, output buffer) off the scheduler's
+// critical path.
+void worker_main(awg_server_t* s) {
+  cudaSetDevice(s->device);
+  while (true) {
+    Request* r = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait_for(lk, std::chrono::milliseconds(50), [&] { return s->stop.load() || !s->to_setup.empty(); });
+      if (s->stop.load()) return;
+      if (s->to_setup.empty()) continue;
+      r = s->to_setup.front();
+      s->to_setup.pop_front();
+    }
+    const bool ok = start_request(s, r);
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      if (ok) {
+        r->ready = true;
+        r->t_ready = now_s(s);
+      } else {
+        s->error = std::string("request set-up failed: ") + awg_last_error();
+        r->state = AWG_REQ_REJECTED;
+        ++s->rej_memory;
+        s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+        s->used -= (int64_t)r->mem;
+        if (r->d_out) s->idle_out[r->out_bytes].push_back(r->d_out);
+        r->d_out = nullptr;
+        recycle_handle(s, r);
+      }
+    }
+    bump(s);
+  }
+}
+
+template <class T>
+bool grow(T** dev, T** host, size_t* cap, size_t need) {
+  if (need <= *cap) return true;
+  size_t ncap = std::max(need, *cap * 2);
+  T *d = nullptr, *h = nullptr;
+  if (cudaMalloc((void**)&d, ncap * sizeof(T)) != cudaSuccess) return false;
+  if (cudaHostAlloc((void**)&h, ncap * sizeof(T), cudaHostAllocDefault) != cudaSuccess) {
+    cudaFree(d);
+    return false;
+  }
+  cudaFree(*dev);
+  cudaFreeHost(*host);
+  *dev = d;
+  *host = h;
+  *cap = ncap;
+  return true;
+}
+
+// Retire released outputs; admit queued requests (any order: a request that does not fit yet
+// waits, up to max_queue_s, without blocking those behind it).  Lock held.
+void admit(awg_server_t* s) {
+  for (auto it = s->all.begin(); it != s->all.end();) {
+    Request* r = it->second;
+    if (r->release_requested && (r->state == AWG_REQ_DONE || r->state == AWG_REQ_REJECTED)) {
+      if (r->d_out) {
+        s->idle_out[r->out_bytes].push_back(r->d_out);
+        s->used -= (int64_t)r->out_bytes;
+      }
+      delete r;
+      it = s->all.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  const double now = now_s(s);
+  bool changed = false;
+  for (auto it = s->pending.begin(); it != s->pending.end();) {
+    Request* r = *it;
+    const size_t mem = footprint(r);
+    int verdict = 0;   // 0 wait, 1 admit, -1 reject (deadline), -2 reject (memory)
+    if (!fits_alone(s, r)) {
+      verdict = -1;
+    } else if ((int64_t)mem > s->budget) {
+      verdict = -2;
+    } else {
+      const bool mem_ok = s->used + (int64_t)mem <= s->budget && (int32_t)s->active.size() < s->max_active;
+      const bool rt_ok = fits_deadline(s, r);
+      if (mem_ok && rt_ok) verdict = 1;
+      else if (now - r->t_arrival > s->max_queue_s) verdict = rt_ok ? -2 : -1;
+    }
+    if (verdict == 0) {
+      ++it;
+      continue;
+    }
+    changed = true;
+    if (verdict == 1) {
+      r->mem = mem;
+      s->used += (int64_t)mem;
+      r->state = AWG_REQ_ACTIVE;
+      ++s->admitted;
+      s->active.push_back(r);
+      s->to_setup.push_back(r);
+    } else {
+      r->state = AWG_REQ_REJECTED;
+      ++(verdict == -1 ? s->rej_deadline : s->rej_memory);
+    }
+    it = s->pending.erase(it);
+  }
+  if (changed) s->cv.notify_all();   // worker; awg_server_drain / poll
+}
+
+// Earliest-deadline-first plan of one round at time `now`.  Chunk 0 of a request is released when
+// its set-up is done; it starts playback when it completes (t_play), and chunk c >= 1 is released
+// when chunk c-1 starts playing (t_play + (c-1) period) and due when chunk c-1 ends
+// (t_play + c period).  A round takes what fills the device's queue up to the horizon; a chunk
+// that does not fit is cut into whole tiles and continued in later rounds.
+// Returns the earliest future release in *next_release.  Lock held.
+void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
+  struct Cand {
+    double due;
+    Request* r;
+  };
+  std::vector<Cand> cands;
+  double min_period = 1e30;
+  *next_release = 1e30;
+  for (Request* r : s->active) {
+    min_period = std::min(min_period, r->period);
+    if (!r->ready || r->issue_chunk >= r->n_chunks) continue;
+    const int32_t c = r->issue_chunk;
+    double rel, due;
+    if (c == 0) {
+      rel = r->t_ready;
+      due = r->t_ready + r->period;
+    } else {
+      if (r->t_play < 0) continue;   // chunk 0 still in flight
+      rel = r->t_play + (double)(c - 1) * r->period;
+      due = r->t_play + (double)c * r->period;
+    }
+    if (rel <= now) cands.push_back({due, r});
+    else *next_release = std::min(*next_release, rel);
+  }
+  if (cands.empty()) return;
+  // work the device may take on now: fill the queue up to the horizon
+  const double H = horizon(min_period);
+  const double queued = s->queued_work / s->P;
+  if (!s->flight.empty() && queued >= H) return;
+  double w_left = std::max(0.5 * H, H - queued - s->a_gpu) * s->P;
+  std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.due < y.due; });
+  rd->rec.first_due = 1e30;
+  for (const Cand& cd : cands)
+    if (cd.r->issue_chunk > 0) {
+      rd->rec.first_due = cd.due;
+      break;
+    }
+  for (const Cand& cd : cands) {
+    if (w_left <= 0 && !rd->pieces.empty()) break;
+    Request* r = cd.r;
+    const double K = std::max(1.0, r->weight);
+    const int64_t remaining = r->chunk - r->issue_off;
+    int64_t take = remaining;
+    if (K * (double)take > w_left) {
+      const int64_t tiles = std::max<int64_t>(1, (int64_t)(w_left / K) / awgk::TILE);
+      take = std::min(remaining, tiles * awgk::TILE);
+    }
+    rd->pieces.push_back({r, r->issue_chunk, r->issue_off, take, take == remaining});
+    rd->work += K * (double)take;
+    w_left -= K * (double)take;
+    r->issue_off += take;
+    if (r->issue_off == r->chunk) {
+      r->issue_off = 0;
+      ++r->issue_chunk;
+    }
+  }
+}
+
+// Issue a planned round on its set's stream (outside the lock: only this thread touches active
+// requests' handles).  The round's tile records live in the set's arena, so rounds on the other
+// streams (including other pieces of the same request) can run at the same time.
+bool issue_round(awg_server_t* s, Round* rd) {
+  const int set = rd->set;
+  cudaStream_t st = s->streams[set];
+  std::sort(rd->pieces.begin(), rd->pieces.end(),
+            [](const Piece& x, const Piece& y) { return x.r->split < y.r->split; });
+  std::vector<size_t> rec0(rd->pieces.size() + 1, 0), act0(rd->pieces.size() + 1, 0);
+  for (size_t i = 0; i < rd->pieces.size(); ++i) {
+    rec0[i + 1] = rec0[i] + awgk::render_recs_needed(rd->pieces[i].r->h, rd->pieces[i].n);
+    act0[i + 1] = act0[i] + awgk::render_slots(rd->pieces[i].r->h);
+  }
+  // grow: the set's previous round is complete (it left the flight queue), so nothing uses them
+  if (rec0.back() > s->cap_arena[set]) {
+    const size_t ncap = std::max(rec0.back(), 2 * s->cap_arena[set]);
+    awgk::TileRec* a = nullptr;
+    if (cudaMalloc((void**)&a, ncap * sizeof(awgk::TileRec)) != cudaSuccess) return false;
+    cudaFree(s->d_arena[set]);
+    s->d_arena[set] = a;
+    s->cap_arena[set] = ncap;
+  }
+  if (act0.back() > s->cap_act[set]) {
+    const size_t ncap = std::max(act0.back(), 2 * s->cap_act[set]);
+    int32_t* a = nullptr;
+    if (cudaMalloc((void**)&a, ncap * sizeof(int32_t)) != cudaSuccess) return false;
+    cudaFree(s->d_act[set]);
+    s->d_act[set] = a;
+    s->cap_act[set] = ncap;
+  }
+  std::vector<awgk::RenderArgs> ra(rd->pieces.size());
+  size_t n_items = 0;
+  bool ok = cudaEventRecord(s->ev_beg[set], st) == cudaSuccess;
+  for (size_t i = 0; i < rd->pieces.size() && ok; ++i) {
+    const Piece& p = rd->pieces[i];
+    int16_t* out = p.r->d_out + (size_t)p.chunk * (size_t)p.r->chunk + (size_t)p.off;
+    const bool own = rec0[i + 1] > rec0[i];   // chirp tile records in this piece
+    ok = awgk::prepare_render(p.r->h, p.n, out, nullptr, st, &ra[i], own ? s->d_arena[set] + rec0[i] : nullptr,
+                              rec0[i + 1] - rec0[i], own ? s->d_act[set] + act0[i] : nullptr) == AWG_OK;
+    n_items += (size_t)ra[i].n_tiles;
+  }
+  rd->rec.pieces = (int32_t)rd->pieces.size();
+  rd->rec.tiles = (int32_t)n_items;
+  ok = ok && grow(&s->d_reqs[set], &s->h_reqs[set], &s->cap_reqs[set], rd->pieces.size()) &&
+       grow(&s->d_items[set], &s->h_items[set], &s->cap_items[set], n_items);
+  if (!ok) return false;
+  size_t it = 0;
+  for (size_t i = 0; i < rd->pieces.size(); ++i) {
+    s->h_reqs[set][i] = ra[i];
+    for (int32_t t = 0; t < ra[i].n_tiles; ++t) s->h_items[set][it++] = make_int2((int)i, t);
+  }
+  ok = cudaMemcpyAsync(s->d_reqs[set], s->h_reqs[set], rd->pieces.size() * sizeof(awgk::RenderArgs),
+                       cudaMemcpyHostToDevice, st) == cudaSuccess &&
+       cudaMemcpyAsync(s->d_items[set], s->h_items[set], n_items * sizeof(int2), cudaMemcpyHostToDevice, st) ==
+           cudaSuccess;
+  size_t b = 0, item0 = 0;
+  while (ok && b < rd->pieces.size()) {
+    size_t e = b, items = 0;
+    while (e < rd->pieces.size() && rd->pieces[e].r->split == rd->pieces[b].r->split)
+      items += (size_t)ra[e++].n_tiles;
+    ok = awgk::launch_render_batch(s->d_reqs[set], s->d_items[set] + item0, (int)items, rd->pieces[b].r->split,
+                                   st) == cudaSuccess;
+    item0 += items;
+    b = e;
+  }
+  return ok && cudaEventRecord(s->ev_end[set], st) == cudaSuccess;
+}
+
+// Account for the oldest round once its end event has completed.
+void complete_round(awg_server_t* s) {
+  Round rd = std::move(s->flight.front());
+  s->flight.pop_front();
+  float end_ms = 0.f, gpu_ms = 0.f;
+  cudaEventElapsedTime(&end_ms, s->ev_ref, s->ev_end[rd.set]);
+  cudaEventElapsedTime(&gpu_ms, s->ev_beg[rd.set], s->ev_end[rd.set]);
+  const double t_done = s->t_ref + 1e-3 * (double)end_ms;   // device completion, server clock
+  const double t_start = t_done - 1e-3 * (double)gpu_ms;    // the round's stream reached it
+  std::vector<Request*> finished;
+  std::lock_guard<std::mutex> lk(s->mu);
+  rd.rec.t_start = t_start;
+  rd.rec.t_done = t_done;
+  rd.rec.work = rd.work;
+  s->trace_rounds.push(rd.rec);
+  s->queued_work = std::max(0.0, s->queued_work - rd.work);
+  ++s->rounds;
+  s->batched += (int64_t)rd.pieces.size();
+  s->max_batch = std::max(s->max_batch, (int64_t)rd.pieces.size());
+  s->tone_samples += rd.work;
+  if (s->first_t < 0) s->first_t = t_start;
+  s->last_t = std::max(s->last_t, t_done);
+  // a round that found the device busy measures the sustained rate: its work over the advance of
+  // the busy interval's end
+  if (t_done > s->busy_end && rd.work > 0) {
+    if (t_start < s->busy_end) {
+      const double rate = rd.work / (t_done - s->busy_end);
+      s->P = std::min(1.2 * s->P_cal, std::max(0.6 * s->P_cal, 0.95 * s->P + 0.05 * rate));
+      s->busy_s += t_done - s->busy_end;
+    } else {
+      s->busy_s += t_done - t_start;
+    }
+    s->busy_end = t_done;
+  }
+  s->host_s = 0.9 * s->host_s + 0.1 * rd.host_s;
+  for (const Piece& p : rd.pieces) {
+    Request* r = p.r;
+    r->t_pieces = std::max(r->t_pieces, t_done);
+    if (!p.last) continue;
+    const double t_chunk = r->t_pieces;   // all pieces of the chunk are complete
+    r->t_pieces = 0;
+    awg_chunk_record_t cr{};
+    cr.id = r->id;
+    cr.chunk = p.chunk;
+    cr.done = t_chunk;
+    if (p.chunk == 0) {
+      r->t_play = t_chunk;
+      s->ttfc.push_back(t_chunk - r->t_arrival);
+      cr.release = r->t_ready;
+      cr.due = r->t_ready + r->period;
+    } else {
+      const double rel = r->t_play + (double)(p.chunk - 1) * r->period;
+      s->lat.push_back(t_chunk - rel);
+      cr.release = rel;
+      cr.due = rel + r->period;
+      cr.late = t_chunk > cr.due;
+      if (cr.late) ++s->misses;
+    }
+    s->trace_chunks.push(cr);
+    ++s->chunks;
+    s->samples += (double)r->chunk;
+    r->done_chunks = p.chunk + 1;
+    if (r->done_chunks == r->n_chunks) finished.push_back(r);
+  }
+  for (Request* r : finished) {
+    r->state = AWG_REQ_DONE;
+    ++s->completed;
+    s->active.erase(std::find(s->active.begin(), s->active.end(), r));
+    recycle_handle(s, r);
+    s->used -= (int64_t)(r->mem - r->out_bytes);
+  }
+  s->cv.notify_all();
+}
+
+void fail_rounds(awg_server_t* s, const std::string& what) {
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->error = what + ": " + awg_last_error();
+  s->stop.store(true);
+  s->cv.notify_all();
+}
+
+// Cost model calibration: the device time of a round of one tile of one tone (fixed cost a_gpu)
+// and of a round of 2048 static tones over 2^19 samples (rate P), best of three each, through the
+// same path as the served rounds.
+int calibrate(awg_server_t* s) {
+  const int32_t K = 2048;
+  const int64_t N = (int64_t)1 << 19;
+  std::vector<double> f(K), a(K, 1.0 / K), th(K, 0.0);
+  for (int32_t k = 0; k < K; ++k) f[k] = s->fs * (0.01 + 0.4 * (double)k / K);
+  awg_t* h = awg_create(s->fs);
+  int16_t* out = nullptr;
+  int st = h ? AWG_OK : AWG_ECUDA;
+  if (!st && cudaMalloc((void**)&out, (size_t)N * sizeof(int16_t)) != cudaSuccess)
+    st = awgk::set_error(AWG_ENOMEM, "calibration buffer");
+  double best[2] = {1e30, 1e30};
+  for (int pass = 0; pass < 2 && !st; ++pass) {
+    const int32_t k = pass == 0 ? 1 : K;
+    const int64_t n = pass == 0 ? awgk::TILE : N;
+    if ((st = awg_set_tones(h, f.data(), a.data(), th.data(), k))) break;
+    Request r;
+    r.h = h;
+    r.d_out = out;
+    r.chunk = n;
+    r.n_chunks = 1;
+    r.split = awg_tone_split(h);
+    for (int rep = 0; rep < 4 && !st; ++rep) {
+      awg_seek(h, 0);
+      Round rd;
+      rd.set = 0;
+      rd.pieces.push_back({&r, 0, 0, n, true});
+      float ms = 0.f;
+      if (!issue_round(s, &rd) || cudaEventSynchronize(s->ev_end[0]) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, s->ev_beg[0], s->ev_end[0]) != cudaSuccess) {
+        st = awgk::set_error(AWG_ECUDA, "calibration round failed");
+        break;
+      }
+      if (rep > 0) best[pass] = std::min(best[pass], 1e-3 * (double)ms);   // the first is a warm-up
+    }
+  }
+  if (out) cudaFree(out);
+  if (h) awg_destroy(h);
+  if (st) return st;
+  s->a_gpu = std::max(2e-6, best[0]);
+  s->P = s->P_cal = (double)K * (double)N / std::max(1e-6, best[1] - s->a_gpu);
+  return AWG_OK;
+}
+
+// Scheduler: up to NSETS rounds in flight on their own streams; the host plans the next round
+// while earlier ones run, and rounds overlap on the device when one alone does not fill it.
+void sched_main(awg_server_t* s) {
+  cudaSetDevice(s->device);
+  while (!s->stop.load()) {
+    const int64_t ep = s->epoch.load();
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      admit(s);
+    }
+    while (!s->flight.empty() && cudaEventQuery(s->ev_end[s->flight.front().set]) == cudaSuccess) complete_round(s);
+
+    double next_release = 1e30;
+    if ((int)s->flight.size() < NSETS) {
+      const double t_plan = now_s(s);
+      Round rd;
+      rd.set = (int)(s->round_seq % NSETS);
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        plan_round(s, t_plan, &rd, &next_release);
+        s->queued_work += rd.work;
+      }
+      if (!rd.pieces.empty()) {
+        if (!issue_round(s, &rd)) {
+          fail_rounds(s, "round failed");
+          break;
+        }
+        const double t_issued = now_s(s);
+        rd.host_s = t_issued - t_plan;
+        rd.rec.t_plan = t_plan;
+        rd.rec.t_issued = t_issued;
+        s->flight.push_back(std::move(rd));
+        ++s->round_seq;
+        continue;
+      }
+    }
+    // Nothing to issue now: wait for the oldest round, the next release or new work.
+    if (!s->flight.empty()) {
+      const cudaEvent_t ev = s->ev_end[s->flight.front().set];
+      while (!s->stop.load()) {
+        const cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) {
+          fail_rounds(s, "round failed");
+          break;
+        }
+        if ((int)s->flight.size() < NSETS && (now_s(s) >= next_release || s->epoch.load() != ep)) break;
+        std::this_thread::yield();
+      }
+      continue;
+    }
+    const double wait = next_release - now_s(s);
+    if (wait > 1e-3) {
+      std::unique_lock<std::mutex> lk(s->mu);
+      s->cv.wait_for(lk, std::chrono::duration<double>(std::min(0.05, wait - 0.5e-3)),
+                     [&] { return s->stop.load() || s->epoch.load() != ep; });
+    } else {
+      while (!s->stop.load() && now_s(s) < next_release && s->epoch.load() == ep) std::this_thread::yield();
+    }
+  }
+  for (int i = 0; i < NSETS; ++i)
+    if (s->streams[i]) cudaStreamSynchronize(s->streams[i]);
+}
+
+}  // namespace
+
+extern "C" {
+
+awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes, int32_t max_active,
+                                double max_queue_ms) {
+  if (!(sample_rate_hz > 0) || mem_budget_bytes <= 0 || max_active < 1 || !(max_queue_ms >= 0)) {
+    awgk::set_error(AWG_EINVAL, "server needs fs > 0, a memory budget, max_active >= 1 and max_queue_ms >= 0");
+    return nullptr;
+  }
+  awg_server_t* s = new awg_server();
+  s->fs = sample_rate_hz;
+  s->budget = mem_budget_bytes;
+  s->max_active = max_active;
+  s->max_queue_s = 1e-3 * max_queue_ms;
+  s->t0 = clk::now();
+  cudaError_t e = cudaGetDevice(&s->device);
+  for (int i = 0; i < NSETS && e == cudaSuccess; ++i) {
+    e = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev_beg[i]);
+    if (e == cudaSuccess) e = cudaEventCreate(&s->ev_end[i]);
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&s->ev_ref);
+  if (e == cudaSuccess) e = awgk::render_setup_attributes();
+  // reference point between the device's event clock and the server clock
+  if (e == cudaSuccess) e = cudaEventRecord(s->ev_ref, s->streams[0]);
+  if (e == cudaSuccess) e = cudaEventSynchronize(s->ev_ref);
+  s->t_ref = now_s(s);
+  if (e != cudaSuccess) {
+    awgk::set_error(AWG_ECUDA, std::string("server set-up: ") + cudaGetErrorString(e));
+    awg_server_destroy(s);
+    return nullptr;
+  }
+  if (calibrate(s) != AWG_OK) {
+    const std::string why = awg_last_error();
+    awg_server_destroy(s);
+    awgk::set_error(AWG_ECUDA, "server calibration: " + why);
+    return nullptr;
+  }
+  s->sched = std::thread(sched_main, s);
+  s->worker = std::thread(worker_main, s);
+  return s;
+}
+
+void awg_server_destroy(awg_server_t* s) {
+  if (!s) return;
+  s->stop.store(true);
+  bump(s);
+  if (s->sched.joinable()) s->sched.join();
+  if (s->worker.joinable()) s->worker.join();
+  for (int i = 0; i < NSETS; ++i)
+    if (s->streams[i]) cudaStreamSynchronize(s->streams[i]);
+  for (auto& kv : s->all) {
+    destroy_handle(kv.second);
+    if (kv.second->d_out) cudaFree(kv.second->d_out);
+    delete kv.second;
+  }
+  for (awg_t* h : s->idle_handles) awg_destroy(h);
+  for (auto& kv : s->idle_out)
+    for (int16_t* p : kv.second) cudaFree(p);
+  for (int i = 0; i < NSETS; ++i) {
+    cudaFree(s->d_arena[i]);
+    cudaFree(s->d_act[i]);
+    cudaFree(s->d_reqs[i]);
+    cudaFree(s->d_items[i]);
+    cudaFreeHost(s->h_reqs[i]);
+    cudaFreeHost(s->h_items[i]);
+    if (s->ev_beg[i]) cudaEventDestroy(s->ev_beg[i]);
+    if (s->ev_end[i]) cudaEventDestroy(s->ev_end[i]);
+  }
+  if (s->ev_ref) cudaEventDestroy(s->ev_ref);
+  for (int i = 0; i < NSETS; ++i)
+    if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
+  delete s;
+}
+
+int64_t awg_server_submit(awg_server_t* s, const awg_request_t* q) {
+  if (!s || !q) return awgk::set_error(AWG_EINVAL, "null server or request");
+  if (q->n_tones < 0 || q->n_chirps < 0 || q->chunk < 1 || q->n_chunks < 1 || q->chunk > ((int64_t)1 << 26))
+    return awgk::set_error(AWG_EINVAL, "bad request sizes");
+  if ((q->n_tones > 0 && (!q->freq_hz || !q->amp || !q->phase_rad)) ||
+      (q->n_chirps > 0 && (!q->chirp_tone || !q->chirp_f_start_hz || !q->chirp_f_end_hz || !q->chirp_duration_s ||
+                           !q->chirp_profile || !q->chirp_start_sample)))
+    return awgk::set_error(AWG_EINVAL, "null request array");
+  Request* r = new Request();
+  r->f.assign(q->freq_hz, q->freq_hz + q->n_tones);
+  r->a.assign(q->amp, q->amp + q->n_tones);
+  r->th.assign(q->phase_rad, q->phase_rad + q->n_tones);
+  r->c_tone.assign(q->chirp_tone, q->chirp_tone + q->n_chirps);
+  r->c_f0.assign(q->chirp_f_start_hz, q->chirp_f_start_hz + q->n_chirps);
+  r->c_f1.assign(q->chirp_f_end_hz, q->chirp_f_end_hz + q->n_chirps);
+  r->c_dur.assign(q->chirp_duration_s, q->chirp_duration_s + q->n_chirps);
+  r->c_prof.assign(q->chirp_profile, q->chirp_profile + q->n_chirps);
+  r->c_start.assign(q->chirp_start_sample, q->chirp_start_sample + q->n_chirps);
+  r->chunk = q->chunk;
+  r->n_chunks = q->n_chunks;
+  r->full_scale = q->full_scale;
+  r->period = (double)q->chunk / s->fs;
+  r->weight = (double)q->n_tones + 0.5 * (double)q->n_chirps;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    r->id = s->next_id++;
+    r->t_arrival = now_s(s);
+    s->all[r->id] = r;
+    s->pending.push_back(r);
+    ++s->submitted;
+  }
+  bump(s);
+  return r->id;
+}
+
+int awg_server_poll(awg_server_t* s, int64_t id, int32_t* state, int32_t* chunks_done) {
+  if (!s) return awgk::set_error(AWG_EINVAL, "null server");
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->all.find(id);
+  if (it == s->all.end()) return awgk::set_error(AWG_EINVAL, "unknown request id");
+  if (state) *state = it->second->state;
+  if (chunks_done) *chunks_done = it->second->done_chunks;
+  return AWG_OK;
+}
+
+int awg_server_read(awg_server_t* s, int64_t id, int16_t* host_out, int64_t n_samples) {
+  if (!s || !host_out) return awgk::set_error(AWG_EINVAL, "null argument");
+  int16_t* src = nullptr;
+  int64_t total = 0;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return awgk::set_error(AWG_EINVAL, "unknown request id");
+    Request* r = it->second;
+    if (r->state != AWG_REQ_DONE) return awgk::set_error(AWG_ESTATE, "request not done");
+    src = r->d_out;
+    total = (int64_t)r->n_chunks * r->chunk;
+  }
+  if (n_samples < 0 || n_samples > total) return awgk::set_error(AWG_EINVAL, "sample count out of range");
+  cudaError_t e = cudaMemcpy(host_out, src, (size_t)n_samples * sizeof(int16_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return awgk::set_error(AWG_ECUDA, std::string("read: ") + cudaGetErrorString(e));
+  return AWG_OK;
+}
+
+int awg_server_release(awg_server_t* s, int64_t id) {
+  if (!s) return awgk::set_error(AWG_EINVAL, "null server");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return awgk::set_error(AWG_EINVAL, "unknown request id");
+    it->second->release_requested = true;
+  }
+  bump(s);
+  return AWG_OK;
+}
+
+int awg_server_drain(awg_server_t* s, int32_t timeout_ms) {
+  if (!s) return awgk::set_error(AWG_EINVAL, "null server");
+  std::unique_lock<std::mutex> lk(s->mu);
+  const bool ok = s->cv.wait_for(lk, std::chrono::milliseconds(std::max(0, timeout_ms)), [&] {
+    if (s->stop.load()) return true;
+    if (!s->pending.empty() || !s->active.empty()) return false;
+    return true;
+  });
+  if (!s->error.empty()) return awgk::set_error(AWG_ECUDA, s->error);
+  return ok ? AWG_OK : awgk::set_error(AWG_ETIMEOUT, "requests still in flight");
+}
+
+int awg_server_stats(awg_server_t* s, awg_server_stats_t* out) {
+  if (!s || !out) return awgk::set_error(AWG_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::memset(out, 0, sizeof(*out));
+  out->submitted = s->submitted;
+  out->admitted = s->admitted;
+  out->rejected_deadline = s->rej_deadline;
+  out->rejected_memory = s->rej_memory;
+  out->completed = s->completed;
+  out->chunks = s->chunks;
+  out->deadline_misses = s->misses;
+  out->latency_p50_ms = 1e3 * percentile(s->lat, 0.50);
+  out->latency_p99_ms = 1e3 * percentile(s->lat, 0.99);
+  out->latency_max_ms = s->lat.empty() ? 0 : 1e3 * *std::max_element(s->lat.begin(), s->lat.end());
+  out->first_chunk_p50_ms = 1e3 * percentile(s->ttfc, 0.50);
+  out->first_chunk_p99_ms = 1e3 * percentile(s->ttfc, 0.99);
+  out->rounds = s->rounds;
+  out->mean_batch = s->rounds ? (double)s->batched / (double)s->rounds : 0.0;
+  out->max_batch = s->max_batch;
+  const double span = s->first_t >= 0 ? std::max(1e-9, s->last_t - s->first_t) : 1e-9;
+  out->tone_samples_per_s = s->tone_samples / span;
+  out->samples_per_s = s->samples / span;
+  out->busy_fraction = s->busy_s / span;
+  out->est_throughput = s->P;
+  out->est_round_cost_ms = 1e3 * s->a_gpu;
+  return AWG_OK;
+}
+
+int32_t awg_server_trace_rounds(awg_server_t* s, awg_round_record_t* out, int32_t cap) {
+  if (!s || (cap > 0 && !out)) return awgk::set_error(AWG_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  return s->trace_rounds.copy(out, cap);
+}
+
+int32_t awg_server_trace_chunks(awg_server_t* s, awg_chunk_record_t* out, int32_t cap) {
+  if (!s || (cap > 0 && !out)) return awgk::set_error(AWG_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  return s->trace_chunks.copy(out, cap);
+}
+
+}  // extern "C"

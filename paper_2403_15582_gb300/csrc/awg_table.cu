@@ -381,7 +381,7 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   if (!enc) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
-    e = cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q);
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     enc = (EncodeTiledFn)fn;
   }

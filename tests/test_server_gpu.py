@@ -1,0 +1,111 @@
+"""Served request stream: continuous batching, admission by deadline and memory, and results that
+do not depend on the co-runners (each request equals its standalone render bit for bit)."""
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def awg(awglib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return awglib
+
+
+def _request(seed, fs, K, chunk, n_chunks, n_chirps):
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(0.02 * fs, 0.45 * fs, K)
+    a = np.full(K, 1.0 / K)
+    th = rng.uniform(0, 2 * np.pi, K)
+    chirps = []
+    for t in rng.choice(K, size=min(n_chirps, K), replace=False):
+        chirps.append(dict(tone=int(t), f_start=float(f[t]), f_end=float(rng.uniform(0.02 * fs, 0.45 * fs)),
+                           duration=float(rng.integers(3000, 60000)) / fs, profile=int(rng.integers(0, 2)),
+                           start_sample=int(rng.integers(0, 5000))))
+    return f, a, th, chirps, chunk, n_chunks
+
+
+def _standalone(awg, fs, req):
+    f, a, th, chirps, chunk, n_chunks = req
+    s = awg.Synth(fs)
+    s.set_tones(f, a, th)
+    s.set_chirp_list(chirps)
+    out = torch.empty(chunk * n_chunks, dtype=torch.int16, device="cuda")
+    for c in range(n_chunks):
+        s.render(chunk, out[c * chunk:])
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_results_same_alone_and_in_the_mix(awg):
+    fs = 20e6     # long playback periods: every request is admitted
+    reqs = [_request(i, fs, K, chunk, 4, nc) for i, (K, chunk, nc) in
+            enumerate([(50, 1 << 16, 10), (700, 1 << 17, 40), (3000, 1 << 16, 100), (129, 70000, 5),
+                       (1500, 1 << 18, 0), (64, 1 << 16, 64), (960, 99999, 30), (5000, 1 << 17, 100)])]
+    srv = awg.Server(fs, 8 << 30, 64)
+    ids = []
+    for i, r in enumerate(reqs):
+        f, a, th, chirps, chunk, n_chunks = r
+        ids.append(srv.submit(f, a, th, chunk, n_chunks, chirps))
+        if i == 3:
+            time.sleep(0.004)    # the rest arrive while the first ones are running
+    srv.drain(60000)
+    st = srv.stats()
+    assert st["admitted"] == len(reqs) and st["completed"] == len(reqs)
+    for rid, r in zip(ids, reqs):
+        state, done = srv.poll(rid)
+        assert state == awg.binding.REQ_DONE and done == r[5]
+        got = srv.read(rid, r[4] * r[5])
+        assert np.array_equal(got, _standalone(awg, fs, r)), rid
+        srv.release(rid)
+    srv.close()
+
+
+def test_admission_rejects_what_cannot_meet_its_deadline(awg):
+    fs = 280e6    # 10,000 tones at 280 MS/s with 2^16-sample chunks (234 us) cannot keep up
+    srv = awg.Server(fs, 8 << 30, 64)
+    f, a, th, chirps, chunk, n = _request(1, fs, 10000, 1 << 16, 4, 0)
+    rid = srv.submit(f, a, th, chunk, n, chirps)
+    f2, a2, th2, c2, chunk2, n2 = _request(2, fs, 100, 1 << 20, 2, 3)
+    rid2 = srv.submit(f2, a2, th2, chunk2, n2, c2)
+    srv.drain(60000)
+    assert srv.poll(rid)[0] == awg.binding.REQ_REJECTED
+    assert srv.poll(rid2)[0] == awg.binding.REQ_DONE
+    st = srv.stats()
+    assert st["rejected_deadline"] >= 1 and st["deadline_misses"] == 0
+    srv.close()
+
+
+def test_admission_by_memory(awg):
+    fs = 20e6
+    srv = awg.Server(fs, 1 << 20, 8)       # 1 MiB budget: a 2^18 x 8 chunk output does not fit
+    f, a, th, chirps, chunk, n = _request(3, fs, 50, 1 << 18, 8, 0)
+    rid = srv.submit(f, a, th, chunk, n, chirps)
+    srv.drain(30000)
+    assert srv.poll(rid)[0] == awg.binding.REQ_REJECTED
+    assert srv.stats()["rejected_memory"] == 1
+    srv.close()
+
+
+def test_chunks_cut_into_tile_pieces_match_standalone(awg):
+    """At 280 MS/s a 2^16-sample chunk plays for 234 us, so rounds stay short and the 2^20-sample
+    chunks of a 3000-tone request are rendered in many tile-aligned pieces; the samples still equal
+    a standalone render of each request."""
+    fs = 280e6
+    reqs = [_request(11, fs, 40, 1 << 16, 16, 5), _request(12, fs, 3000, 1 << 20, 2, 50)]
+    srv = awg.Server(fs, 8 << 30, 64)
+    ids = [srv.submit(r[0], r[1], r[2], r[4], r[5], r[3]) for r in reqs]
+    srv.drain(60000)
+    st = srv.stats()
+    assert st["completed"] == 2, st
+    assert st["rounds"] >= 20, st        # the 2^20 chunks were cut
+    assert st["max_batch"] >= 2, st      # the short request's chunks joined rounds of the long one
+    for rid, r in zip(ids, reqs):
+        got = srv.read(rid, r[4] * r[5])
+        assert np.array_equal(got, _standalone(awg, fs, r)), rid
+        srv.release(rid)
+    srv.close()
