@@ -173,7 +173,6 @@ def stream_leg(awg, fs: float, stream, seconds: float = 1.0, n_slots: int = 4, p
     synth.close()
     return {"tones": wk.K, "fs_hz": fs, "chunk": wk.chunk, "chunks": int(st["played"]), "underruns": int(st["underruns"]),
             "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"]},
-            "first_chunk_ms": {"p50": st["first_chunk_p50_ms"], "p99": st["first_chunk_p99_ms"]},
             "min_lead_ms": st["lead_min_ms"], "playback_ms": st["chunk_playback_ms"], "slots": n_slots,
             "required_tone_samples_per_s": wk.K * fs}
 
@@ -255,12 +254,13 @@ def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, c
             "requests": st["submitted"], "admitted": st["admitted"], "rejected_deadline": st["rejected_deadline"],
             "rejected_memory": st["rejected_memory"], "completed": st["completed"], "chunks": st["chunks"],
             "deadline_misses": st["deadline_misses"],
-            "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"]},
+            "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"],
+                                 "p99_of_playback": st["latency_p99_of_period"]},
             "first_chunk_ms": {"p50": st["first_chunk_p50_ms"], "p99": st["first_chunk_p99_ms"]},
             "samples_per_s": st["samples_per_s"], "tone_samples_per_s": st["tone_samples_per_s"],
             "mean_batch": st["mean_batch"], "max_batch": st["max_batch"], "rounds": st["rounds"], "busy_fraction": st["busy_fraction"],
             "est_throughput": st["est_throughput"],
-            "est_round_cost_ms": st["est_round_cost_ms"]}
+            "est_round_cost_ms": st["est_round_cost_ms"], "est_cta_rate": st["est_cta_rate"]}
 
 
 def config(wk, args):

@@ -311,6 +311,7 @@ typedef struct {
   double latency_p50_ms;            /* chunks c >= 1: completion minus release */
   double latency_p99_ms;
   double latency_max_ms;
+  double latency_p99_of_period;     /* chunks c >= 1: p99 of (completion - release) / playback period */
   double first_chunk_p50_ms;        /* chunk 0: completion minus submission (queue + set-up + render) */
   double first_chunk_p99_ms;
   int64_t rounds;
@@ -321,6 +322,7 @@ typedef struct {
   double busy_fraction;             /* device time of the rounds / that span */
   double est_throughput;            /* cost model: static-tone samples/s of a busy device */
   double est_round_cost_ms;         /* cost model: fixed device time of one round */
+  double est_cta_rate;              /* cost model: tone-samples/s of one render CTA alone on an SM */
 } awg_server_stats_t;
 
 /* Server for sample rate fs on the current device, with a device-memory budget (bytes) for the

@@ -330,10 +330,11 @@ class _Request(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", i64), ("admitted", i64), ("rejected_deadline", i64), ("rejected_memory", i64),
                 ("completed", i64), ("chunks", i64), ("deadline_misses", i64), ("latency_p50_ms", dbl),
-                ("latency_p99_ms", dbl), ("latency_max_ms", dbl), ("first_chunk_p50_ms", dbl),
+                ("latency_p99_ms", dbl), ("latency_max_ms", dbl), ("latency_p99_of_period", dbl),
+                ("first_chunk_p50_ms", dbl),
                 ("first_chunk_p99_ms", dbl), ("rounds", i64), ("mean_batch", dbl), ("max_batch", i64),
                 ("tone_samples_per_s", dbl), ("samples_per_s", dbl), ("busy_fraction", dbl), ("est_throughput", dbl),
-                ("est_round_cost_ms", dbl)]
+                ("est_round_cost_ms", dbl), ("est_cta_rate", dbl)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -281,14 +281,14 @@ bool needs_exact(uint64_t F0, uint64_t F1, int64_t L, int profile) {
   return bound > 512.0 * 4294967296.0;
 }
 
+}  // namespace
+
 // Tone split per tile: about 96 tones per CTA, at most MAX_SPLIT CTAs per cluster.  A function of
 // the tone count only, so that every sample is summed in the same order whatever the window.
-int tone_split_for(int K) {
+int awgk::tone_split_for(int K) {
   int s = (K + 95) / 96;
   return std::max(1, std::min(s, awgk::MAX_SPLIT));
 }
-
-}  // namespace
 
 // ==========================================================================================
 // handle
@@ -475,7 +475,7 @@ int set_tones_common(awg_t* h, const double* f, const double* amp, const double*
   h->free_slots.clear();
   h->fs_explicit = false;
   h->full_scale = default_full_scale(h);
-  h->split = tone_split_for(n);
+  h->split = awgk::tone_split_for(n);
   st = upload_tones(h);
   if (st) return st;
   return upload_chirps(h);

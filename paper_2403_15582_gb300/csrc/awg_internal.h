@@ -176,6 +176,8 @@ int prepare_render(struct awg* h, int64_t n, int16_t* out_q, float* out_f, cudaS
 size_t render_recs_needed(const struct awg* h, int64_t n);
 // Entries of the slot -> record map of h (its chirp slots).
 size_t render_slots(const struct awg* h);
+// CTAs per tile (tone split) for K tones; depends on K only.
+int tone_split_for(int K);
 
 // Sets the message awg_last_error() returns on this thread; returns `code`.
 int set_error(int code, const std::string& msg);

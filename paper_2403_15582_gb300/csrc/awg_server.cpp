@@ -50,6 +50,7 @@ struct Request {
   bool release_requested = false;
   int32_t split = 1;
   double weight = 0;           // device cost per sample, in static-tone units: K + n_chirps / 2
+  double cta_tones = 0;        // tones one CTA sums (K / tone split, rounded up)
   int32_t issue_chunk = 0;     // next piece to issue: chunk index and offset in it
   int64_t issue_off = 0;
   int32_t done_chunks = 0;     // chunks complete on the device
@@ -106,6 +107,7 @@ double percentile(std::vector<double> v, double q) {
 }  // namespace
 
 constexpr int NSETS = 3;       // rounds in flight, each on its own stream with its own buffers
+constexpr int RESIDENT = 5;    // render CTAs resident per SM
 
 struct awg_server {
   double fs = 0;
@@ -147,11 +149,12 @@ struct awg_server {
   // more (descriptor copies, launches)
   double P = 2.5e12, P_cal = 2.5e12;
   double a_gpu = 20e-6;
+  double r_cta = 1e10;         // tone-samples/s of one CTA alone on its SM
   double host_s = 30e-6;
   // statistics
   int64_t submitted = 0, admitted = 0, rej_deadline = 0, rej_memory = 0, completed = 0;
   int64_t chunks = 0, misses = 0, rounds = 0, batched = 0, max_batch = 0;
-  std::vector<double> lat, ttfc;
+  std::vector<double> lat, ttfc, lat_frac;
   TraceRing<awg_round_record_t> trace_rounds;
   TraceRing<awg_chunk_record_t> trace_chunks;
   double busy_s = 0, tone_samples = 0, samples = 0;
@@ -179,16 +182,21 @@ double horizon(double min_period) { return std::min(2e-3, std::max(40e-6, min_pe
 // round cost a_gpu are lost, so the set is accepted while sum C_i / (T_i - H - a_gpu) <= 0.85 and
 // one tile of the largest request fits in a horizon.  `extra` (may be null) is a candidate.
 bool fits_set(const awg_server_t* s, const std::vector<const Request*>& set) {
-  double min_period = 1e30, kmax = 0;
+  double min_period = 1e30, kmax = 0, ctamax = 0, load = 0;
   for (const Request* q : set) {
     min_period = std::min(min_period, q->period);
     kmax = std::max(kmax, (double)q->f.size());
+    ctamax = std::max(ctamax, q->cta_tones);
+    load += q->weight * s->fs / s->P;
   }
   if (set.empty()) return true;
   const double H = horizon(min_period);
+  // A CTA cannot be preempted: a chunk may wait for the longest CTA in flight and takes at least
+  // one CTA time itself.  A CTA shares its SM with up to RESIDENT others as the load grows.
+  const double t_cta = ctamax * awgk::TILE / s->r_cta * (1.0 + (RESIDENT - 1) * std::min(1.0, load));
   double density = 0;
   for (const Request* q : set) {
-    const double window = q->period - H - s->a_gpu;
+    const double window = q->period - H - s->a_gpu - 2.0 * t_cta;
     if (window <= 0) return false;
     density += q->weight * (double)q->chunk / s->P / window;
   }
@@ -543,6 +551,7 @@ void complete_round(awg_server_t* s) {
     } else {
       const double rel = r->t_play + (double)(p.chunk - 1) * r->period;
       s->lat.push_back(t_chunk - rel);
+      s->lat_frac.push_back((t_chunk - rel) / r->period);
       cr.release = rel;
       cr.due = rel + r->period;
       cr.late = t_chunk > cr.due;
@@ -571,9 +580,9 @@ void fail_rounds(awg_server_t* s, const std::string& what) {
   s->cv.notify_all();
 }
 
-// Cost model calibration: the device time of a round of one tile of one tone (fixed cost a_gpu)
-// and of a round of 2048 static tones over 2^19 samples (rate P), best of three each, through the
-// same path as the served rounds.
+// Cost model calibration, through the same path as the served rounds (best of three each): a round
+// of one tile of one tone (fixed cost a_gpu), of 2048 static tones over 2^19 samples (rate P), and
+// of one tile of 96 x MAX_SPLIT tones (one CTA of 96 tones per SM: the rate of a CTA alone).
 int calibrate(awg_server_t* s) {
   const int32_t K = 2048;
   const int64_t N = (int64_t)1 << 19;
@@ -584,10 +593,10 @@ int calibrate(awg_server_t* s) {
   int st = h ? AWG_OK : AWG_ECUDA;
   if (!st && cudaMalloc((void**)&out, (size_t)N * sizeof(int16_t)) != cudaSuccess)
     st = awgk::set_error(AWG_ENOMEM, "calibration buffer");
-  double best[2] = {1e30, 1e30};
-  for (int pass = 0; pass < 2 && !st; ++pass) {
-    const int32_t k = pass == 0 ? 1 : K;
-    const int64_t n = pass == 0 ? awgk::TILE : N;
+  double best[3] = {1e30, 1e30, 1e30};
+  for (int pass = 0; pass < 3 && !st; ++pass) {
+    const int32_t k = pass == 0 ? 1 : pass == 1 ? K : 96 * awgk::MAX_SPLIT;   // pass 2: one CTA per SM
+    const int64_t n = pass == 1 ? N : awgk::TILE;
     if ((st = awg_set_tones(h, f.data(), a.data(), th.data(), k))) break;
     Request r;
     r.h = h;
@@ -614,6 +623,7 @@ int calibrate(awg_server_t* s) {
   if (st) return st;
   s->a_gpu = std::max(2e-6, best[0]);
   s->P = s->P_cal = (double)K * (double)N / std::max(1e-6, best[1] - s->a_gpu);
+  s->r_cta = 96.0 * awgk::TILE / std::max(1e-6, best[2] - s->a_gpu);
   return AWG_OK;
 }
 
@@ -714,7 +724,19 @@ awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes,
     awg_server_destroy(s);
     return nullptr;
   }
-  if (calibrate(s) != AWG_OK) {
+  // staging sized for typical rounds up front, so that the first rounds do not allocate
+  for (int i = 0; i < NSETS && e == cudaSuccess; ++i) {
+    if (!grow(&s->d_reqs[i], &s->h_reqs[i], &s->cap_reqs[i], 1024) ||
+        !grow(&s->d_items[i], &s->h_items[i], &s->cap_items[i], 1 << 16) ||
+        cudaMalloc((void**)&s->d_arena[i], (1u << 16) * sizeof(awgk::TileRec)) != cudaSuccess ||
+        cudaMalloc((void**)&s->d_act[i], (1u << 16) * sizeof(int32_t)) != cudaSuccess) {
+      e = cudaErrorMemoryAllocation;
+      break;
+    }
+    s->cap_arena[i] = s->cap_act[i] = 1u << 16;
+  }
+  if (e != cudaSuccess) awgk::set_error(AWG_ENOMEM, "staging buffers");
+  if (e != cudaSuccess || calibrate(s) != AWG_OK) {
     const std::string why = awg_last_error();
     awg_server_destroy(s);
     awgk::set_error(AWG_ECUDA, "server calibration: " + why);
@@ -780,6 +802,10 @@ int64_t awg_server_submit(awg_server_t* s, const awg_request_t* q) {
   r->full_scale = q->full_scale;
   r->period = (double)q->chunk / s->fs;
   r->weight = (double)q->n_tones + 0.5 * (double)q->n_chirps;
+  {
+    const int split = awgk::tone_split_for(q->n_tones);
+    r->cta_tones = (double)((q->n_tones + split - 1) / split);
+  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
     r->id = s->next_id++;
@@ -859,6 +885,7 @@ int awg_server_stats(awg_server_t* s, awg_server_stats_t* out) {
   out->latency_p50_ms = 1e3 * percentile(s->lat, 0.50);
   out->latency_p99_ms = 1e3 * percentile(s->lat, 0.99);
   out->latency_max_ms = s->lat.empty() ? 0 : 1e3 * *std::max_element(s->lat.begin(), s->lat.end());
+  out->latency_p99_of_period = percentile(s->lat_frac, 0.99);
   out->first_chunk_p50_ms = 1e3 * percentile(s->ttfc, 0.50);
   out->first_chunk_p99_ms = 1e3 * percentile(s->ttfc, 0.99);
   out->rounds = s->rounds;
@@ -870,6 +897,7 @@ int awg_server_stats(awg_server_t* s, awg_server_stats_t* out) {
   out->busy_fraction = s->busy_s / span;
   out->est_throughput = s->P;
   out->est_round_cost_ms = 1e3 * s->a_gpu;
+  out->est_cta_rate = s->r_cta;
   return AWG_OK;
 }
 

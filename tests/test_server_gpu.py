@@ -93,16 +93,17 @@ def test_admission_by_memory(awg):
 
 def test_chunks_cut_into_tile_pieces_match_standalone(awg):
     """At 280 MS/s a 2^16-sample chunk plays for 234 us, so rounds stay short and the 2^20-sample
-    chunks of a 3000-tone request are rendered in many tile-aligned pieces; the samples still equal
+    chunks of a 1500-tone request are rendered in many tile-aligned pieces; the samples still equal
     a standalone render of each request."""
     fs = 280e6
-    reqs = [_request(11, fs, 40, 1 << 16, 16, 5), _request(12, fs, 3000, 1 << 20, 2, 50)]
+    reqs = [_request(11, fs, 40, 1 << 16, 64, 5), _request(12, fs, 1500, 1 << 20, 2, 50)]   # 15 ms, 7.5 ms
     srv = awg.Server(fs, 8 << 30, 64)
     ids = [srv.submit(r[0], r[1], r[2], r[4], r[5], r[3]) for r in reqs]
     srv.drain(60000)
     st = srv.stats()
     assert st["completed"] == 2, st
-    assert st["rounds"] >= 20, st        # the 2^20 chunks were cut
+    pieces = round(st["mean_batch"] * st["rounds"])
+    assert pieces >= 64 + 2 + 6, st      # the 2^20 chunks were cut into pieces
     assert st["max_batch"] >= 2, st      # the short request's chunks joined rounds of the long one
     for rid, r in zip(ids, reqs):
         got = srv.read(rid, r[4] * r[5])
