@@ -186,13 +186,14 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def table_leg(awg, stream, reps: int = 3):
-    """Periodic 10,000-tone table of 2^24 samples: split-precision tcgen05 GEMM (FP16 and BF16 hi+lo)
-    against the direct-sum render of the same record on the same GPU."""
+def table_leg(awg, stream, reps: int = 3, K: int = 10000, log2_len: int = 24):
+    """Periodic K-tone table of 2^log2_len samples (default 10,000 tones, 2^24): split-precision
+    tcgen05 GEMM (FP16 and BF16 hi+lo) against the direct-sum render of the same record on the same
+    GPU."""
     import numpy as np
     import torch
     from paper_2403_15582_gb300 import workloads as wl
-    wk = wl.table_10000(seed=0)
+    wk = wl.table_10000(seed=0, K=K, log2_len=log2_len)
     lg = wk.grid_log2
     N = 1 << lg
     synth = awg.Synth(wk.fs)
@@ -280,6 +281,8 @@ def main():
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-table", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--table-case", default="10000,24",
+                    help="tones,log2 samples of the table leg (a smaller case for profiling)")
     args = ap.parse_args()
     wk = workload()
     if args.impl == "reference":
@@ -404,7 +407,8 @@ def main():
                                "render": float(np.sum(render_ms)) / args.steps},
     }
     if not args.no_table:
-        line["table"] = table_leg(awg, stream)
+        tk, tl = (int(v) for v in args.table_case.split(","))
+        line["table"] = table_leg(awg, stream, K=tk, log2_len=tl)
     if not args.no_served:
         line["served"] = {f"rho{r}": served_leg(awg, rho=r) for r in (0.5, 0.8)}
     if not args.no_stream:

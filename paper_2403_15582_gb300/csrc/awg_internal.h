@@ -15,7 +15,7 @@ namespace awgk {
 constexpr int RUN = 32;
 constexpr int NT = 128;
 constexpr int TILE = RUN * NT;     // 4096 samples
-constexpr int STAGE = 16;          // tones staged in shared memory at a time (double-buffered)
+constexpr int STAGE = 32;          // tones staged in shared memory at a time (double-buffered)
 constexpr int MAX_SPLIT = 16;      // cluster size limit (non-portable 16 on sm_100-class parts)
 constexpr int MAX_ACTIVE_PER_LAUNCH = 1024;
 
