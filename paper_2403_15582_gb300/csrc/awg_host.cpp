@@ -315,7 +315,7 @@ struct awg {
   size_t cap_trace = 0;
   uint32_t* d_tab = nullptr;           // exact per-sample phases of TONE_EXACT chirps
   size_t cap_tab = 0;
-  uint16_t* d_gemm = nullptr;          // table GEMM operands: A hi, A lo, B hi, B lo
+  uint16_t* d_gemm = nullptr;          // table GEMM B operand: hi, lo (A is generated in the kernel)
   size_t cap_gemm = 0;
   int64_t cursor = 0;
   double full_scale = 0;
@@ -1008,8 +1008,8 @@ int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q
   }
   const int64_t M = (int64_t)1 << (log2_len - 8);
   const size_t Kp = awgk::table_kp(std::max(h->K, 1));
-  const size_t a_elems = (size_t)M * Kp, b_elems = (size_t)256 * Kp;
-  int st = ensure(&h->d_gemm, &h->cap_gemm, 2 * a_elems + 2 * b_elems, h, "table GEMM operands");
+  const size_t b_elems = (size_t)256 * Kp;
+  int st = ensure(&h->d_gemm, &h->cap_gemm, 2 * b_elems, h, "table GEMM operands");
   if (st) return st;
   awgk::TableArgs2 t;
   t.tones = h->d_tones;
@@ -1017,10 +1017,8 @@ int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q
   t.M = M;
   t.nb_log2 = 8;
   t.precision = precision;
-  t.a_hi = h->d_gemm;
-  t.a_lo = h->d_gemm + a_elems;
-  t.b_hi = h->d_gemm + 2 * a_elems;
-  t.b_lo = h->d_gemm + 2 * a_elems + b_elems;
+  t.b_hi = h->d_gemm;
+  t.b_lo = h->d_gemm + b_elems;
   t.out_q = out_q;
   t.out_f = out_f;
   t.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;

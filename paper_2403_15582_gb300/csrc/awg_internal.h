@@ -145,9 +145,7 @@ struct TableArgs2 {
   int64_t M;              // rows: record length / 256
   int32_t nb_log2;        // log2 of the columns (8: 256 samples per row)
   int32_t precision;      // 0 BF16, 1 FP16 hi+lo operands
-  void* a_hi;             // M x Kp
-  void* a_lo;
-  void* b_hi;             // 256 x Kp
+  void* b_hi;             // 256 x Kp (the A operand is generated inside the GEMM kernel)
   void* b_lo;
   int16_t* out_q;
   float* out_f;
@@ -155,7 +153,7 @@ struct TableArgs2 {
   int32_t* status;
 };
 size_t table_kp(int K);  // padded inner dimension (2K rounded up to the K tile)
-cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s);   // operand halves
+cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s);   // B operand halves
 cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s);   // tensor-core GEMM + epilogue
 
 }  // namespace awgk

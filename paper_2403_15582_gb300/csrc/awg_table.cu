@@ -10,14 +10,19 @@
 // memory and quantises in the epilogue.
 //
 // Kernel structure: a cluster of S CTAs per 128-row tile of X splits the K dimension (fewer FP32
-// accumulations per chain); each CTA (192 threads) has
-//   warp 0   TMA producer: 2-stage ring of {A_hi, A_lo (128 x 64), B_hi, B_lo (256 x 64)} tiles,
-//            128-byte swizzle, mbarrier transaction counts
-//   warp 1   allocates 256 TMEM columns; lane 0 issues tcgen05.mma (M 128, N 256, K 16) x 3 passes
-//            x 4 k-steps per stage, commits each stage back to the producer
-//   warps 2-5 epilogue: tcgen05.ld 32x32b of both accumulators into a padded FP32 partial tile in
-//            shared memory; then the cluster sums the S partial tiles through distributed shared
-//            memory in rank order, and each CTA scales, rounds, clamps and stores its rows.
+// accumulations per chain); each CTA (192 threads) has a 2-stage ring of
+// {A_hi, A_lo (128 x 64), B_hi, B_lo (256 x 64)} tiles in the 128-byte-swizzled K-major layout:
+//   warp 0   TMA producer of the B tiles (prepared once per call, 256 x 2K, L2-resident),
+//            mbarrier transaction counts
+//   warp 1   allocates 512 TMEM columns; lane 0 issues tcgen05.mma (M 128, N 256, K 16) x 3 passes
+//            x 4 k-steps per stage, commits each stage back to the producers
+//   warps 2-5 generate the A tiles in shared memory (one tone per lane, every fourth row per warp:
+//            A_k sin a_k(n1), A_k cos a_k(n1) from the exact phase word, SFU sine and cosine, hi + lo
+//            split), so the M x 2K A
+//            operand never exists in HBM; then the epilogue: tcgen05.ld 32x32b of both
+//            accumulators into a padded FP32 partial tile in shared memory; the cluster sums the S
+//            partial tiles through distributed shared memory in rank order, and each CTA scales,
+//            rounds, clamps and stores its rows.
 // Every wait is bounded (about 2 s); on a timeout the CTA records AWG_ETIMEOUT, lets in-flight
 // copies and MMAs drain (bounded), frees its TMEM and exits.
 #include <cooperative_groups.h>
@@ -115,11 +120,76 @@ struct TableGemmArgs {
   float scale;           // 32767 / FS
   int32_t* status;
   uint32_t idesc;
+  const ToneRec* tones;  // A operand source: phase word, frequency word, amplitude
+  int32_t K;
+  int32_t nb_log2;       // row n1 starts at sample n1 << nb_log2
 };
 
+template <typename T>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi);
+template <>
+__device__ __forceinline__ uint32_t pack2<__nv_bfloat16>(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+template <>
+__device__ __forceinline__ uint32_t pack2<__half>(float lo, float hi) {
+  const __half2 v = __floats2half2_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+template <typename T>
+__device__ __forceinline__ float2 unpack2(uint32_t u);
+template <>
+__device__ __forceinline__ float2 unpack2<__nv_bfloat16>(uint32_t u) {
+  return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xFFFF0000u));
+}
+template <>
+__device__ __forceinline__ float2 unpack2<__half>(uint32_t u) {
+  const __half2 v = *reinterpret_cast<const __half2*>(&u);
+  return __half22float2(v);
+}
+
+// The A tile of one stage for one generator warp: lane j takes tone kt0 + j (its phase word,
+// frequency word and amplitude, loaded once), warp g the rows g, g + 4, ..., g + 124; for each row
+// n1 it forms the hi and lo halves of (A_k sin a, A_k cos a), a = 2 pi (Phi0_k + n1 NB F_k) / 2^64,
+// stepping the exact phase word by 4 NB F_k from row to row.  The pair is one 32-bit word at byte
+// 4 (j mod 4) of 16-byte chunk j / 4 of the row, which the 128-byte swizzle moves to chunk
+// (j / 4) ^ (row mod 8).  The sine and cosine take the top 32 bits of the phase word as a signed
+// turn on the SFU (|error| < 5e-7).
+template <typename T>
+__device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint32_t row0, int g, int lane,
+                                           uint32_t tile_hi, uint32_t tile_lo) {
+  const int k = kt0 + lane;
+  uint64_t w = 0, step = 0;
+  float amp = 0.f;
+  if (k < a.K) {
+    const ToneRec* t = a.tones + k;
+    const uint64_t f8 = __ldg(&t->F) << a.nb_log2;
+    w = __ldg(&t->phi_ref) + (uint64_t)(row0 + (uint32_t)g) * f8;
+    step = f8 << 2;
+    amp = __ldg(&t->A);
+  }
+  const uint32_t col = (uint32_t)(lane & 3) * 4u;
+  const uint32_t chunk = (uint32_t)(lane >> 2);
+#pragma unroll 8
+  for (int i = 0; i < TM / 4; ++i) {
+    const uint32_t r = (uint32_t)(g + 4 * i);
+    float sn, cs;
+    __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
+    const float sv = amp * sn, cv = amp * cs;
+    const uint32_t hv = pack2<T>(sv, cv);
+    const float2 h = unpack2<T>(hv);
+    const uint32_t lv = pack2<T>(sv - h.x, cv - h.y);
+    const uint32_t off = r * 128u + ((chunk ^ (r & 7u)) << 4) + col;
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(tile_hi + off), "r"(hv) : "memory");
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(tile_lo + off), "r"(lv) : "memory");
+    w += step;
+  }
+}
+
+template <typename T>
 __global__ void __launch_bounds__(192, 1)
-    table_gemm_kernel(const __grid_constant__ CUtensorMap mA_hi, const __grid_constant__ CUtensorMap mA_lo,
-                      const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
+    table_gemm_kernel(const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
                       const __grid_constant__ TableGemmArgs a) {
   extern __shared__ uint8_t dyn_smem[];
   __shared__ alignas(8) uint64_t bars[2 * NSTAGE + 1];   // full[2], empty[2], done
@@ -139,7 +209,7 @@ __global__ void __launch_bounds__(192, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(full0 + 8 * s, 1);
+      mbar_init(full0 + 8 * s, 1 + 4);   // the B copies' transaction arrive + four generator warps
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(done, 1);
@@ -167,10 +237,8 @@ __global__ void __launch_bounds__(192, 1)
       }
       if (s_fail) break;
       const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
-      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+      mbar_expect_tx(full0 + 8 * s, 2 * B_TILE);
       const int kx = (kb0 + kb) * TK;
-      tma_load_2d(st, &mA_hi, kx, row0, full0 + 8 * s);
-      tma_load_2d(st + A_TILE, &mA_lo, kx, row0, full0 + 8 * s);
       tma_load_2d(st + 2 * A_TILE, &mB_hi, kx, 0, full0 + 8 * s);
       tma_load_2d(st + 2 * A_TILE + B_TILE, &mB_lo, kx, 0, full0 + 8 * s);
       issued = kb + 1;
@@ -206,6 +274,23 @@ __global__ void __launch_bounds__(192, 1)
     }
     mma_commit(done);               // all MMAs issued so far complete -> epilogue (also on abort)
   } else if (warp >= 2) {
+    // ---------------- A operand generation ----------------
+    {
+      const int g = warp - 2;   // rows g, g + 4, ...
+      for (int kb = 0; kb < n_kb; ++kb) {
+        const int s = kb % NSTAGE;
+        if (kb >= NSTAGE && !mbar_wait(empty0 + 8 * s, (uint32_t)(((kb / NSTAGE) - 1) & 1))) {
+          s_fail = 1;
+          break;
+        }
+        if (s_fail) break;
+        const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
+        gen_a_tile<T>(a, (kb0 + kb) * (TK / 2), (uint32_t)row0, g, lane, st, st + A_TILE);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full0 + 8 * s) : "memory");
+      }
+    }
     // ---------------- epilogue ----------------
     const bool ok = mbar_wait(done, 0);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -303,25 +388,6 @@ __device__ __forceinline__ void split_store(T* hi, T* lo, int64_t i, float v) {
   lo[i] = to_half<T>(v - from_half<T>(h));
 }
 
-// Aop[n1][2k] = A_k sin a_k(n1), Aop[n1][2k+1] = A_k cos a_k(n1); zero beyond 2K.
-template <typename T>
-__global__ void prep_a_kernel(const ToneRec* tones, int K, int64_t M, int64_t Kp, int NBlog2, T* hi, T* lo) {
-  const int64_t pairs = Kp / 2;
-  const int64_t total = M * pairs;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n1 = i / pairs, k = i - n1 * pairs;
-    float s = 0.f, c = 0.f, A = 0.f;
-    if (k < K) {
-      const ToneRec& t = tones[k];
-      const uint64_t w = t.phi_ref + (((uint64_t)n1 << NBlog2) * t.F);
-      sincos_word(w, &s, &c);
-      A = t.A;
-    }
-    split_store<T>(hi, lo, n1 * Kp + 2 * k, A * s);
-    split_store<T>(hi, lo, n1 * Kp + 2 * k + 1, A * c);
-  }
-}
-
 // Bt[n2][2k] = cos b_k(n2), Bt[n2][2k+1] = sin b_k(n2) (the B operand stored K-major).
 template <typename T>
 __global__ void prep_b_kernel(const ToneRec* tones, int K, int64_t Kp, T* hi, T* lo) {
@@ -356,19 +422,13 @@ cudaError_t encode_2d(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt,
 size_t table_kp(int K) { return (((size_t)2 * K + TK - 1) / TK) * TK; }
 
 cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s) {
-  const int64_t M = t.M;
   const int64_t Kp = (int64_t)table_kp(t.K);
-  const bool bf16 = (t.precision == 0);
   const int threads = 256;
-  const int blocks = 152 * 8;
-  if (bf16) {
-    prep_a_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(t.tones, t.K, M, Kp, t.nb_log2, (__nv_bfloat16*)t.a_hi,
-                                                           (__nv_bfloat16*)t.a_lo);
+  const int blocks = 152 * 4;
+  if (t.precision == 0)
     prep_b_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(t.tones, t.K, Kp, (__nv_bfloat16*)t.b_hi, (__nv_bfloat16*)t.b_lo);
-  } else {
-    prep_a_kernel<__half><<<blocks, threads, 0, s>>>(t.tones, t.K, M, Kp, t.nb_log2, (__half*)t.a_hi, (__half*)t.a_lo);
+  else
     prep_b_kernel<__half><<<blocks, threads, 0, s>>>(t.tones, t.K, Kp, (__half*)t.b_hi, (__half*)t.b_lo);
-  }
   return cudaGetLastError();
 }
 
@@ -386,9 +446,7 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
     enc = (EncodeTiledFn)fn;
   }
   const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  CUtensorMap mAh, mAl, mBh, mBl;
-  if ((e = encode_2d(enc, &mAh, dt, t.a_hi, (uint64_t)Kp, (uint64_t)M, TK, TM)) != cudaSuccess) return e;
-  if ((e = encode_2d(enc, &mAl, dt, t.a_lo, (uint64_t)Kp, (uint64_t)M, TK, TM)) != cudaSuccess) return e;
+  CUtensorMap mBh, mBl;
   if ((e = encode_2d(enc, &mBh, dt, t.b_hi, (uint64_t)Kp, (uint64_t)TN, TK, TN)) != cudaSuccess) return e;
   if ((e = encode_2d(enc, &mBl, dt, t.b_lo, (uint64_t)Kp, (uint64_t)TN, TK, TN)) != cudaSuccess) return e;
 
@@ -398,12 +456,16 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   ga.out_f = t.out_f;
   ga.scale = t.scale;
   ga.status = t.status;
+  ga.tones = t.tones;
+  ga.K = t.K;
+  ga.nb_log2 = t.nb_log2;
   // instruction descriptor: FP32 accumulate, A/B BF16 (1) or FP16 (0), both K-major, N/8, M/16
   const uint32_t fmt = bf16 ? 1u : 0u;
   ga.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   const size_t smem = (size_t)NSTAGE * STAGE_BYTES + 1024;
   static_assert((size_t)TM * PART_STRIDE * 4 <= (size_t)NSTAGE * STAGE_BYTES, "partial tile fits in the stages");
-  e = cudaFuncSetAttribute(table_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = bf16 ? table_gemm_kernel<__nv_bfloat16> : table_gemm_kernel<__half>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // K split over a cluster of up to 4 CTAs per 128-row tile
   const unsigned split = (unsigned)(ga.n_kb < 4 ? ga.n_kb : 4);
@@ -419,7 +481,7 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, table_gemm_kernel, mAh, mAl, mBh, mBl, ga);
+  return cudaLaunchKernelEx(&cfg, kern, mBh, mBl, ga);
 }
 
 }  // namespace awgk
