@@ -146,6 +146,17 @@ int awg_render(awg_t* h, int64_t n, int16_t* out, void* stream);
 /* As awg_render, also writing the FP32 sum x[n] (unscaled) to out_f32 (out_q may be NULL). */
 int awg_render_f32(awg_t* h, int64_t n, float* out_f32, int16_t* out_q, void* stream);
 
+/* Render n_chunks consecutive chunks of `chunk` samples (the chunk loop of Sec. IV: the cursor
+ * advances chunk by chunk) into out[0 .. n_chunks * chunk), with the same samples as n_chunks
+ * calls of awg_render.  The chunks are issued as one pipelined sequence: the chirp set-up of chunk
+ * c+1 and the start of its render overlap the end of chunk c's render on the device (programmatic
+ * dependent launch; two record buffers used alternately, guarded by device counters), and a final
+ * join kernel restores plain stream order for later work on `stream`.  out is device memory or
+ * mapped pinned host memory.  AWG_EINVAL for chunk < 1, n_chunks < 0 or overflow.  A wait that
+ * times out inside the sequence (about 2 s) sets the device status to AWG_ETIMEOUT (see
+ * awg_device_status). */
+int awg_render_chunks(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, void* stream);
+
 /* Phase words Phi_k(sample) of the first n tones (n <= tone count), computed on the device by the
  * exact closed form (192-bit, the function that seeds every render tile) and copied to
  * out_host.  Synchronous. */

@@ -52,6 +52,7 @@ SIGNATURES = [
     ("awg_cursor", i64, [P]),
     ("awg_render", ctypes.c_int, [P, i64, P, P]),
     ("awg_render_f32", ctypes.c_int, [P, i64, P, P, P]),
+    ("awg_render_chunks", ctypes.c_int, [P, i64, i32, P, P]),
     ("awg_phase_words", ctypes.c_int, [P, i64, P, i32]),
     ("awg_render_phases", ctypes.c_int, [P, i32, i64, i32, P]),
     ("awg_tone_split", i32, [P]),
@@ -223,6 +224,10 @@ class Synth:
 
     def render(self, n: int, out, stream=None):
         _check(lib().awg_render(self._h, int(n), _ptr(out), _stream_ptr(stream)))
+
+    def render_chunks(self, chunk: int, n_chunks: int, out, stream=None):
+        """n_chunks consecutive chunks of `chunk` samples into out, as one pipelined sequence."""
+        _check(lib().awg_render_chunks(self._h, int(chunk), int(n_chunks), _ptr(out), _stream_ptr(stream)))
 
     def table_gemm(self, log2_len: int, precision: int, out_q=None, out_f=None, stream=None):
         _check(lib().awg_table_gemm(self._h, int(log2_len), int(precision), _ptr(out_q), _ptr(out_f), _stream_ptr(stream)))

@@ -308,6 +308,14 @@ struct awg {
   size_t cap_chirps = 0;
   TileRec* d_recs = nullptr;          // chirp tile records of the current render window
   size_t cap_recs = 0;
+  // pipelined chunk sequences (awg_render_chunks): the tile records of a group of chunks, and a
+  // device counter of the render CTAs that have stored their samples
+  TileRec* d_seq_recs = nullptr;
+  size_t cap_seq_recs = 0;
+  int32_t* d_seq_act = nullptr;
+  size_t cap_seq_act = 0;
+  unsigned long long* d_seq_exit = nullptr;
+  unsigned long long seq_exit_target = 0;
   int32_t* d_status = nullptr;
   uint64_t* d_words = nullptr;
   size_t cap_words = 0;
@@ -677,6 +685,136 @@ int awgk::prepare_render(awg_t* h, int64_t n, int16_t* out_q, float* out_f, cuda
   return AWG_OK;
 }
 
+namespace {
+
+// Chirp slots active in the window [c, c + n) (tile-aligned span), excluding exact-table chirps.
+std::vector<int32_t> active_slots(const awg_t* h, int64_t c, int64_t n, int64_t* tile0, int32_t* n_tiles) {
+  const int64_t t0 = c / awgk::TILE, t1 = (c + n - 1) / awgk::TILE;
+  const int64_t span0 = t0 * awgk::TILE, span1 = (t1 + 1) * awgk::TILE - 1;
+  std::vector<int32_t> active;
+  for (size_t sl = 0; sl < h->chirps.size(); ++sl) {
+    const ChirpRec& cr = h->chirps[sl];
+    if (cr.tone < 0 || (cr.flags & awgk::TONE_EXACT)) continue;
+    if (cr.n_s <= span1 && cr.n_s + cr.L >= span0) active.push_back((int32_t)sl);
+  }
+  *tile0 = t0;
+  *n_tiles = (int32_t)(t1 - t0 + 1);
+  return active;
+}
+
+// n_chunks consecutive chunk renders, pipelined.  The chunks are taken in groups whose chirp tile
+// records fit a fixed budget; for each group one set-up launch computes the records of every
+// chunk of the group (in stream order: it waits for everything before it), then the chunk renders
+// follow with programmatic dependent launch: the first waits for the set-up, and each later one
+// may start as soon as every CTA of the one before has started, so a render's tail overlaps the
+// next render's start (a chunk is one wave of the device or less at typical sizes).  A join kernel
+// (stream order, then a bounded wait on a device counter of render CTAs that stored their
+// samples) ends each group, so the next group's set-up and later work on the stream see every
+// chunk complete.
+constexpr size_t SEQ_RECORD_BUDGET = (size_t)1 << 21;   // 2M records (352 MiB) per group
+
+int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, cudaStream_t s) {
+  cudaError_t e;
+  if (!h->d_seq_exit) {
+    if (cudaMalloc((void**)&h->d_seq_exit, sizeof(unsigned long long)) != cudaSuccess)
+      return fail(AWG_ENOMEM, "cudaMalloc sequence counter");
+    if ((e = cudaMemset(h->d_seq_exit, 0, sizeof(unsigned long long))) != cudaSuccess)
+      return cuda_fail(e, "sequence counter");
+  }
+  const int64_t c0 = h->cursor;
+  struct Group {
+    int32_t g0, g1;
+    int64_t tile0;
+    int32_t n_tiles;
+    std::vector<int32_t> active;
+  };
+  std::vector<Group> groups;
+  size_t max_recs = 1;
+  for (int32_t g0 = 0; g0 < n_chunks;) {
+    // the largest group from g0 whose records fit the budget (at least one chunk)
+    Group g;
+    g.g0 = g0;
+    g.g1 = g0 + 1;
+    g.active = active_slots(h, c0 + (int64_t)g0 * chunk, chunk, &g.tile0, &g.n_tiles);
+    while (g.g1 < n_chunks) {
+      int64_t t0;
+      int32_t nt;
+      std::vector<int32_t> a2 = active_slots(h, c0 + (int64_t)g0 * chunk, (int64_t)(g.g1 + 1 - g0) * chunk, &t0, &nt);
+      if (a2.size() * (size_t)nt > SEQ_RECORD_BUDGET || nt > INT32_MAX / awgk::MAX_SPLIT) break;
+      g.active.swap(a2);
+      g.tile0 = t0;
+      g.n_tiles = nt;
+      ++g.g1;
+    }
+    max_recs = std::max(max_recs, g.active.size() * (size_t)g.n_tiles);
+    g0 = g.g1;
+    groups.push_back(std::move(g));
+  }
+  int st = ensure(&h->d_seq_recs, &h->cap_seq_recs, max_recs, h, "tile records");
+  if (st) return st;
+  st = ensure(&h->d_seq_act, &h->cap_seq_act, std::max<size_t>(1, h->chirps.size()), h, "slot map");
+  if (st) return st;
+  if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
+  for (const Group& grp : groups) {
+    const int32_t g0 = grp.g0, g1 = grp.g1;
+    const int64_t tile0 = grp.tile0;
+    const int32_t n_tiles = grp.n_tiles;
+    const std::vector<int32_t>& active = grp.active;
+    for (size_t b = 0; b < active.size(); b += awgk::MAX_ACTIVE_PER_LAUNCH) {
+      awgk::PrepArgs pa;
+      std::memset(&pa, 0, sizeof(pa));
+      pa.chirps = h->d_chirps;
+      pa.recs = h->d_seq_recs;
+      pa.act_of_slot = h->d_seq_act;
+      pa.tile0 = tile0;
+      pa.n_tiles = n_tiles;
+      pa.n_active = (int32_t)std::min<size_t>(awgk::MAX_ACTIVE_PER_LAUNCH, active.size() - b);
+      pa.act_base = (int32_t)b;
+      std::memcpy(pa.W, h->W, sizeof(pa.W));
+      std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
+      for (int i = 0; i < pa.n_active; ++i) pa.slots[i] = active[b + (size_t)i];
+      if ((e = awgk::launch_prep(pa, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+    }
+    for (int32_t c = g0; c < g1; ++c) {
+      const int64_t wc = c0 + (int64_t)c * chunk;
+      const int64_t t_first = wc / awgk::TILE, t_last = (wc + chunk - 1) / awgk::TILE;
+      awgk::RenderArgs ra;
+      std::memset(&ra, 0, sizeof(ra));
+      ra.tones = h->d_tones;
+      ra.exact_tab = h->d_tab;
+      ra.chirps = h->d_chirps;
+      ra.recs = h->d_seq_recs;
+      ra.act_of_slot = h->d_seq_act;
+      ra.rec_stride = n_tiles;
+      ra.rec_tile0 = (int32_t)(t_first - tile0);
+      ra.K = h->K;
+      ra.split = h->split;
+      ra.tile0 = t_first;
+      ra.n_tiles = (int32_t)(t_last - t_first + 1);
+      ra.win_start = wc;
+      ra.win_end = wc + chunk;
+      ra.out_q = out + (size_t)c * (size_t)chunk;
+      ra.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
+      ra.status = h->d_status;
+      std::memcpy(ra.inv_odd, h->inv_odd, sizeof(ra.inv_odd));
+      ra.pdl = c == g0 ? 1 : 2;
+      ra.exit_ctr = h->d_seq_exit;
+      if ((e = awgk::launch_render(ra, s)) != cudaSuccess) return cuda_fail(e, "render launch");
+      h->seq_exit_target += (unsigned long long)ra.n_tiles * (unsigned long long)h->split;
+    }
+    if ((e = awgk::launch_join(h->d_seq_exit, h->seq_exit_target, h->d_status, s)) != cudaSuccess)
+      return cuda_fail(e, "join launch");
+  }
+  if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
+  if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
+  h->timed = true;
+  h->have_done = true;
+  h->cursor = c0 + (int64_t)n_chunks * chunk;
+  return AWG_OK;
+}
+
+}  // namespace
+
 // ==========================================================================================
 // C ABI
 // ==========================================================================================
@@ -759,6 +897,9 @@ void awg_destroy(awg_t* h) {
   cudaFree(h->d_chirps);
   cudaFree(h->d_act);
   cudaFree(h->d_recs);
+  cudaFree(h->d_seq_recs);
+  cudaFree(h->d_seq_act);
+  cudaFree(h->d_seq_exit);
   cudaFree(h->d_status);
   cudaFree(h->d_words);
   cudaFree(h->d_trace);
@@ -913,6 +1054,23 @@ int awg_render(awg_t* h, int64_t n, int16_t* out, void* stream) {
 int awg_render_f32(awg_t* h, int64_t n, float* out_f32, int16_t* out_q, void* stream) {
   if (n > 0 && !out_f32) return fail(AWG_EINVAL, "null output");
   return render_impl(h, n, out_f32, out_q, stream);
+}
+
+int awg_render_chunks(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, void* stream) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (chunk < 1 || n_chunks < 0) return fail(AWG_EINVAL, "chunk must be >= 1 and n_chunks >= 0");
+  if (n_chunks == 0) return AWG_OK;
+  if (!out) return fail(AWG_EINVAL, "null output");
+  if (chunk > (INT64_MAX - h->cursor) / n_chunks) return fail(AWG_EINVAL, "sample index overflow");
+  if (chunk / awgk::TILE + 2 > (int64_t)(INT32_MAX / awgk::MAX_SPLIT)) return fail(AWG_EINVAL, "chunk too long");
+  if (n_chunks == 1 || h->profiling) {   // per-call profiling events would split the pipeline
+    for (int32_t c = 0; c < n_chunks; ++c) {
+      const int st = render_impl(h, chunk, nullptr, out + (size_t)c * (size_t)chunk, stream);
+      if (st) return st;
+    }
+    return AWG_OK;
+  }
+  return render_chunks_impl(h, chunk, n_chunks, out, (cudaStream_t)stream);
 }
 
 int awg_phase_words(awg_t* h, int64_t sample, uint64_t* out_host, int32_t n) {

@@ -90,6 +90,15 @@ struct RenderArgs {
   float scale;            // 32767 / FS
   int32_t* status;
   uint64_t inv_odd[3][3];
+  // record rows: the records of active chirp a for window tile t are at recs[a * rec_stride +
+  // rec_tile0 + t] (rec_stride 0: n_tiles, the render's own set-up)
+  int32_t rec_stride;
+  int32_t rec_tile0;
+  // pipelined chunk sequences (otherwise 0 / null): pdl 1 waits for the preceding kernel (the
+  // records' set-up) and then lets the next kernel launch early; pdl 2 only lets it launch early
+  // (no data from the preceding kernel); each CTA adds 1 to *exit_ctr once its samples are stored
+  int32_t pdl;
+  unsigned long long* exit_ctr;
 };
 
 struct PhaseArgs {
@@ -125,6 +134,8 @@ struct TableArgs {      // exact per-sample 32-bit phases of one short chirp, m 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_exact_table(const TableArgs& a, int64_t L, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
+cudaError_t launch_join(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status,
+                        cudaStream_t s);
 // items[i] = (request index into reqs, window tile); every request has split == `split`.
 cudaError_t launch_render_batch(const RenderArgs* reqs, const int2* items, int n_items, int split, cudaStream_t s);
 cudaError_t launch_phase_words(const PhaseArgs& a, cudaStream_t s);

@@ -22,6 +22,7 @@
 // signed fraction of a turn (round to nearest) and runs on the SFU (__sinf in [-pi, pi)).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cstdint>
 
 #include "awg_internal.h"
@@ -371,6 +372,24 @@ __device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const Pre
   }
 }
 
+// Programmatic dependent launch (pipelined chunk sequences): the next kernel in the stream may
+// start once every CTA of this one has passed launch_dependents; wait blocks until the preceding
+// kernel has completed and its memory is visible.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Bounded wait (~2 s) until a device counter reaches target; false on timeout.
+__device__ bool wait_counter(const unsigned long long* ctr, unsigned long long target) {
+  const volatile unsigned long long* v = ctr;
+  if (*v >= target) return true;
+  const uint64_t t0 = global_ns();
+  while (*v < target) {
+    if (global_ns() - t0 > 2000000000ull) return false;
+    __nanosleep(256);
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(128) prep_kernel(const __grid_constant__ PrepArgs a) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)a.n_active * a.n_tiles;
@@ -486,6 +505,12 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
 #pragma unroll
   for (int r = 0; r < RUN; ++r) acc[r] = 0.f;
 
+  if (a.pdl == 1) {   // pipelined sequence: the records' set-up (the preceding kernel) is complete
+    pdl_wait();         // before the next render may start (it relies on the same set-up)
+    pdl_launch_dependents();
+  } else if (a.pdl == 2) {
+    pdl_launch_dependents();
+  }
   if (tid == 0) {
 #pragma unroll
     for (int b = 0; b < 4; ++b) mbar_init(&s_bar[b], 1);
@@ -532,7 +557,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
         d.kind = (inside && !exact) ? ((tr.flags & TONE_LINEAR) ? DESC_LINEAR : DESC_MINJERK) : DESC_MIXED;
         if (!exact) {
           need = true;
-          src = a.recs + (int64_t)a.act_of_slot[tr.slot] * a.n_tiles + tile;
+          src = a.recs + (int64_t)a.act_of_slot[tr.slot] * (a.rec_stride ? a.rec_stride : a.n_tiles) + a.rec_tile0 + tile;
         }
       }
       s_desc[b][tid] = d;
@@ -584,26 +609,27 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
             acc[r] = fmaf(A, sin_centred(p), acc[r]);
             p += f;
           }
-        } else if (kind == DESC_LINEAR) {
-          const RunPoly q = poly_state(s_rec[b][i], rb, true);
-          uint32_t p = q.p + HALF_TURN, f = q.f;
-          const uint32_t g = q.g;
-#pragma unroll
-          for (int r = 0; r < RUN; ++r) {
-            acc[r] = fmaf(A, sin_centred(p), acc[r]);
-            p += f;
-            f += g;
-          }
-        } else if (kind == DESC_MINJERK) {
-          const RunPoly q = poly_state(s_rec[b][i], rb, false);
+        } else if (kind != DESC_MIXED) {
+          const RunPoly q = poly_state(s_rec[b][i], rb, kind == DESC_LINEAR);
           uint32_t p = q.p + HALF_TURN, f = q.f, g = q.g;
           const uint32_t h = q.h;
+          if (__all_sync(0xffffffffu, h == 0)) {
+            // linear chirps, and minimum-jerk chirps whose third difference rounds to zero at
+            // 2^-32 turn (long ramps): g is constant over the run, the same integers as below
 #pragma unroll
-          for (int r = 0; r < RUN; ++r) {
-            acc[r] = fmaf(A, sin_centred(p), acc[r]);
-            p += f;
-            f += g;
-            g += h;
+            for (int r = 0; r < RUN; ++r) {
+              acc[r] = fmaf(A, sin_centred(p), acc[r]);
+              p += f;
+              f += g;
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < RUN; ++r) {
+              acc[r] = fmaf(A, sin_centred(p), acc[r]);
+              p += f;
+              f += g;
+              g += h;
+            }
           }
         } else {
           tone_run(s_tone[b][i], &s_rec[b][i], rb, &s_red[tid], acc, T0, n0, a.exact_tab);
@@ -663,6 +689,11 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
         if (a.out_f) a.out_f[n - a.win_start] = xs[u];
       }
     }
+  }
+  if (a.exit_ctr) {   // this CTA's samples are stored and visible
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(a.exit_ctr, 1ull);
   }
 }
 
@@ -744,6 +775,19 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// End of a pipelined sequence: returns once every render CTA of the sequence has stored its
+// samples (*exit_ctr >= target), so that later work in the stream sees all of them.
+__global__ void join_kernel(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status) {
+  if (!wait_counter(exit_ctr, target)) atomicExch(status, STATUS_TIMEOUT);
+  __threadfence();
+}
+
+cudaError_t launch_join(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status,
+                        cudaStream_t s) {
+  join_kernel<<<1, 1, 0, s>>>(exit_ctr, target, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s) {
   if (a.n_tiles == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
@@ -751,13 +795,15 @@ cudaError_t launch_render(const RenderArgs& a, cudaStream_t s) {
   cfg.blockDim = dim3(NT, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = (unsigned)a.split;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = a.pdl ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, render_kernel, a);
 }
 
