@@ -228,6 +228,40 @@ def table_leg(awg, stream, reps: int = 3, K: int = 10000, log2_len: int = 24):
     return out
 
 
+def static_leg(awg, stream, reps: int = 5):
+    """Static combs in both sine variants: the 100-tone 2^20-sample record and a 10,000-tone comb
+    over 2^22 samples (one render call each; best of reps; library profiling events)."""
+    import numpy as np
+    import torch
+    from paper_2403_15582_gb300 import workloads as wl
+    out = {}
+    c1 = wl.static_100(seed=0)
+    rng = np.random.default_rng(0)
+    f = 80e6 + 1e4 * np.sort(rng.choice(10000, 10000, replace=False)).astype(np.float64)
+    cases = {"static-100tone-2^20": (c1.fs, c1.freq_hz, c1.amp, c1.phase_rad, c1.n_samples),
+             "static-10000tone-2^22": (280e6, f, np.full(10000, 1e-4), rng.uniform(0, 2 * np.pi, 10000), 1 << 22)}
+    for name, (fs, fr, amp, th, n) in cases.items():
+        synth = awg.Synth(fs)
+        synth.set_tones(fr, amp, th)
+        q = torch.empty(n, dtype=torch.int16, device="cuda")
+        res = {}
+        for mode, label in ((awg.SINE_SFU, "sfu"), (awg.SINE_ROTATOR, "rotator")):
+            synth.set_sine_mode(mode)
+            synth.seek(0)
+            synth.render(n, q, stream)      # warm-up
+            synth.profile_begin()
+            for _ in range(reps):
+                synth.seek(0)
+                synth.render(n, q, stream)
+            torch.cuda.synchronize()
+            _, rend, _ = synth.profile_end()
+            ms = float(np.min(rend))
+            res[label] = {"render_ms": ms, "tone_samples_per_s": len(fr) * n / (ms * 1e-3)}
+        out[name] = res
+        synth.close()
+    return out
+
+
 def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, capacity: float = 2.5e12):
     """Served rearrangement stream: Poisson arrivals of requests (50-10,000 tones, up to 100 chirping
     over 0.1-2 ms, 8 chunks of 2^16-2^20 samples) at rho x capacity / mean request work, submitted in
@@ -281,6 +315,7 @@ def main():
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--no-table", action="store_true")
     ap.add_argument("--no-served", action="store_true")
+    ap.add_argument("--no-static", action="store_true")
     ap.add_argument("--table-case", default="10000,24",
                     help="tones,log2 samples of the table leg (a smaller case for profiling)")
     args = ap.parse_args()
@@ -433,6 +468,8 @@ def main():
         "kernel_ms_per_step": {"prep": float(np.sum(prep_ms)) / args.steps,
                                "render": float(np.sum(render_ms)) / args.steps},
     }
+    if not args.no_static:
+        line["static"] = static_leg(awg, stream)
     if not args.no_table:
         tk, tl = (int(v) for v in args.table_case.split(","))
         line["table"] = table_leg(awg, stream, K=tk, log2_len=tl)

@@ -138,6 +138,19 @@ int awg_seek(awg_t* h, int64_t sample);
 /* The render cursor (next sample awg_render writes), or -1 for NULL. */
 int64_t awg_cursor(const awg_t* h);
 
+/* How static tone segments are evaluated (chirp segments always use the SFU form):
+ * AWG_SINE_SFU (default): every sample's sine from its phase word on the SFU, error <= 2^-21.4 per
+ *   sample; AWG_SINE_ROTATOR: the exact phase word at the start of each run of 32 samples gives
+ *   sin and cos on the SFU, then 31 complex rotations by the per-sample step (cos, sin of
+ *   2 pi F / 2^64, rounded to FP32 on the host) on the FP32 pipe, 5 FP32 operations per
+ *   tone-sample; error <= 1.2e-5 |A| per tone-sample (rounding of the step and of 4 operations
+ *   per rotation over at most 31 rotations).  The mode is part of the handle's state: every
+ *   render path uses it, and output depends on it (not bit-identical between modes).  AWG_EINVAL
+ *   for other values. */
+enum { AWG_SINE_SFU = 0, AWG_SINE_ROTATOR = 1 };
+int awg_set_sine_mode(awg_t* h, int32_t mode);
+int32_t awg_sine_mode(const awg_t* h);
+
 /* Render samples cursor .. cursor+n-1 as int16 codes into out[0..n) on `stream`, then advance
  * the cursor by n.  Asynchronous.  Output is a function of the absolute sample index and the
  * tone set only: render(a) followed by render(b) equals render(a+b) bit for bit. */

@@ -11,6 +11,7 @@ LIB_PATH = os.path.join(HERE, "libawg.so")
 
 AWG_OK, AWG_EINVAL, AWG_ENOMEM, AWG_ECUDA, AWG_ETIMEOUT, AWG_EDEADLINE, AWG_ESTATE = 0, -1, -2, -3, -4, -5, -6
 PREC_BF16, PREC_FP16 = 0, 1
+SINE_SFU, SINE_ROTATOR = 0, 1
 PROFILE_LINEAR, PROFILE_MINJERK = 0, 1
 
 # (name, restype, argtypes) of every symbol declared in include/awg.h
@@ -50,6 +51,8 @@ SIGNATURES = [
     ("awg_ring_slot", P, [P, i32]),
     ("awg_seek", ctypes.c_int, [P, i64]),
     ("awg_cursor", i64, [P]),
+    ("awg_set_sine_mode", ctypes.c_int, [P, i32]),
+    ("awg_sine_mode", i32, [P]),
     ("awg_render", ctypes.c_int, [P, i64, P, P]),
     ("awg_render_f32", ctypes.c_int, [P, i64, P, P, P]),
     ("awg_render_chunks", ctypes.c_int, [P, i64, i32, P, P]),
@@ -224,6 +227,14 @@ class Synth:
 
     def render(self, n: int, out, stream=None):
         _check(lib().awg_render(self._h, int(n), _ptr(out), _stream_ptr(stream)))
+
+    def set_sine_mode(self, mode: int):
+        """SINE_SFU (default) or SINE_ROTATOR for static tone segments."""
+        _check(lib().awg_set_sine_mode(self._h, int(mode)))
+
+    @property
+    def sine_mode(self) -> int:
+        return int(lib().awg_sine_mode(self._h))
 
     def render_chunks(self, chunk: int, n_chunks: int, out, stream=None):
         """n_chunks consecutive chunks of `chunk` samples into out, as one pipelined sequence."""

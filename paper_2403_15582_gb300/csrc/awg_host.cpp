@@ -283,6 +283,14 @@ bool needs_exact(uint64_t F0, uint64_t F1, int64_t L, int profile) {
 
 }  // namespace
 
+// cos and sin of the per-sample phase step 2 pi F / 2^64, rounded to float (rotator variant).
+void rotation_of(uint64_t F, float* c, float* s) {
+  const double turn = (double)(F >> 11) * 0x1p-53;
+  const double ang = 6.283185307179586476925 * turn;
+  *c = (float)std::cos(ang);
+  *s = (float)std::sin(ang);
+}
+
 // Tone split per tile: about 96 tones per CTA, at most MAX_SPLIT CTAs per cluster.  A function of
 // the tone count only, so that every sample is summed in the same order whatever the window.
 int awgk::tone_split_for(int K) {
@@ -329,6 +337,7 @@ struct awg {
   double full_scale = 0;
   bool fs_explicit = false;
   int split = 1;
+  int32_t sine_mode = AWG_SINE_SFU;
   cudaStream_t priv = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
   bool timed = false, have_done = false;
@@ -468,6 +477,7 @@ int set_tones_common(awg_t* h, const double* f, const double* amp, const double*
     std::memset(&t, 0, sizeof(t));
     t.phi_ref = P;
     t.F = F;
+    rotation_of(F, &t.rot_c, &t.rot_s);
     t.n_s = awgk::NO_CHIRP;
     t.n_e = awgk::NO_CHIRP;
     t.A = (float)amp[k];
@@ -586,6 +596,7 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream)
   ra.act_of_slot = h->d_act;
   ra.K = h->K;
   ra.split = h->split;
+  ra.sine_mode = h->sine_mode;
   ra.tile0 = tile0;
   ra.n_tiles = n_tiles;
   ra.win_start = c;
@@ -672,6 +683,7 @@ int awgk::prepare_render(awg_t* h, int64_t n, int16_t* out_q, float* out_f, cuda
   ra->act_of_slot = act;
   ra->K = h->K;
   ra->split = h->split;
+  ra->sine_mode = h->sine_mode;
   ra->tile0 = tile0;
   ra->n_tiles = n_tiles;
   ra->win_start = c;
@@ -789,6 +801,7 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
       ra.rec_tile0 = (int32_t)(t_first - tile0);
       ra.K = h->K;
       ra.split = h->split;
+      ra.sine_mode = h->sine_mode;
       ra.tile0 = t_first;
       ra.n_tiles = (int32_t)(t_last - t_first + 1);
       ra.win_start = wc;
@@ -968,6 +981,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     if (t.slot >= 0) {   // fold the finished chirp into the static state
       t.phi_ref = t.phi_post_ref;
       t.F = t.F_end;
+      t.rot_c = t.rot_c_end;
+      t.rot_s = t.rot_s_end;
       h->chirps[(size_t)t.slot].tone = -1;
       h->free_slots.push_back(t.slot);
       t.slot = -1;
@@ -999,6 +1014,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     t.n_s = p.ns;
     t.n_e = p.ns + p.L;
     t.F_end = p.F1;
+    rotation_of(p.F1, &t.rot_c_end, &t.rot_s_end);
     t.phi_post_ref = phi_end - (uint64_t)t.n_e * p.F1;
     t.flags = c.flags;
   }
@@ -1045,6 +1061,15 @@ int awg_seek(awg_t* h, int64_t sample) {
 }
 
 int64_t awg_cursor(const awg_t* h) { return h ? h->cursor : -1; }
+
+int awg_set_sine_mode(awg_t* h, int32_t mode) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (mode != AWG_SINE_SFU && mode != AWG_SINE_ROTATOR) return fail(AWG_EINVAL, "unknown sine mode");
+  h->sine_mode = mode;
+  return AWG_OK;
+}
+
+int32_t awg_sine_mode(const awg_t* h) { return h ? h->sine_mode : -1; }
 
 int awg_render(awg_t* h, int64_t n, int16_t* out, void* stream) {
   if (n > 0 && !out) return fail(AWG_EINVAL, "null output");
@@ -1278,6 +1303,7 @@ int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream) {
   ra.act_of_slot = act;
   ra.K = h->K;
   ra.split = h->split;
+  ra.sine_mode = h->sine_mode;
   ra.tile0 = tile0;
   ra.n_tiles = (int32_t)n_tiles;
   ra.win_start = c;

@@ -16,12 +16,14 @@ constexpr int RUN = 32;
 constexpr int NT = 128;
 constexpr int TILE = RUN * NT;     // 4096 samples
 constexpr int STAGE = 32;          // tones staged in shared memory at a time (double-buffered)
+constexpr int SINE_SFU = 0;        // static segments: SFU sine of every sample's phase
+constexpr int SINE_ROTATOR = 1;    // static segments: exact sin/cos at the run start, then rotations
 constexpr int MAX_SPLIT = 16;      // cluster size limit (non-portable 16 on sm_100-class parts)
 constexpr int MAX_ACTIVE_PER_LAUNCH = 1024;
 
 constexpr int64_t NO_CHIRP = INT64_MAX;
 
-// Per-tone record read by the render kernel.  64 bytes, 16-byte aligned (bulk-copied).
+// Per-tone record read by the render kernel.  80 bytes, 16-byte aligned (bulk-copied).
 struct alignas(16) ToneRec {
   uint64_t phi_ref;       // static segment before the chirp (or the only one): Phi(n) = phi_ref + n F
   uint64_t F;
@@ -33,8 +35,10 @@ struct alignas(16) ToneRec {
   int32_t slot;           // chirp slot, -1 if none
   int32_t flags;          // TONE_EXACT / TONE_LINEAR
   int32_t tab_off;        // TONE_EXACT: offset of this chirp's per-sample phase table
+  float rot_c, rot_s;     // cos, sin of the per-sample step 2 pi F / 2^64 (rotator sine variant)
+  float rot_c_end, rot_s_end;   // the same for F_end
 };
-static_assert(sizeof(ToneRec) == 64, "ToneRec layout");
+static_assert(sizeof(ToneRec) == 80, "ToneRec layout");
 constexpr int32_t TONE_EXACT = 1;    // chirp read from a per-sample table of exact phases
 constexpr int32_t TONE_LINEAR = 2;   // linear chirp: differences of order >= 3 are exactly zero
 
@@ -90,6 +94,7 @@ struct RenderArgs {
   float scale;            // 32767 / FS
   int32_t* status;
   uint64_t inv_odd[3][3];
+  int32_t sine_mode;      // SINE_SFU or SINE_ROTATOR (static segments)
   // record rows: the records of active chirp a for window tile t are at recs[a * rec_stride +
   // rec_tile0 + t] (rec_stride 0: n_tiles, the render's own set-up)
   int32_t rec_stride;

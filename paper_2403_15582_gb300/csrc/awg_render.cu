@@ -475,13 +475,14 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
 // Per-stage tone descriptor, built by warp 0 once per (tone, tile) so that the other threads
 // skip the classification and the 64-bit phase set-up of static segments.
 struct alignas(16) Desc {
-  uint64_t p0;    // DESC_STATIC: phase word at the tile start of the segment covering the tile
-  uint64_t F;     // DESC_STATIC: its frequency word
+  uint64_t p0;    // static: phase word at the tile start of the segment covering the tile
+  uint64_t F;     // static: its frequency word
   float A;
   int32_t kind;
-  int32_t pad[2];
+  float c, s;     // DESC_STATIC_ROT: cos and sin of the per-sample phase step
 };
-enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3 };
+enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_STATIC_ROT = 4 };
+
 
 // One CTA's share of one tile: tones [K crank / split, K (crank+1) / split) of window tile `tile`
 // of the render described by `a`, then the cluster-wide sum and the store of this CTA's slice.
@@ -539,17 +540,19 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
       const ToneRec& tr = s_tone[b][tid];
       Desc d;
       d.A = tr.A;
-      d.pad[0] = d.pad[1] = 0;
+      d.c = d.s = 0.f;
       const int tcls = classify_tile(tr, T0);
       const bool exact = (tr.flags & TONE_EXACT) != 0;
-      if (tcls == TILE_PRE) {
+      if (tcls == TILE_PRE || tcls == TILE_POST) {
+        const bool pre = tcls == TILE_PRE;
+        d.F = pre ? tr.F : tr.F_end;
+        d.p0 = (pre ? tr.phi_ref : tr.phi_post_ref) + (uint64_t)T0 * d.F;
         d.kind = DESC_STATIC;
-        d.F = tr.F;
-        d.p0 = tr.phi_ref + (uint64_t)T0 * tr.F;
-      } else if (tcls == TILE_POST) {
-        d.kind = DESC_STATIC;
-        d.F = tr.F_end;
-        d.p0 = tr.phi_post_ref + (uint64_t)T0 * tr.F_end;
+        if (a.sine_mode == SINE_ROTATOR) {
+          d.kind = DESC_STATIC_ROT;
+          d.c = pre ? tr.rot_c : tr.rot_c_end;
+          d.s = pre ? tr.rot_s : tr.rot_s_end;
+        }
       } else {
         d.F = 0;
         d.p0 = 0;
@@ -609,27 +612,41 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
             acc[r] = fmaf(A, sin_centred(p), acc[r]);
             p += f;
           }
-        } else if (kind != DESC_MIXED) {
-          const RunPoly q = poly_state(s_rec[b][i], rb, kind == DESC_LINEAR);
+        } else if (kind == DESC_STATIC_ROT) {
+          // exact phase word at the run start, SFU sine and cosine once, then 31 rotations by the
+          // per-sample step on the FP32 pipe (amplitude folded into the phasor)
+          const uint64_t w = d.p0 + (uint64_t)run_off * d.F;
+          float sn, cs;
+          __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
+          float im = A * sn, re = A * cs;
+          const float c = d.c, s = d.s;
+#pragma unroll
+          for (int r = 0; r < RUN; ++r) {
+            acc[r] += im;
+            const float t = fmaf(re, c, -im * s);
+            im = fmaf(re, s, im * c);
+            re = t;
+          }
+        } else if (kind == DESC_LINEAR) {
+          const RunPoly q = poly_state(s_rec[b][i], rb, true);
+          uint32_t p = q.p + HALF_TURN, f = q.f;
+          const uint32_t g = q.g;
+#pragma unroll
+          for (int r = 0; r < RUN; ++r) {
+            acc[r] = fmaf(A, sin_centred(p), acc[r]);
+            p += f;
+            f += g;
+          }
+        } else if (kind == DESC_MINJERK) {
+          const RunPoly q = poly_state(s_rec[b][i], rb, false);
           uint32_t p = q.p + HALF_TURN, f = q.f, g = q.g;
           const uint32_t h = q.h;
-          if (__all_sync(0xffffffffu, h == 0)) {
-            // linear chirps, and minimum-jerk chirps whose third difference rounds to zero at
-            // 2^-32 turn (long ramps): g is constant over the run, the same integers as below
 #pragma unroll
-            for (int r = 0; r < RUN; ++r) {
-              acc[r] = fmaf(A, sin_centred(p), acc[r]);
-              p += f;
-              f += g;
-            }
-          } else {
-#pragma unroll
-            for (int r = 0; r < RUN; ++r) {
-              acc[r] = fmaf(A, sin_centred(p), acc[r]);
-              p += f;
-              f += g;
-              g += h;
-            }
+          for (int r = 0; r < RUN; ++r) {
+            acc[r] = fmaf(A, sin_centred(p), acc[r]);
+            p += f;
+            f += g;
+            g += h;
           }
         } else {
           tone_run(s_tone[b][i], &s_rec[b][i], rb, &s_red[tid], acc, T0, n0, a.exact_tab);
