@@ -5,12 +5,15 @@ Workload (the one the headline metric is quoted on): 1000 tones, each chirped fr
 frequency to a seeded target in 80-180 MHz over 35 ms at 280 MS/s (9.8M samples); even tones
 linear, odd tones minimum-jerk; amplitudes U[0.5, 1]/1000; int16 output in 2^18-sample chunks.
 
-One step = the whole record rendered chunk by chunk through the C ABI (per chunk: the chirp
-tile set-up kernel and the render kernel with its fused quantise-and-store).  `value` is
-tone-samples per second with the tone state resident on the device; `e2e` repeats the step
-through the public API from host arrays (set_tones + set_chirps, then rendering straight into
-pinned host memory).  The CPU oracle is timed on the host cores on a bounded window of the same
-workload (`cpu_baseline`); `--impl reference` times only that oracle.
+One step = the whole record rendered chunk by chunk through the C ABI: awg_render_chunks over the
+37 full chunks (one chirp tile set-up per group of chunks, one render kernel per chunk with its
+fused quantise-and-store, consecutive renders overlapping on the device), then the last, shorter
+chunk through awg_render.  `value` is tone-samples per second with the tone state resident on the
+device; `e2e` repeats the step through the public API from host arrays (set_tones + set_chirps,
+then rendering straight into pinned host memory).  The CPU oracle is timed on the host cores on a
+bounded window of the same workload (`cpu_baseline`); `--impl reference` times only that oracle.
+With N GPUs (torchrun) every rank renders its own replica of the workload; the step time is the
+maximum over ranks.
 """
 from __future__ import annotations
 
@@ -44,6 +47,16 @@ RENDER_TRAFFIC_BYTES = 11.419648e6   # ncu dram__bytes_read+write of one 2^18-sa
 CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
                 "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
                 "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The maximum of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def workload():
@@ -400,11 +413,7 @@ def main():
     torch.cuda.synchronize()
     prep_ms, render_ms, _ = synth.profile_end()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     work_per_step = K * N
     value = world * work_per_step * args.steps / (total_ms * 1e-3)
     status = synth.device_status()
@@ -422,13 +431,9 @@ def main():
         stream.synchronize()
         if i >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_total = sum(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_ms), dist, "cuda")
     e2e_value = world * work_per_step * args.steps / (e2e_total * 1e-3)
-    h2d = K * (2 * 64 + 208)     # tone records twice (set_tones, set_chirps) + chirp records
+    h2d = K * (2 * 80 + 208)     # tone records twice (set_tones, set_chirps) + chirp records
 
     if rank != 0:
         if dist is not None:
