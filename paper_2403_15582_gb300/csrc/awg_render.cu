@@ -641,12 +641,23 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
           const RunPoly q = poly_state(s_rec[b][i], rb, false);
           uint32_t p = q.p + HALF_TURN, f = q.f, g = q.g;
           const uint32_t h = q.h;
+          if (__all_sync(0xffffffffu, h == 0)) {
+            // third difference below 2^-33 turn (long ramps): g is constant over the run, the
+            // same integers as the loop below
 #pragma unroll
-          for (int r = 0; r < RUN; ++r) {
-            acc[r] = fmaf(A, sin_centred(p), acc[r]);
-            p += f;
-            f += g;
-            g += h;
+            for (int r = 0; r < RUN; ++r) {
+              acc[r] = fmaf(A, sin_centred(p), acc[r]);
+              p += f;
+              f += g;
+            }
+          } else {
+#pragma unroll
+            for (int r = 0; r < RUN; ++r) {
+              acc[r] = fmaf(A, sin_centred(p), acc[r]);
+              p += f;
+              f += g;
+              g += h;
+            }
           }
         } else {
           tone_run(s_tone[b][i], &s_rec[b][i], rb, &s_red[tid], acc, T0, n0, a.exact_tab);
