@@ -279,6 +279,26 @@ def static_leg(awg, stream, reps: int = 5):
             res[label] = {"render_ms": ms, "tone_samples_per_s": len(fr) * n / (ms * 1e-3)}
         out[name] = res
         synth.close()
+    # digital SFDR of the int16 output for grid tones (periodic 2^20-sample record, unwindowed FFT)
+    lg, N = 20, 1 << 20
+    for K in (1, 100):
+        j = np.sort(rng.choice(np.arange(N // 20, N // 2 - N // 20), K, replace=False))
+        synth = awg.Synth(280e6)
+        synth.set_tones(j * 280e6 / N, np.full(K, 1.0 / K), rng.uniform(0, 2 * np.pi, K), grid_log2=lg)
+        q = torch.empty(N, dtype=torch.int16, device="cuda")
+        res = {}
+        for mode, label in ((awg.SINE_SFU, "sfu"), (awg.SINE_ROTATOR, "rotator")):
+            synth.set_sine_mode(mode)
+            synth.seek(0)
+            synth.render(N, q, stream)
+            torch.cuda.synchronize()
+            P = np.abs(np.fft.rfft(q.cpu().numpy().astype(np.float64))) ** 2
+            mask = np.ones(P.size, dtype=bool)
+            mask[0] = False
+            mask[j] = False
+            res[label] = float(10 * np.log10(P[j].min() / P[mask].max()))
+        out[f"sfdr_dbc_grid_{K}tone_2^20"] = res
+        synth.close()
     return out
 
 

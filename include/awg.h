@@ -159,6 +159,14 @@ int awg_render(awg_t* h, int64_t n, int16_t* out, void* stream);
 /* As awg_render, also writing the FP32 sum x[n] (unscaled) to out_f32 (out_q may be NULL). */
 int awg_render_f32(awg_t* h, int64_t n, float* out_f32, int16_t* out_q, void* stream);
 
+/* Channel multiplexing for a multi-channel DAC (the WM step of Sec. IV-C, fused into the render's
+ * store): handles[c] (n_channels of them, 1..8, distinct, one sample rate, one device) each
+ * render n samples from their own cursor; sample i of channel c goes to out[i * n_channels + c],
+ * so the buffer holds groups of n_channels samples, one per channel, as the card reads them.
+ * Each channel's samples are the same as its awg_render output.  Every cursor advances by n; on
+ * an error none does. */
+int awg_render_multiplexed(awg_t* const* handles, int32_t n_channels, int64_t n, int16_t* out, void* stream);
+
 /* Render n_chunks consecutive chunks of `chunk` samples (the chunk loop of Sec. IV: the cursor
  * advances chunk by chunk) into out[0 .. n_chunks * chunk), with the same samples as n_chunks
  * calls of awg_render.  The chunks are issued as one pipelined sequence: the chirp set-up of chunk

@@ -56,6 +56,7 @@ SIGNATURES = [
     ("awg_render", ctypes.c_int, [P, i64, P, P]),
     ("awg_render_f32", ctypes.c_int, [P, i64, P, P, P]),
     ("awg_render_chunks", ctypes.c_int, [P, i64, i32, P, P]),
+    ("awg_render_multiplexed", ctypes.c_int, [P, i32, i64, P, P]),
     ("awg_phase_words", ctypes.c_int, [P, i64, P, i32]),
     ("awg_render_phases", ctypes.c_int, [P, i32, i64, i32, P]),
     ("awg_tone_split", i32, [P]),
@@ -288,6 +289,12 @@ class RingStats(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def render_multiplexed(synths, n: int, out, stream=None):
+    """Interleave n samples of each Synth's channel into out[i * len(synths) + c]."""
+    arr = (ctypes.c_void_p * len(synths))(*[s._h.value for s in synths])
+    _check(lib().awg_render_multiplexed(arr, len(synths), int(n), _ptr(out), _stream_ptr(stream)))
 
 
 class Ring:

@@ -528,7 +528,7 @@ int build_exact_tables(awg_t* h) {
   return AWG_OK;
 }
 
-int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream) {
+int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride = 1) {
   if (!h) return fail(AWG_EINVAL, "null handle");
   if (n < 0) return fail(AWG_EINVAL, "sample count must be >= 0");
   if (n == 0) return AWG_OK;
@@ -597,6 +597,7 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream)
   ra.K = h->K;
   ra.split = h->split;
   ra.sine_mode = h->sine_mode;
+  ra.q_stride = q_stride;
   ra.tile0 = tile0;
   ra.n_tiles = n_tiles;
   ra.win_start = c;
@@ -1074,6 +1075,32 @@ int32_t awg_sine_mode(const awg_t* h) { return h ? h->sine_mode : -1; }
 int awg_render(awg_t* h, int64_t n, int16_t* out, void* stream) {
   if (n > 0 && !out) return fail(AWG_EINVAL, "null output");
   return render_impl(h, n, nullptr, out, stream);
+}
+
+int awg_render_multiplexed(awg_t* const* handles, int32_t n_channels, int64_t n, int16_t* out, void* stream) {
+  if (!handles || n_channels < 1 || n_channels > 8) return fail(AWG_EINVAL, "need 1..8 channel handles");
+  if (n < 0) return fail(AWG_EINVAL, "sample count must be >= 0");
+  if (n == 0) return AWG_OK;
+  if (!out) return fail(AWG_EINVAL, "null output");
+  int64_t cursors[8];
+  for (int32_t c = 0; c < n_channels; ++c) {
+    const awg_t* h = handles[c];
+    if (!h) return fail(AWG_EINVAL, "null channel handle");
+    for (int32_t d = 0; d < c; ++d)
+      if (handles[d] == h) return fail(AWG_EINVAL, "a handle appears in two channels");
+    if (h->fs != handles[0]->fs) return fail(AWG_EINVAL, "channels must share one sample rate");
+    if (h->device != handles[0]->device) return fail(AWG_EINVAL, "channels must be on one device");
+    if (h->cursor > INT64_MAX - n) return fail(AWG_EINVAL, "sample index overflow");
+    cursors[c] = h->cursor;
+  }
+  for (int32_t c = 0; c < n_channels; ++c) {
+    const int st = render_impl(handles[c], n, nullptr, out + c, stream, n_channels);
+    if (st) {
+      for (int32_t d = 0; d < c; ++d) handles[d]->cursor = cursors[d];
+      return st;
+    }
+  }
+  return AWG_OK;
 }
 
 int awg_render_f32(awg_t* h, int64_t n, float* out_f32, int16_t* out_q, void* stream) {

@@ -95,6 +95,7 @@ struct RenderArgs {
   int32_t* status;
   uint64_t inv_odd[3][3];
   int32_t sine_mode;      // SINE_SFU or SINE_ROTATOR (static segments)
+  int32_t q_stride;       // int16 output: sample i goes to out_q[i * q_stride] (0: 1; channel multiplexing)
   // record rows: the records of active chirp a for window tile t are at recs[a * rec_stride +
   // rec_tile0 + t] (rec_stride 0: n_tiles, the render's own set-up)
   int32_t rec_stride;

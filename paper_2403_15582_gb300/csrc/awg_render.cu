@@ -713,7 +713,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
       if (n >= a.win_start && n < a.win_end) {
         float q = rintf(xs[u] * a.scale);
         q = fminf(fmaxf(q, -32767.f), 32767.f);
-        if (a.out_q) a.out_q[n - a.win_start] = (int16_t)q;
+        if (a.out_q) a.out_q[(n - a.win_start) * (a.q_stride ? a.q_stride : 1)] = (int16_t)q;
         if (a.out_f) a.out_f[n - a.win_start] = xs[u];
       }
     }
