@@ -151,6 +151,25 @@ enum { AWG_SINE_SFU = 0, AWG_SINE_ROTATOR = 1 };
 int awg_set_sine_mode(awg_t* h, int32_t mode);
 int32_t awg_sine_mode(const awg_t* h);
 
+/* Periodic hand-off (the end state of the Playback pathway, Sec. IV-C: once the chirps are over
+ * the output is a periodic waveform).  When every tone's final frequency (after its chirp, if it
+ * has one) lies on the f_s / 2^log2_len grid (Eq. freqapprox), the waveform from
+ * n_p = max(cursor, the first 4096-sample tile boundary after the last chirp's end) on is
+ * periodic with period N = 2^log2_len.  This call computes that period once into a device table owned by the handle (method
+ * AWG_PERIODIC_DIRECT: the render kernel over one period of the static state, in the handle's
+ * sine mode, so replayed samples equal the rendered ones bit for bit; AWG_PERIODIC_GEMM_BF16 /
+ * _FP16: the split-precision table GEMM, within 1 LSB), synchronising `stream`.  After it,
+ * awg_render / awg_render_chunks / awg_render_multiplexed render samples before n_p as usual and
+ * replay the table for samples from n_p on (a copy kernel; awg_render_f32 and
+ * awg_render_noalloc keep rendering).  awg_set_tones and awg_set_chirps end the hand-off.
+ * AWG_EINVAL: log2_len outside 12..30 (15..30 for the GEMM), unknown method, a final frequency
+ * off the grid. */
+enum { AWG_PERIODIC_DIRECT = 0, AWG_PERIODIC_GEMM_BF16 = 1, AWG_PERIODIC_GEMM_FP16 = 2 };
+int awg_set_periodic(awg_t* h, int32_t log2_len, int32_t method, void* stream);
+/* n_p of the active hand-off, or -1. */
+int64_t awg_periodic_start(const awg_t* h);
+int awg_clear_periodic(awg_t* h);
+
 /* Render samples cursor .. cursor+n-1 as int16 codes into out[0..n) on `stream`, then advance
  * the cursor by n.  Asynchronous.  Output is a function of the absolute sample index and the
  * tone set only: render(a) followed by render(b) equals render(a+b) bit for bit. */

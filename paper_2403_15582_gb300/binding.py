@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(HERE, "libawg.so")
 AWG_OK, AWG_EINVAL, AWG_ENOMEM, AWG_ECUDA, AWG_ETIMEOUT, AWG_EDEADLINE, AWG_ESTATE = 0, -1, -2, -3, -4, -5, -6
 PREC_BF16, PREC_FP16 = 0, 1
 SINE_SFU, SINE_ROTATOR = 0, 1
+PERIODIC_DIRECT, PERIODIC_GEMM_BF16, PERIODIC_GEMM_FP16 = 0, 1, 2
 PROFILE_LINEAR, PROFILE_MINJERK = 0, 1
 
 # (name, restype, argtypes) of every symbol declared in include/awg.h
@@ -53,6 +54,9 @@ SIGNATURES = [
     ("awg_cursor", i64, [P]),
     ("awg_set_sine_mode", ctypes.c_int, [P, i32]),
     ("awg_sine_mode", i32, [P]),
+    ("awg_set_periodic", ctypes.c_int, [P, i32, i32, P]),
+    ("awg_periodic_start", i64, [P]),
+    ("awg_clear_periodic", ctypes.c_int, [P]),
     ("awg_render", ctypes.c_int, [P, i64, P, P]),
     ("awg_render_f32", ctypes.c_int, [P, i64, P, P, P]),
     ("awg_render_chunks", ctypes.c_int, [P, i64, i32, P, P]),
@@ -236,6 +240,17 @@ class Synth:
     @property
     def sine_mode(self) -> int:
         return int(lib().awg_sine_mode(self._h))
+
+    def set_periodic(self, log2_len: int, method: int = 0, stream=None):
+        """Periodic hand-off after the chirps (PERIODIC_DIRECT, PERIODIC_GEMM_BF16 / _FP16)."""
+        _check(lib().awg_set_periodic(self._h, int(log2_len), int(method), _stream_ptr(stream)))
+
+    @property
+    def periodic_start(self) -> int:
+        return int(lib().awg_periodic_start(self._h))
+
+    def clear_periodic(self):
+        _check(lib().awg_clear_periodic(self._h))
 
     def render_chunks(self, chunk: int, n_chunks: int, out, stream=None):
         """n_chunks consecutive chunks of `chunk` samples into out, as one pipelined sequence."""

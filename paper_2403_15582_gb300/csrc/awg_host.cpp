@@ -338,6 +338,11 @@ struct awg {
   bool fs_explicit = false;
   int split = 1;
   int32_t sine_mode = AWG_SINE_SFU;
+  // periodic hand-off: from sample periodic_start on, x[n] = periodic table[n mod 2^periodic_log2]
+  int16_t* d_periodic = nullptr;
+  size_t cap_periodic = 0;
+  int32_t periodic_log2 = 0;
+  int64_t periodic_start = -1;
   cudaStream_t priv = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
   bool timed = false, have_done = false;
@@ -489,6 +494,7 @@ int set_tones_common(awg_t* h, const double* f, const double* amp, const double*
   h->tones.swap(tones);
   h->amp.swap(a);
   h->K = n;
+  h->periodic_start = -1;
   h->chirps.clear();
   h->free_slots.clear();
   h->fs_explicit = false;
@@ -535,6 +541,26 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream,
   if (!out_f && !out_q) return fail(AWG_EINVAL, "no output buffer");
   if (h->cursor > INT64_MAX - n) return fail(AWG_EINVAL, "sample index overflow");
   cudaStream_t s = (cudaStream_t)stream;
+  if (h->periodic_start >= 0 && !out_f && h->cursor + n > h->periodic_start) {
+    // periodic hand-off: render up to the start of the periodic part, replay the table after it
+    const int64_t n1 = std::max<int64_t>(0, h->periodic_start - h->cursor);
+    if (n1 > 0) {
+      const int st = render_impl(h, n1, nullptr, out_q, stream, q_stride);
+      if (st) return st;
+    }
+    const int64_t c = h->cursor, n2 = n - n1;
+    cudaError_t e;
+    if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
+    if ((e = awgk::launch_replay(h->d_periodic, h->periodic_log2, c, n2, out_q + (size_t)n1 * (size_t)q_stride,
+                                 q_stride, s)) != cudaSuccess)
+      return cuda_fail(e, "replay launch");
+    if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
+    if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
+    h->timed = true;
+    h->have_done = true;
+    h->cursor = c + n2;
+    return AWG_OK;
+  }
   const int64_t c = h->cursor;
   const int64_t tile0 = c / awgk::TILE;
   const int64_t tile_last = (c + n - 1) / awgk::TILE;
@@ -911,6 +937,7 @@ void awg_destroy(awg_t* h) {
   cudaFree(h->d_chirps);
   cudaFree(h->d_act);
   cudaFree(h->d_recs);
+  cudaFree(h->d_periodic);
   cudaFree(h->d_seq_recs);
   cudaFree(h->d_seq_act);
   cudaFree(h->d_seq_exit);
@@ -974,6 +1001,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   }
   int st = wait_idle(h);
   if (st) return st;
+  h->periodic_start = -1;
   const size_t slots_before = h->chirps.size();
   std::vector<int32_t> changed_tones, changed_slots;
   for (const Pending& p : pend) {
@@ -1072,6 +1100,75 @@ int awg_set_sine_mode(awg_t* h, int32_t mode) {
 
 int32_t awg_sine_mode(const awg_t* h) { return h ? h->sine_mode : -1; }
 
+int awg_set_periodic(awg_t* h, int32_t log2_len, int32_t method, void* stream) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (log2_len < 12 || log2_len > 30) return fail(AWG_EINVAL, "log2_len must be 12..30");
+  if (method != AWG_PERIODIC_DIRECT && method != AWG_PERIODIC_GEMM_BF16 && method != AWG_PERIODIC_GEMM_FP16)
+    return fail(AWG_EINVAL, "unknown periodic method");
+  if (method != AWG_PERIODIC_DIRECT && log2_len < 15) return fail(AWG_EINVAL, "the GEMM table needs log2_len >= 15");
+  // the static state that follows every chirp, and where it starts
+  const uint64_t grid_mask = (1ull << (64 - log2_len)) - 1;
+  int64_t start = h->cursor;
+  std::vector<ToneRec> view(h->tones.size());
+  for (size_t k = 0; k < h->tones.size(); ++k) {
+    const ToneRec& t = h->tones[k];
+    ToneRec v;
+    std::memset(&v, 0, sizeof(v));
+    const bool chirped = t.slot >= 0;
+    v.phi_ref = chirped ? t.phi_post_ref : t.phi_ref;
+    v.F = chirped ? t.F_end : t.F;
+    v.rot_c = chirped ? t.rot_c_end : t.rot_c;
+    v.rot_s = chirped ? t.rot_s_end : t.rot_s;
+    v.n_s = awgk::NO_CHIRP;
+    v.n_e = awgk::NO_CHIRP;
+    v.A = t.A;
+    v.slot = -1;
+    if (v.F & grid_mask) return fail(AWG_EINVAL, "a tone's final frequency is not on the f_s / 2^log2_len grid");
+    // from the first whole tile after the chirp the render takes the static path, so replayed
+    // samples equal rendered ones bit for bit in either sine mode
+    if (chirped) start = std::max(start, (t.n_e / awgk::TILE + 1) * awgk::TILE);
+    view[k] = v;
+  }
+  const int64_t N = (int64_t)1 << log2_len;
+  int st = ensure(&h->d_periodic, &h->cap_periodic, (size_t)N, h, "periodic table");
+  if (st) return st;
+  awg_t* tmp = awg_create(h->fs);
+  if (!tmp) return AWG_ENOMEM;
+  tmp->tones = view;
+  tmp->amp = h->amp;
+  tmp->K = h->K;
+  tmp->split = h->split;
+  tmp->sine_mode = h->sine_mode;
+  tmp->full_scale = h->full_scale;
+  tmp->fs_explicit = true;
+  st = upload_tones(tmp);
+  if (!st) st = upload_chirps(tmp);
+  if (!st) {
+    if (method == AWG_PERIODIC_DIRECT)
+      st = render_impl(tmp, N, nullptr, h->d_periodic, stream);
+    else
+      st = awg_table_gemm(tmp, log2_len, method == AWG_PERIODIC_GEMM_FP16 ? AWG_PREC_FP16 : AWG_PREC_BF16,
+                          h->d_periodic, nullptr, stream);
+  }
+  if (!st) {
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) st = cuda_fail(e, "periodic table");
+  }
+  awg_destroy(tmp);
+  if (st) return st;
+  h->periodic_log2 = log2_len;
+  h->periodic_start = start;
+  return AWG_OK;
+}
+
+int64_t awg_periodic_start(const awg_t* h) { return h ? h->periodic_start : -1; }
+
+int awg_clear_periodic(awg_t* h) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  h->periodic_start = -1;
+  return AWG_OK;
+}
+
 int awg_render(awg_t* h, int64_t n, int16_t* out, void* stream) {
   if (n > 0 && !out) return fail(AWG_EINVAL, "null output");
   return render_impl(h, n, nullptr, out, stream);
@@ -1115,7 +1212,8 @@ int awg_render_chunks(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, v
   if (!out) return fail(AWG_EINVAL, "null output");
   if (chunk > (INT64_MAX - h->cursor) / n_chunks) return fail(AWG_EINVAL, "sample index overflow");
   if (chunk / awgk::TILE + 2 > (int64_t)(INT32_MAX / awgk::MAX_SPLIT)) return fail(AWG_EINVAL, "chunk too long");
-  if (n_chunks == 1 || h->profiling) {   // per-call profiling events would split the pipeline
+  if (n_chunks == 1 || h->profiling || h->periodic_start >= 0) {
+    // per-call profiling events would split the pipeline; a periodic tail is replayed per chunk
     for (int32_t c = 0; c < n_chunks; ++c) {
       const int st = render_impl(h, chunk, nullptr, out + (size_t)c * (size_t)chunk, stream);
       if (st) return st;

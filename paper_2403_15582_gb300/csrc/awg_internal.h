@@ -140,6 +140,8 @@ struct TableArgs {      // exact per-sample 32-bit phases of one short chirp, m 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s);
 cudaError_t launch_exact_table(const TableArgs& a, int64_t L, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
+cudaError_t launch_replay(const int16_t* tab, int32_t log2_len, int64_t c, int64_t n, int16_t* out, int32_t stride,
+                          cudaStream_t s);
 cudaError_t launch_join(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status,
                         cudaStream_t s);
 // items[i] = (request index into reqs, window tile); every request has split == `split`.

@@ -803,6 +803,36 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Replay of a periodic record (period mask + 1 = 2^log2 samples): out[i * stride] =
+// table[(c + i) mod period].  16-byte vectors when the stride is 1 and both sides are aligned
+// to 8 samples (a vector never wraps: the period is a multiple of 8).
+__global__ void replay_kernel(const int16_t* __restrict__ tab, uint64_t mask, int64_t c, int64_t n,
+                              int16_t* __restrict__ out, int32_t stride, int vec) {
+  const int64_t step = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t done = 0;
+  if (vec) {
+    const int64_t nv = n / 8;
+    for (int64_t v = t0; v < nv; v += step) {
+      const uint64_t src = ((uint64_t)c + (uint64_t)v * 8u) & mask;
+      reinterpret_cast<uint4*>(out)[v] = *reinterpret_cast<const uint4*>(tab + src);
+    }
+    done = nv * 8;
+  }
+  for (int64_t i = done + t0; i < n; i += step) out[i * stride] = tab[((uint64_t)c + (uint64_t)i) & mask];
+}
+
+cudaError_t launch_replay(const int16_t* tab, int32_t log2_len, int64_t c, int64_t n, int16_t* out, int32_t stride,
+                          cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const uint64_t mask = ((uint64_t)1 << log2_len) - 1;
+  const int vec = stride == 1 && (c & 7) == 0 && ((uintptr_t)out & 15) == 0 && log2_len >= 3;
+  const int64_t work = vec ? n / 8 + 1 : n;
+  const int64_t blocks = std::min<int64_t>((work + 255) / 256, 152 * 16);
+  replay_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(tab, mask, c, n, out, stride, vec);
+  return cudaGetLastError();
+}
+
 // End of a pipelined sequence: returns once every render CTA of the sequence has stored its
 // samples (*exit_ctr >= target), so that later work in the stream sees all of them.
 __global__ void join_kernel(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status) {
