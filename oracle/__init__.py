@@ -64,11 +64,13 @@ def lib():
         L = ctypes.CDLL(_LIB_PATH)
         P = ctypes.c_void_p
         i64, i32, u64, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double
-        L.oracle_render.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, i64, i64, P, ctypes.c_int, P]
+        L.oracle_render.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, i64, i64, P, ctypes.c_int, P, P, P, P, P]
         L.oracle_render.restype = ctypes.c_int
         L.oracle_render_work_bytes.argtypes = [ctypes.c_int, ctypes.c_int]
         L.oracle_render_work_bytes.restype = ctypes.c_size_t
-        L.oracle_render_at.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P, i64, P, ctypes.c_int, P]
+        L.oracle_render_at.argtypes = [ctypes.c_int, P, P, P, P, P, P, P, P, P, i64, P, ctypes.c_int, P, P, P, P, P]
+        L.oracle_amp_at.argtypes = [dbl, i32, i64, i64, dbl, P, i64, P]
+        L.oracle_amp_at.restype = None
         L.oracle_render_at.restype = None
         L.oracle_phase_words_seq.argtypes = [u64, u64, i32, i64, i64, P, u64, i64, i64, P]
         L.oracle_phase_words_at.argtypes = [u64, u64, i32, i64, i64, P, u64, P, i64, P]
@@ -189,10 +191,26 @@ class Waveform:
     L: list = field(default_factory=list)
     d: list = field(default_factory=list)          # 7 ints mod 2^192 (zeros if no chirp)
     F_end: list = field(default_factory=list)
+    # amplitude ramps a_k(n) (Eq. dynamicandstatic): tone -> (profile, a_ns, a_L, A_end)
+    ramps: dict = field(default_factory=dict)
 
     @property
     def K(self) -> int:
         return len(self.F)
+
+    def ramp_arrays(self):
+        """(ramp pairs, a_ns, a_L, A_end) for the C oracle, or Nones without ramps."""
+        if not self.ramps:
+            return None, None, None, None
+        K = self.K
+        rp = np.zeros(2 * K, dtype=np.int32)
+        ns = np.zeros(K, dtype=np.int64)
+        L = np.zeros(K, dtype=np.int64)
+        Ae = np.array(self.A, dtype=np.float64)
+        for k, (prof, a_ns, a_L, A_end) in self.ramps.items():
+            rp[2 * k], rp[2 * k + 1] = 1, int(prof)
+            ns[k], L[k], Ae[k] = int(a_ns), int(a_L), float(A_end)
+        return rp, ns, L, Ae
 
     def full_scale(self) -> float:
         """Default full scale: sum |A_k|, which can never clip."""
@@ -256,6 +274,10 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _pn(a):
+    return None if a is None else _p(a)
+
+
 def render(w: Waveform, n0: int, N: int, nthreads: int = 1) -> np.ndarray:
     """x[n] for n = n0 .. n0+N-1 in FP64 (Eq. dynamicandstatic: sum of A_k sin(phi_k[n]))."""
     L_ = lib()
@@ -264,8 +286,9 @@ def render(w: Waveform, n0: int, N: int, nthreads: int = 1) -> np.ndarray:
     if N == 0:
         return out
     work = np.zeros(L_.oracle_render_work_bytes(w.K, nthreads), dtype=np.uint8)
+    rp, ans, aL, Ae = w.ramp_arrays()
     used = L_.oracle_render(w.K, _p(F), _p(phi), _p(A), _p(hc), _p(ns), _p(Lc), _p(d), _p(Fe),
-                            int(n0), int(N), _p(out), int(nthreads), _p(work))
+                            int(n0), int(N), _p(out), int(nthreads), _p(work), _pn(rp), _pn(ans), _pn(aL), _pn(Ae))
     render.last_threads = used
     return out
 
@@ -282,9 +305,29 @@ def render_at(w: Waveform, samples, nthreads: int = 1) -> np.ndarray:
     if idx.size == 0:
         return out
     work = np.zeros(L_.oracle_render_work_bytes(w.K, 1), dtype=np.uint8)
+    rp, ans, aL, Ae = w.ramp_arrays()
     L_.oracle_render_at(w.K, _p(F), _p(phi), _p(A), _p(hc), _p(ns), _p(Lc), _p(d), _p(Fe),
-                        _p(idx), int(idx.size), _p(out), int(nthreads), _p(work))
+                        _p(idx), int(idx.size), _p(out), int(nthreads), _p(work), _pn(rp), _pn(ans), _pn(aL), _pn(Ae))
     return out
+
+
+def amp_at(A: float, profile: int, a_ns: int, a_L: int, A_end: float, samples) -> np.ndarray:
+    """Amplitude of one ramping tone at the given samples (the oracle's a(n))."""
+    idx = np.ascontiguousarray(np.asarray(samples, dtype=np.int64))
+    out = np.zeros(idx.size, dtype=np.float64)
+    lib().oracle_amp_at(float(A), int(profile), int(a_ns), int(a_L), float(A_end), _p(idx), int(idx.size), _p(out))
+    return out
+
+
+def add_ramps(w: Waveform, ramps, fs: Optional[float] = None) -> Waveform:
+    """Attach amplitude ramps [{tone, amp_end, duration, profile, start_sample}] to a waveform; a
+    ramp moves the tone's amplitude from its value A_k to amp_end over L = rint(duration fs)
+    samples (the same length rule as a chirp).  One ramp per tone."""
+    fs = w.fs if fs is None else fs
+    for r in ramps:
+        w.ramps[int(r["tone"])] = (int(r["profile"]), int(r.get("start_sample", 0)), chirp_length(r["duration"], fs),
+                                   float(r["amp_end"]))
+    return w
 
 
 def quantize(x: np.ndarray, FS: float) -> np.ndarray:

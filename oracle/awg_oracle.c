@@ -20,6 +20,8 @@
  *                 d_0 carries the rounding offset 2^127, so top64() rounds to nearest.
  *   after chirp:  Phi(n) = Phi_end + (n - n_s - L) * F_end   (Eq. freqchirp, case 2),
  *                 Phi_end = Phi(n_s + L) from the cascade.
+ *   amplitude:    A_k, or a ramp a_k(n) from A_k to A_end (see amp_at) for a_j[i] of
+ *                 Eq. dynamicandstatic.
  * Sine is libm sin() in FP64 of the signed turn u = (int64)Phi * 2^-64, the sum runs over
  * tones in ascending order in FP64, and quantisation is round-half-even with a symmetric clamp
  * at +-32767.
@@ -116,7 +118,26 @@ typedef struct {
   int64_t n_s, L;               /* chirp covers samples n_s .. n_s+L (m = 0..L) */
   const uint64_t* d;            /* 7 x 3 limbs */
   uint64_t phi_start, phi_end, F_end;
+  int32_t has_ramp, ramp_prof;  /* amplitude ramp a_j[i] of Eq. dynamicandstatic (0: none) */
+  int64_t a_ns, a_L;            /* the amplitude moves from A to A_end over samples a_ns .. a_ns+a_L */
+  double A_end;
 } tone_t;
+
+/*
+ * Amplitude a(n) of Eq. dynamicandstatic.  The paper leaves a_j[i] open; the ramp used here moves
+ * from A to A_end along the same profiles as the frequency ramps: with tau = (n - a_ns)/a_L,
+ * linear s(tau) = tau, minimum-jerk s(tau) = 10 tau^3 - 15 tau^4 + 6 tau^5 (the minimum-jerk
+ * frequency trajectory whose integral is the phase of Eq. freqchirp); a = A + (A_end - A) s.
+ * Before the ramp a = A, after it a = A_end.
+ */
+static double amp_at(const tone_t* t, int64_t n) {
+  if (!t->has_ramp || n <= t->a_ns) return t->A;
+  int64_t m = n - t->a_ns;
+  if (m >= t->a_L) return t->A_end;
+  double tau = (double)m / (double)t->a_L;
+  double s = t->ramp_prof == 0 ? tau : tau * tau * tau * (10.0 - 15.0 * tau + 6.0 * tau * tau);
+  return t->A + (t->A_end - t->A) * s;
+}
 
 /* Phase word at absolute sample n by the closed form (used to seed sequential runs). */
 static uint64_t phase_closed(const tone_t* t, int64_t n) {
@@ -190,6 +211,10 @@ static void build_tones(int K, const uint64_t* F, const uint64_t* phi_ref, const
                         const uint64_t* d, const uint64_t* F_end, tone_t* tones) {
   for (int k = 0; k < K; k++) {
     tone_t* t = &tones[k];
+    t->has_ramp = 0;
+    t->ramp_prof = 0;
+    t->a_ns = t->a_L = 0;
+    t->A_end = A[k];
     t->F = F[k];
     t->phi_ref = phi_ref[k];
     t->A = A[k];
@@ -207,6 +232,33 @@ static void build_tones(int K, const uint64_t* F, const uint64_t* phi_ref, const
       t->phi_end = 0;
     }
   }
+}
+
+/* Amplitude ramps (ramp: K x {has_ramp, profile} int32 pairs; a_ns, a_L: int64; A_end: FP64). */
+static void apply_ramps(int K, const int32_t* ramp, const int64_t* a_ns, const int64_t* a_L, const double* A_end,
+                        tone_t* tones) {
+  if (!ramp) return;
+  for (int k = 0; k < K; k++) {
+    tones[k].has_ramp = ramp[2 * k];
+    tones[k].ramp_prof = ramp[2 * k + 1];
+    tones[k].a_ns = a_ns[k];
+    tones[k].a_L = a_L[k];
+    tones[k].A_end = A_end[k];
+  }
+}
+
+/* Amplitudes a(n) of one tone at samples n[0..N) (for tests). */
+void oracle_amp_at(double A, int32_t profile, int64_t a_ns, int64_t a_L, double A_end, const int64_t* n,
+                   int64_t N, double* out) {
+  tone_t t;
+  memset(&t, 0, sizeof(t));
+  t.A = A;
+  t.has_ramp = 1;
+  t.ramp_prof = profile;
+  t.a_ns = a_ns;
+  t.a_L = a_L;
+  t.A_end = A_end;
+  for (int64_t i = 0; i < N; i++) out[i] = amp_at(&t, n[i]);
 }
 
 /* Post-chirp anchor Phi_end = Phi(n_s + L), for tests and for the host bookkeeping of tests. */
@@ -257,10 +309,12 @@ void oracle_cascade_at(const uint64_t* d, int64_t m, uint64_t* out) {
 int oracle_render(int K, const uint64_t* F, const uint64_t* phi_ref, const double* A,
                   const int32_t* has_chirp, const int64_t* n_s, const int64_t* L,
                   const uint64_t* d, const uint64_t* F_end, int64_t n0, int64_t N, double* out,
-                  int nthreads, void* work /* K * sizeof(tone_t) + nthreads*K*sizeof(gen_t) */) {
+                  int nthreads, void* work /* K * sizeof(tone_t) + nthreads*K*sizeof(gen_t) */,
+                  const int32_t* ramp, const int64_t* a_ns, const int64_t* a_L, const double* A_end) {
   tone_t* tones = (tone_t*)work;
   gen_t* gens = (gen_t*)((char*)work + (size_t)K * sizeof(tone_t));
   build_tones(K, F, phi_ref, A, has_chirp, n_s, L, d, F_end, tones);
+  apply_ramps(K, ramp, a_ns, a_L, A_end, tones);
   if (nthreads < 1) nthreads = 1;
   int used = 1;
 #ifdef _OPENMP
@@ -281,7 +335,7 @@ int oracle_render(int K, const uint64_t* F, const uint64_t* phi_ref, const doubl
       for (int64_t i = lo; i < hi; i++) {
         double x = 0.0;
         for (int k = 0; k < K; k++) {
-          x += tones[k].A * word_sin(gen_phase(&g[k]));
+          x += amp_at(&tones[k], n0 + i) * word_sin(gen_phase(&g[k]));
           gen_advance(&g[k]);
         }
         out[i] = x;
@@ -300,16 +354,18 @@ size_t oracle_render_work_bytes(int K, int nthreads) {
 void oracle_render_at(int K, const uint64_t* F, const uint64_t* phi_ref, const double* A,
                       const int32_t* has_chirp, const int64_t* n_s, const int64_t* L,
                       const uint64_t* d, const uint64_t* F_end, const int64_t* n, int64_t N,
-                      double* out, int nthreads, void* work /* K * sizeof(tone_t) */) {
+                      double* out, int nthreads, void* work /* K * sizeof(tone_t) */,
+                      const int32_t* ramp, const int64_t* a_ns, const int64_t* a_L, const double* A_end) {
   tone_t* tones = (tone_t*)work;
   build_tones(K, F, phi_ref, A, has_chirp, n_s, L, d, F_end, tones);
+  apply_ramps(K, ramp, a_ns, a_L, A_end, tones);
   (void)nthreads;
 #ifdef _OPENMP
 #pragma omp parallel for num_threads(nthreads > 0 ? nthreads : 1) schedule(dynamic, 4)
 #endif
   for (int64_t i = 0; i < N; i++) {
     double x = 0.0;
-    for (int k = 0; k < K; k++) x += tones[k].A * word_sin(phase_closed(&tones[k], n[i]));
+    for (int k = 0; k < K; k++) x += amp_at(&tones[k], n[i]) * word_sin(phase_closed(&tones[k], n[i]));
     out[i] = x;
   }
 }

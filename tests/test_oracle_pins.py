@@ -391,3 +391,63 @@ def test_repeated_chirps_fold_continuously(oracle):
         words = oracle.phase_words_seq(w, 0, n0, 64)
         for i, wd in enumerate(words):
             assert abs(_sdiff(wd, round(exact_turns(n0 + i) * TWO64))) <= 3, (n0, i)
+
+
+# ---------------------------------------------------------------------------------------------
+# amplitude ramps a_j[i] (Eq. dynamicandstatic): A -> A_end along the linear or minimum-jerk
+# profile s(tau) (10 tau^3 - 15 tau^4 + 6 tau^5, the minimum-jerk trajectory of Eq. freqchirp)
+# ---------------------------------------------------------------------------------------------
+def _check_amp_pins(amp, A0, A1, ns, L, profile):
+    """Pins of a ramp sampler amp(samples) -> values: constant outside, exact ends, midpoint
+    (A0 + A1)/2, point symmetry s(tau) + s(1 - tau) = 1, and the slopes the profile fixes."""
+    dA = A1 - A0
+    m = np.arange(0, L + 1)
+    a = amp(ns + m)
+    assert np.all(amp(np.array([ns - 5, ns - 1, ns])) == A0)
+    assert np.all(amp(np.array([ns + L, ns + L + 1, ns + 10 * L])) == A1)
+    assert abs(a[L // 2] - 0.5 * (A0 + A1)) <= 1e-12 * abs(dA)
+    assert np.max(np.abs(a + a[::-1] - (A0 + A1))) <= 1e-12 * abs(dA)
+    d = np.diff(a)
+    if profile == 0:
+        assert np.max(np.abs(d - dA / L)) <= 1e-12 * abs(dA)
+    else:
+        assert abs(d[0]) <= 11 * abs(dA) / L**3 and abs(d[-1]) <= 11 * abs(dA) / L**3
+        assert abs(d[L // 2] / (dA / L) - 1.875) <= 2e-3       # s'(1/2) = 30/16
+
+
+@pytest.mark.parametrize("profile", [0, 1])
+def test_amp_ramp_pins(oracle, profile):
+    for A0, A1, ns, L in [(0.25, 1.0, 1000, 4000), (1.0, 0.0, 0, 1000), (-0.5, 0.75, 123456789, 20000)]:
+        _check_amp_pins(lambda n: oracle.amp_at(A0, profile, ns, L, A1, n), A0, A1, ns, L, profile)
+
+
+@pytest.mark.parametrize("mutant", ["swapped_coeffs", "profile_swap", "missing_cube", "length_plus_one"])
+def test_amp_pins_catch_planted_mistakes(oracle, mutant):
+    A0, A1, ns, L = 0.25, 1.0, 1000, 4000
+
+    def amp(n):
+        n = np.asarray(n, dtype=np.float64)
+        tau = np.clip((n - ns) / (L + 1 if mutant == "length_plus_one" else L), 0.0, 1.0)
+        if mutant == "swapped_coeffs":
+            s = tau**3 * (6 - 15 * tau + 10 * tau**2)
+        elif mutant == "profile_swap":
+            s = tau
+        elif mutant == "missing_cube":
+            s = np.where((tau > 0) & (tau < 1), 10 - 15 * tau + 6 * tau**2, tau)
+        else:
+            s = tau**3 * (10 - 15 * tau + 6 * tau**2)
+        return A0 + (A1 - A0) * s
+
+    with pytest.raises(AssertionError):
+        _check_amp_pins(amp, A0, A1, ns, L, 1)
+
+
+def test_amp_ramp_seen_through_the_render(oracle):
+    """A tone at f_s/4 with phase pi/2 reads sin = 1 exactly at every fourth sample, so the
+    rendered sum there is the amplitude itself: the ramp enters x[n] as a_j[i] sin(phi_j[i])."""
+    fs = 2.0**28
+    w = oracle.make_waveform(fs, [fs / 4], [0.3], [np.pi / 2])
+    oracle.add_ramps(w, [dict(tone=0, amp_end=0.9, duration=4000 / fs, profile=1, start_sample=800)])
+    x = oracle.render(w, 0, 6000)
+    n = np.arange(0, 6000, 4)
+    assert np.array_equal(x[n], oracle.amp_at(0.3, 1, 800, 4000, 0.9, n))
