@@ -260,9 +260,16 @@ def static_leg(awg, stream, reps: int = 5):
     f = 80e6 + 1e4 * np.sort(rng.choice(10000, 10000, replace=False)).astype(np.float64)
     cases = {"static-100tone-2^20": (c1.fs, c1.freq_hz, c1.amp, c1.phase_rad, c1.n_samples),
              "static-10000tone-2^22": (280e6, f, np.full(10000, 1e-4), rng.uniform(0, 2 * np.pi, 10000), 1 << 22)}
+    # the same comb with 100 tones fading (minimum-jerk amplitude ramps of 1 ms) inside the record
+    ramps = [dict(tone=int(t), amp_end=0.0 if i % 2 else 2e-4, duration=1e-3, profile=1,
+                  start_sample=int(rng.integers(0, (1 << 22) - 280000)))
+             for i, t in enumerate(rng.choice(10000, 100, replace=False))]
+    cases["static-10000tone-2^22+100ramps"] = cases["static-10000tone-2^22"]
     for name, (fs, fr, amp, th, n) in cases.items():
         synth = awg.Synth(fs)
         synth.set_tones(fr, amp, th)
+        if name.endswith("ramps"):
+            synth.set_ramp_list(ramps)
         q = torch.empty(n, dtype=torch.int16, device="cuda")
         res = {}
         for mode, label in ((awg.SINE_SFU, "sfu"), (awg.SINE_ROTATOR, "rotator")):

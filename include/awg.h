@@ -120,6 +120,22 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
                    const double* duration_s, const int32_t* profile, const int64_t* start_sample,
                    int32_t n);
 
+/* Schedule n amplitude ramps (the time-varying amplitude a_j[i] of Eq. dynamicandstatic, e.g. to
+ * switch tweezers on and off smoothly).  Ramp i moves tone[i]'s amplitude from its current value
+ * to amp_end[i] over L = rint(duration[i] fs) samples (1 <= L < 2^28) starting at absolute sample
+ * start_sample[i]: a(n) = A + (amp_end - A) s(tau), tau = (n - start)/L, with s(tau) = tau
+ * (AWG_PROFILE_LINEAR) or 10 tau^3 - 15 tau^4 + 6 tau^5 (AWG_PROFILE_MINJERK, the minimum-jerk
+ * profile of Eq. freqchirp); a = A before the ramp and amp_end after it.  Ramps and chirps are
+ * independent (a tone may do both at once).  A tone holds one ramp at a time: a new ramp is
+ * accepted once the cursor has passed the previous one's end, whose amp_end becomes the tone's
+ * amplitude.  Ramps start at or after the cursor; one ramp per tone per call.  Full scale is not
+ * changed: set it explicitly (awg_set_full_scale) when amplitudes ramp above their initial
+ * values, since the default sum |A_k| could then clip.  Tiles in which a ramp is under way are
+ * rendered by the kernel's general per-sample path (amplitude in FP32, error <= 6e-7 |amp_end - A|).
+ * EINVAL on any violation (nothing is applied). */
+int awg_set_amp_ramps(awg_t* h, const int32_t* tone, const double* amp_end, const double* duration_s,
+                      const int32_t* profile, const int64_t* start_sample, int32_t n);
+
 /* Full-scale value FS that maps to int16 code 32767 (q = clamp(rint(x * 32767/FS), +-32767)).
  * fs_value <= 0 restores the default sum |A_k|, which can never clip. */
 int awg_set_full_scale(awg_t* h, double fs_value);

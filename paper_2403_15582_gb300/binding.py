@@ -30,6 +30,7 @@ SIGNATURES = [
     ("awg_set_tones", ctypes.c_int, [P, P, P, P, i32]),
     ("awg_set_tones_grid", ctypes.c_int, [P, P, i32, P, P, i32]),
     ("awg_set_chirps", ctypes.c_int, [P, P, P, P, P, P, P, i32]),
+    ("awg_set_amp_ramps", ctypes.c_int, [P, P, P, P, P, P, i32]),
     ("awg_set_full_scale", ctypes.c_int, [P, dbl]),
     ("awg_full_scale", dbl, [P]),
     ("awg_sample_rate", dbl, [P]),
@@ -232,6 +233,20 @@ class Synth:
 
     def render(self, n: int, out, stream=None):
         _check(lib().awg_render(self._h, int(n), _ptr(out), _stream_ptr(stream)))
+
+    def set_amp_ramps(self, tone, amp_end, duration_s, profile, start_sample):
+        t = np.ascontiguousarray(tone, dtype=np.int32)
+        a, d = _f64(amp_end), _f64(duration_s)
+        p = np.ascontiguousarray(profile, dtype=np.int32)
+        s0 = np.ascontiguousarray(start_sample, dtype=np.int64)
+        _check(lib().awg_set_amp_ramps(self._h, _p(t), _p(a), _p(d), _p(p), _p(s0), int(t.size)))
+
+    def set_ramp_list(self, ramps):
+        """Ramps as dicts {tone, amp_end, duration, profile, start_sample}."""
+        r = list(ramps)
+        if r:
+            self.set_amp_ramps([x["tone"] for x in r], [x["amp_end"] for x in r], [x["duration"] for x in r],
+                               [x["profile"] for x in r], [x.get("start_sample", 0) for x in r])
 
     def set_sine_mode(self, mode: int):
         """SINE_SFU (default) or SINE_ROTATOR for static tone segments."""

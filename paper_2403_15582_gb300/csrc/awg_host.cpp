@@ -1045,7 +1045,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     t.F_end = p.F1;
     rotation_of(p.F1, &t.rot_c_end, &t.rot_s_end);
     t.phi_post_ref = phi_end - (uint64_t)t.n_e * p.F1;
-    t.flags = c.flags;
+    t.flags = (t.flags & (awgk::TONE_AMP_RAMP | awgk::TONE_AMP_MINJERK)) | c.flags;
   }
   // only the records that changed go to the device (the whole chirp array if it had to grow)
   std::sort(changed_tones.begin(), changed_tones.end());
@@ -1063,6 +1063,47 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   for (const ChirpRec& c : h->chirps) any_exact |= (c.tone >= 0 && (c.flags & awgk::TONE_EXACT));
   if (any_exact) return upload_tones(h);   // table offsets may have moved for any exact tone
   return upload_runs(h->d_tones, h->tones, changed_tones, "upload tones");
+}
+
+int awg_set_amp_ramps(awg_t* h, const int32_t* tone, const double* amp_end, const double* duration_s,
+                      const int32_t* profile, const int64_t* start_sample, int32_t n) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (n < 0) return fail(AWG_EINVAL, "ramp count must be >= 0");
+  if (n == 0) return AWG_OK;
+  if (!tone || !amp_end || !duration_s || !profile || !start_sample) return fail(AWG_EINVAL, "null ramp array");
+  std::vector<char> seen((size_t)h->K, 0);
+  std::vector<int64_t> L((size_t)n);
+  for (int32_t i = 0; i < n; ++i) {
+    const int32_t k = tone[i];
+    if (k < 0 || k >= h->K) return fail(AWG_EINVAL, "ramp tone index out of range");
+    if (seen[(size_t)k]) return fail(AWG_EINVAL, "two ramps for one tone in one call");
+    seen[(size_t)k] = 1;
+    if (!is_fin(amp_end[i]) || std::fabs(amp_end[i]) > 3.0e38) return fail(AWG_EINVAL, "ramp amplitude must be finite");
+    int st = chirp_length_impl(duration_s[i], h->fs, &L[(size_t)i]);
+    if (st) return st;
+    if (profile[i] != AWG_PROFILE_LINEAR && profile[i] != AWG_PROFILE_MINJERK) return fail(AWG_EINVAL, "unknown ramp profile");
+    if (start_sample[i] < h->cursor) return fail(AWG_EINVAL, "ramp starts before the render cursor");
+    if (start_sample[i] > INT64_MAX / 2) return fail(AWG_EINVAL, "ramp start too large");
+    const ToneRec& t = h->tones[(size_t)k];
+    if ((t.flags & awgk::TONE_AMP_RAMP) && t.a_ns + t.a_L >= h->cursor)
+      return fail(AWG_EINVAL, "tone already has a ramp that has not finished rendering");
+  }
+  int st = wait_idle(h);
+  if (st) return st;
+  h->periodic_start = -1;
+  std::vector<int32_t> changed;
+  for (int32_t i = 0; i < n; ++i) {
+    ToneRec& t = h->tones[(size_t)tone[i]];
+    if (t.flags & awgk::TONE_AMP_RAMP) t.A = t.A_end;   // fold the finished ramp
+    t.a_ns = start_sample[i];
+    t.a_L = (int32_t)L[(size_t)i];
+    t.A_end = (float)amp_end[i];
+    t.flags = (t.flags & ~(awgk::TONE_AMP_RAMP | awgk::TONE_AMP_MINJERK)) | awgk::TONE_AMP_RAMP |
+              (profile[i] == AWG_PROFILE_MINJERK ? awgk::TONE_AMP_MINJERK : 0);
+    changed.push_back(tone[i]);
+  }
+  std::sort(changed.begin(), changed.end());
+  return upload_runs(h->d_tones, h->tones, changed, "upload tones");
 }
 
 int awg_set_full_scale(awg_t* h, double v) {
@@ -1121,8 +1162,10 @@ int awg_set_periodic(awg_t* h, int32_t log2_len, int32_t method, void* stream) {
     v.rot_s = chirped ? t.rot_s_end : t.rot_s;
     v.n_s = awgk::NO_CHIRP;
     v.n_e = awgk::NO_CHIRP;
-    v.A = t.A;
+    const bool ramped = (t.flags & awgk::TONE_AMP_RAMP) != 0;
+    v.A = ramped ? t.A_end : t.A;
     v.slot = -1;
+    if (ramped) start = std::max(start, ((t.a_ns + t.a_L) / awgk::TILE + 1) * awgk::TILE);
     if (v.F & grid_mask) return fail(AWG_EINVAL, "a tone's final frequency is not on the f_s / 2^log2_len grid");
     // from the first whole tile after the chirp the render takes the static path, so replayed
     // samples equal rendered ones bit for bit in either sine mode
@@ -1312,6 +1355,7 @@ int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q
   const uint64_t grid_mask = (log2_len >= 64) ? 0 : ((1ull << (64 - log2_len)) - 1);
   for (const ToneRec& t : h->tones) {
     if (t.slot >= 0) return fail(AWG_EINVAL, "table GEMM needs static tones (a tone holds a chirp)");
+    if (t.flags & awgk::TONE_AMP_RAMP) return fail(AWG_EINVAL, "table GEMM needs constant amplitudes (a tone holds a ramp)");
     if (t.F & grid_mask) return fail(AWG_EINVAL, "table GEMM needs every tone on the f_s / 2^log2_len grid");
   }
   const int64_t M = (int64_t)1 << (log2_len - 8);

@@ -23,7 +23,7 @@ constexpr int MAX_ACTIVE_PER_LAUNCH = 1024;
 
 constexpr int64_t NO_CHIRP = INT64_MAX;
 
-// Per-tone record read by the render kernel.  80 bytes, 16-byte aligned (bulk-copied).
+// Per-tone record read by the render kernel.  96 bytes, 16-byte aligned (bulk-copied).
 struct alignas(16) ToneRec {
   uint64_t phi_ref;       // static segment before the chirp (or the only one): Phi(n) = phi_ref + n F
   uint64_t F;
@@ -37,10 +37,15 @@ struct alignas(16) ToneRec {
   int32_t tab_off;        // TONE_EXACT: offset of this chirp's per-sample phase table
   float rot_c, rot_s;     // cos, sin of the per-sample step 2 pi F / 2^64 (rotator sine variant)
   float rot_c_end, rot_s_end;   // the same for F_end
+  int64_t a_ns;           // amplitude ramp (TONE_AMP_RAMP): A -> A_end over samples a_ns .. a_ns + a_L
+  float A_end;
+  int32_t a_L;
 };
-static_assert(sizeof(ToneRec) == 80, "ToneRec layout");
+static_assert(sizeof(ToneRec) == 96, "ToneRec layout");
 constexpr int32_t TONE_EXACT = 1;    // chirp read from a per-sample table of exact phases
 constexpr int32_t TONE_LINEAR = 2;   // linear chirp: differences of order >= 3 are exactly zero
+constexpr int32_t TONE_AMP_RAMP = 4;      // the amplitude ramps (see ToneRec::a_ns)
+constexpr int32_t TONE_AMP_MINJERK = 8;   // ... along the minimum-jerk profile (else linear)
 
 // Per-chirp record (one per live slot): the 192-bit forward-difference words.
 struct alignas(16) ChirpRec {

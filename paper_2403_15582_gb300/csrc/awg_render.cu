@@ -410,12 +410,28 @@ __global__ void __launch_bounds__(128) prep_kernel(const __grid_constant__ PrepA
 // render
 // ------------------------------------------------------------------------------------------
 // Per (tone, run) contribution of one staged tone, added into the thread's RUN partial sums.
+// Amplitude a(n) of a ramping tone (TONE_AMP_RAMP): A before a_ns, A_end from a_ns + a_L on, and
+// A + (A_end - A) s(tau) between, tau = (n - a_ns) / a_L, s linear or minimum-jerk
+// (10 tau^3 - 15 tau^4 + 6 tau^5).  FP32; error <= 6e-7 |A_end - A|.
+__device__ float ramp_amp(const ToneRec& t, int64_t n) {
+  if (n <= t.a_ns) return t.A;
+  const int64_t m = n - t.a_ns;
+  if (m >= t.a_L) return t.A_end;
+  const float tau = (float)m / (float)t.a_L;
+  const float s = (t.flags & TONE_AMP_MINJERK) ? tau * tau * tau * fmaf(tau, fmaf(6.f, tau, -15.f), 10.f) : tau;
+  return fmaf(t.A_end - t.A, s, t.A);
+}
+
 __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, const RunBin& rb, float* col,
                                          float (&acc)[RUN], int64_t T0, int64_t n0, const uint32_t* exact_tab) {
-  const float A = tr.A;
+  const bool ramp = (tr.flags & TONE_AMP_RAMP) != 0;
+  const bool ramp_run = ramp && n0 + RUN - 1 > tr.a_ns && n0 < tr.a_ns + tr.a_L;   // a(n) varies in the run
+  const float A = (ramp && n0 >= tr.a_ns + tr.a_L) ? tr.A_end : tr.A;
   const int tcls = classify_tile(tr, T0);
   int mode;   // 0 static before the chirp, 1 static after, 2 chirp polynomial, 3 general
-  if (tcls == TILE_PRE) {
+  if (ramp_run) {
+    mode = 3;
+  } else if (tcls == TILE_PRE) {
     mode = 0;
   } else if (tcls == TILE_POST) {
     mode = 1;
@@ -454,7 +470,7 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
     const uint32_t p_post = static_p0(tr.phi_post_ref, tr.F_end, n0), f_post = static_f(tr.F_end);
     const bool exact = (tr.flags & TONE_EXACT) != 0;
     RunPoly st = {0, 0, 0, 0};
-    if (!exact) st = poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0);
+    if (!exact && tcls == TILE_CHIRP) st = poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0);
     const int64_t r1 = tr.n_s - n0, r2 = tr.n_e - n0;
     uint32_t pp = st.p, ff = st.f, gg = st.g;
     for (int r = 0; r < RUN; ++r) {
@@ -467,8 +483,13 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
       ff += gg;
       gg += st.h;
     }
+    if (ramp_run) {
 #pragma unroll
-    for (int r = 0; r < RUN; ++r) acc[r] = fmaf(A, col[r * NT], acc[r]);
+      for (int r = 0; r < RUN; ++r) acc[r] = fmaf(ramp_amp(tr, n0 + r), col[r * NT], acc[r]);
+    } else {
+#pragma unroll
+      for (int r = 0; r < RUN; ++r) acc[r] = fmaf(A, col[r * NT], acc[r]);
+    }
   }
 }
 
@@ -539,7 +560,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     if (tid < cnt) {
       const ToneRec& tr = s_tone[b][tid];
       Desc d;
-      d.A = tr.A;
+      const bool ramp = (tr.flags & TONE_AMP_RAMP) != 0;
+      d.A = (ramp && T0 >= tr.a_ns + tr.a_L) ? tr.A_end : tr.A;
       d.c = d.s = 0.f;
       const int tcls = classify_tile(tr, T0);
       const bool exact = (tr.flags & TONE_EXACT) != 0;
@@ -563,6 +585,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
           src = a.recs + (int64_t)a.act_of_slot[tr.slot] * (a.rec_stride ? a.rec_stride : a.n_tiles) + a.rec_tile0 + tile;
         }
       }
+      // an amplitude ramp inside the tile: the general per-sample path
+      if (ramp && T0 + TILE - 1 > tr.a_ns && T0 < tr.a_ns + tr.a_L) d.kind = DESC_MIXED;
       s_desc[b][tid] = d;
     }
     const unsigned mask = __ballot_sync(0xffffffffu, need);
