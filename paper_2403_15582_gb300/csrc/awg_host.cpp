@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/awg.h"
@@ -121,8 +122,24 @@ Big big_shl(const Big& a, int s) {   // s < 512
   return r;
 }
 uint64_t big_divmod_u64(Big& a, uint64_t d) {   // a /= d, returns remainder
+  int top = 7;
+  while (top > 0 && a.l[top] == 0) --top;         // leading zero limbs stay zero
+  if (d < (1ull << 32)) {
+    // 32-bit halves: every partial dividend is below 2^64, so 64-bit hardware division does
+    uint64_t rem = 0;
+    for (int i = top; i >= 0; --i) {
+      const uint64_t hi = (rem << 32) | (a.l[i] >> 32);
+      const uint64_t qh = hi / d;
+      rem = hi - qh * d;
+      const uint64_t lo = (rem << 32) | (a.l[i] & 0xFFFFFFFFull);
+      const uint64_t ql = lo / d;
+      rem = lo - ql * d;
+      a.l[i] = (qh << 32) | ql;
+    }
+    return rem;
+  }
   u128 rem = 0;
-  for (int i = 7; i >= 0; --i) {
+  for (int i = top; i >= 0; --i) {
     u128 cur = (rem << 64) | a.l[i];
     a.l[i] = (uint64_t)(cur / d);
     rem = cur % d;
@@ -147,7 +164,7 @@ int big_cmp(const Big& a, const Big& b) {
 }
 
 // Delta^k [m^p] at m = 0 = sum_j (-1)^(k-j) C(k,j) j^p  (k! S(p,k), Stirling numbers of the 2nd kind)
-s128 power_difference(int p, int k) {
+s128 power_difference_sum(int p, int k) {
   s128 s = 0;
   s128 binom = 1;   // C(k, j)
   for (int j = 0; j <= k; ++j) {
@@ -157,6 +174,18 @@ s128 power_difference(int p, int k) {
     s += (((k - j) & 1) ? -1 : 1) * binom * pw;
   }
   return s;
+}
+
+// The same values, tabulated once (p, k <= 6): they are constants of every chirp's set-up.
+s128 power_difference(int p, int k) {
+  static const struct Table {
+    s128 v[7][7];
+    Table() {
+      for (int pp = 0; pp <= 6; ++pp)
+        for (int kk = 0; kk <= 6; ++kk) v[pp][kk] = power_difference_sum(pp, kk);
+    }
+  } table;
+  return table.v[p][k];
 }
 
 // round_half_even( sign * mag * 2^127 / L^pw ), returned mod 2^192
@@ -1003,8 +1032,34 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   if (st) return st;
   h->periodic_start = -1;
   const size_t slots_before = h->chirps.size();
+  // the coefficient words, end offsets and exact-table flags of every chirp: pure functions of
+  // the chirp, computed on several host threads for large batches
+  struct Coeffs {
+    W192 d[7];
+    uint64_t end_offset;
+    bool exact;
+  };
+  std::vector<Coeffs> co(pend.size());
+  auto work = [&](size_t lo, size_t hi) {
+    for (size_t i = lo; i < hi; ++i) {
+      const Pending& p = pend[i];
+      (void)chirp_coeffs_impl(p.F0, p.F1, p.L, p.profile, co[i].d);   // validated above
+      co[i].end_offset = chirp_offset_word(co[i].d, p.L);
+      co[i].exact = needs_exact(p.F0, p.F1, p.L, p.profile);
+    }
+  };
+  const size_t n_threads = std::min<size_t>({8, std::max(1u, std::thread::hardware_concurrency()), pend.size() / 64 + 1});
+  if (n_threads <= 1) {
+    work(0, pend.size());
+  } else {
+    std::vector<std::thread> pool;
+    for (size_t t = 0; t < n_threads; ++t)
+      pool.emplace_back(work, pend.size() * t / n_threads, pend.size() * (t + 1) / n_threads);
+    for (std::thread& th : pool) th.join();
+  }
   std::vector<int32_t> changed_tones, changed_slots;
-  for (const Pending& p : pend) {
+  for (size_t pi = 0; pi < pend.size(); ++pi) {
+    const Pending& p = pend[pi];
     ToneRec& t = h->tones[(size_t)p.tone];
     changed_tones.push_back(p.tone);
     if (t.slot >= 0) {   // fold the finished chirp into the static state
@@ -1016,9 +1071,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
       h->free_slots.push_back(t.slot);
       t.slot = -1;
     }
-    W192 d[7];
-    st = chirp_coeffs_impl(p.F0, p.F1, p.L, p.profile, d);
-    if (st) return st;   // validated above; cannot fail
+    const W192* d = co[pi].d;
     int32_t slot;
     if (!h->free_slots.empty()) {
       slot = h->free_slots.back();
@@ -1036,9 +1089,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     c.n_s = p.ns;
     c.L = p.L;
     c.tone = p.tone;
-    c.flags = (needs_exact(p.F0, p.F1, p.L, p.profile) ? awgk::TONE_EXACT : 0) |
-              (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0);
-    const uint64_t phi_end = c.phi_start + chirp_offset_word(d, p.L);
+    c.flags = (co[pi].exact ? awgk::TONE_EXACT : 0) | (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0);
+    const uint64_t phi_end = c.phi_start + co[pi].end_offset;
     t.slot = slot;
     t.n_s = p.ns;
     t.n_e = p.ns + p.L;
