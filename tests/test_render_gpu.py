@@ -358,3 +358,51 @@ def test_set_chirps_validation(awg):
     s.render(1000, q)
     with pytest.raises(awg.AwgError):
         s.set_chirps([1], [80e6], [90e6], [1e-3], [0], [10])     # starts before the cursor
+
+
+def test_maximum_sizes(awg, oracle):
+    """Large tone counts (65,536 tones: 4096 per CTA of a 16-CTA cluster) far into the stream, and
+    one render call of more than 2^30 samples (output offsets beyond 2^31 bytes), each checked at
+    sampled indices against the oracle's closed form."""
+    rng = np.random.default_rng(77)
+    fs = 280e6
+    K = 65536
+    f = rng.uniform(0, fs, K)
+    a = rng.uniform(-1, 1, K) / 256
+    th = rng.uniform(0, 2 * np.pi, K)
+    chirps = [dict(tone=int(t), f_start=float(f[t]), f_end=float(rng.uniform(1e6, 139e6)),
+                   duration=float(rng.uniform(1e-3, 5e-3)), profile=int(t % 2), start_sample=(1 << 33) + int(rng.integers(0, 200000)))
+              for t in rng.choice(K, 1000, replace=False)]
+    s = awg.Synth(fs)
+    s.set_tones(f, a, th)
+    s.seek(1 << 33)
+    s.set_chirp_list(chirps)
+    n = 1 << 20
+    q = torch.empty(n, dtype=torch.int16, device="cuda")
+    x = torch.empty(n, dtype=torch.float32, device="cuda")
+    s.render_f32(n, x, q)
+    torch.cuda.synchronize()
+    assert s.device_status() == 0 and s.tone_split == 16
+    w = oracle.make_waveform(fs, f, a, th, chirps)
+    idx = np.unique(rng.integers(0, n, 200))
+    x_ref = oracle.render_at(w, (1 << 33) + idx, nthreads=NTHREADS)
+    xs = x.cpu().numpy()[idx].astype(np.float64)
+    assert np.max(np.abs(xs - x_ref)) <= fp32_bound(a, 16)
+    q_ref = oracle.quantize(x_ref, w.full_scale())
+    assert np.max(np.abs(q.cpu().numpy()[idx].astype(np.int32) - q_ref)) <= 1
+
+    # one call of 2^30 + 4097 samples (2 GiB of int16)
+    f2, a2, th2 = [12.5e6, 77.77e6, 133e6], [0.5, -0.3, 0.2], [0.1, 0.2, 0.3]
+    s2 = awg.Synth(fs)
+    s2.set_tones(f2, a2, th2)
+    N = (1 << 30) + 4097
+    big = torch.empty(N, dtype=torch.int16, device="cuda")
+    s2.render(N, big)
+    torch.cuda.synchronize()
+    assert s2.device_status() == 0 and s2.cursor == N
+    w2 = oracle.make_waveform(fs, f2, a2, th2)
+    idx2 = np.unique(np.concatenate([rng.integers(0, N, 100), rng.integers(N - (1 << 20), N, 100), [N - 1, 1 << 30]]))
+    q2 = oracle.quantize(oracle.render_at(w2, idx2, nthreads=NTHREADS), w2.full_scale())
+    got = big[torch.as_tensor(idx2, device="cuda")].cpu().numpy().astype(np.int32)
+    assert np.max(np.abs(got - q2)) <= 1
+    del big
