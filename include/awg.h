@@ -167,6 +167,21 @@ enum { AWG_SINE_SFU = 0, AWG_SINE_ROTATOR = 1 };
 int awg_set_sine_mode(awg_t* h, int32_t mode);
 int32_t awg_sine_mode(const awg_t* h);
 
+/* Engine for static tones.  AWG_STATIC_DIRECT (default): every tone through the render kernel.
+ * AWG_STATIC_GEMM_FP16 / _BF16: in every 4096-sample tile, the tones that are static there (no
+ * chirp and no amplitude ramp under way in the tile; before or after the tone's chirp) are summed
+ * on the tensor cores by the table GEMM of awg_table_gemm, over 256-sample rows aligned to
+ * absolute sample indices (x[256 r + c] = sum_k [A_k sin a_k(r)] cos b_k(c) + [A_k cos a_k(r)]
+ * sin b_k(c) from exact phase words, split-precision operands, FP32 accumulation; two column
+ * pairs per tone, one per segment); the remaining tones go through the render kernel, which adds
+ * the GEMM's FP32 sum before quantising.  Within one engine a sample's value
+ * does not depend on how the stream is cut into calls.  Output stays within 1 LSB of the oracle;
+ * it is not bit-identical to the direct engine.  awg_render_chunks renders chunk by chunk with a
+ * GEMM engine; awg_render_noalloc always uses the direct engine.  AWG_EINVAL for other values. */
+enum { AWG_STATIC_DIRECT = 0, AWG_STATIC_GEMM_FP16 = 1, AWG_STATIC_GEMM_BF16 = 2 };
+int awg_set_static_engine(awg_t* h, int32_t engine);
+int32_t awg_static_engine(const awg_t* h);
+
 /* Periodic hand-off (the end state of the Playback pathway, Sec. IV-C: once the chirps are over
  * the output is a periodic waveform).  When every tone's final frequency (after its chirp, if it
  * has one) lies on the f_s / 2^log2_len grid (Eq. freqapprox), the waveform from

@@ -13,6 +13,7 @@ AWG_OK, AWG_EINVAL, AWG_ENOMEM, AWG_ECUDA, AWG_ETIMEOUT, AWG_EDEADLINE, AWG_ESTA
 PREC_BF16, PREC_FP16 = 0, 1
 SINE_SFU, SINE_ROTATOR = 0, 1
 PERIODIC_DIRECT, PERIODIC_GEMM_BF16, PERIODIC_GEMM_FP16 = 0, 1, 2
+STATIC_DIRECT, STATIC_GEMM_FP16, STATIC_GEMM_BF16 = 0, 1, 2
 PROFILE_LINEAR, PROFILE_MINJERK = 0, 1
 
 # (name, restype, argtypes) of every symbol declared in include/awg.h
@@ -55,6 +56,8 @@ SIGNATURES = [
     ("awg_cursor", i64, [P]),
     ("awg_set_sine_mode", ctypes.c_int, [P, i32]),
     ("awg_sine_mode", i32, [P]),
+    ("awg_set_static_engine", ctypes.c_int, [P, i32]),
+    ("awg_static_engine", i32, [P]),
     ("awg_set_periodic", ctypes.c_int, [P, i32, i32, P]),
     ("awg_periodic_start", i64, [P]),
     ("awg_clear_periodic", ctypes.c_int, [P]),
@@ -255,6 +258,14 @@ class Synth:
     @property
     def sine_mode(self) -> int:
         return int(lib().awg_sine_mode(self._h))
+
+    def set_static_engine(self, engine: int):
+        """STATIC_DIRECT (default), STATIC_GEMM_FP16 or STATIC_GEMM_BF16 for window-static tones."""
+        _check(lib().awg_set_static_engine(self._h, int(engine)))
+
+    @property
+    def static_engine(self) -> int:
+        return int(lib().awg_static_engine(self._h))
 
     def set_periodic(self, log2_len: int, method: int = 0, stream=None):
         """Periodic hand-off after the chirps (PERIODIC_DIRECT, PERIODIC_GEMM_BF16 / _FP16)."""

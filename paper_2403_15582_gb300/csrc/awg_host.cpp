@@ -367,6 +367,9 @@ struct awg {
   bool fs_explicit = false;
   int split = 1;
   int32_t sine_mode = AWG_SINE_SFU;
+  int32_t static_engine = AWG_STATIC_DIRECT;
+  float* d_base = nullptr;             // tensor-core engine: FP32 sum of the window's static tones
+  size_t cap_base = 0;
   // periodic hand-off: from sample periodic_start on, x[n] = periodic table[n mod 2^periodic_log2]
   int16_t* d_periodic = nullptr;
   size_t cap_periodic = 0;
@@ -563,7 +566,19 @@ int build_exact_tables(awg_t* h) {
   return AWG_OK;
 }
 
+int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride,
+                  const float* base, int32_t skip_static);
+int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride);
+
 int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride = 1) {
+  if (h && h->static_engine != AWG_STATIC_DIRECT && n > 0 && (out_f || out_q) &&
+      !(h->periodic_start >= 0 && !out_f && h->cursor + n > h->periodic_start))
+    return render_engine(h, n, out_f, out_q, stream, q_stride);
+  return render_direct(h, n, out_f, out_q, stream, q_stride, nullptr, 0);
+}
+
+int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride,
+                  const float* base, int32_t skip_static) {
   if (!h) return fail(AWG_EINVAL, "null handle");
   if (n < 0) return fail(AWG_EINVAL, "sample count must be >= 0");
   if (n == 0) return AWG_OK;
@@ -653,6 +668,8 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream,
   ra.split = h->split;
   ra.sine_mode = h->sine_mode;
   ra.q_stride = q_stride;
+  ra.base = base;
+  ra.skip_static = skip_static;
   ra.tile0 = tile0;
   ra.n_tiles = n_tiles;
   ra.win_start = c;
@@ -674,6 +691,76 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream,
   h->timed = true;
   h->have_done = true;
   h->cursor = c + n;
+  return AWG_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Tensor-core static engine: in every 4096-sample tile, the tones that are static there
+// (tile_segment_static, either segment of the tone) are summed by the table GEMM over 256-sample
+// rows aligned to absolute sample indices, two column pairs per tone (before and after its
+// chirp); the others by the render kernel, which skips the static ones and adds the GEMM's FP32
+// sum before quantising.  The split depends on the tile and the tone state only, so a sample's
+// value does not depend on how the stream is cut into calls.  Pieces of at most 2^26 samples.
+int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t PIECE = (int64_t)1 << 26;
+  for (int64_t off = 0; off < n; off += PIECE) {
+    const int64_t m = std::min(PIECE, n - off), c = h->cursor;
+    // every tone static (one segment, constant amplitude) in every tile the piece touches: the
+    // GEMM writes the output itself
+    const int64_t t_first = c / awgk::TILE, t_last = (c + m - 1) / awgk::TILE;
+    bool all_static = q_stride == 1 && h->K > 0;
+    for (size_t k = 0; k < h->tones.size() && all_static; ++k) {
+      const ToneRec& t = h->tones[k];
+      const int64_t s0 = t_first * awgk::TILE, s1 = (t_last + 1) * awgk::TILE - 1;
+      if (t.slot >= 0 && !(s1 < t.n_s || s0 > t.n_e)) all_static = false;
+      if ((t.flags & awgk::TONE_AMP_RAMP) && !(s1 <= t.a_ns || s0 >= t.a_ns + t.a_L)) all_static = false;
+    }
+    int16_t* oq = out_q ? out_q + (size_t)off * (size_t)q_stride : nullptr;
+    float* of = out_f ? out_f + off : nullptr;
+    int st;
+    if (h->K == 0) {
+      if ((st = render_direct(h, m, of, oq, stream, q_stride, nullptr, 0))) return st;
+      continue;
+    }
+    const size_t Kp = awgk::table_kp_window(std::max(h->K, 1));
+    const size_t b_elems = (size_t)256 * Kp;
+    if ((st = ensure(&h->d_gemm, &h->cap_gemm, 2 * b_elems, h, "table GEMM operands"))) return st;
+    if (!all_static && (st = ensure(&h->d_base, &h->cap_base, (size_t)m, h, "static sum"))) return st;
+    awgk::TableArgs2 t;
+    std::memset(&t, 0, sizeof(t));
+    t.tones = h->d_tones;
+    t.K = h->K;
+    t.nb_log2 = 8;
+    t.row_base = c >> 8;
+    t.M = ((c + m - 1) >> 8) - t.row_base + 1;
+    t.win_start = c;
+    t.win_end = c + m;
+    t.window_mode = 1;
+    t.precision = h->static_engine == AWG_STATIC_GEMM_FP16 ? AWG_PREC_FP16 : AWG_PREC_BF16;
+    t.b_hi = h->d_gemm;
+    t.b_lo = h->d_gemm + b_elems;
+    t.out_q = all_static ? oq : nullptr;
+    t.out_f = all_static ? of : h->d_base;
+    t.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
+    t.status = h->d_status;
+    cudaError_t e;
+    if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
+    if ((e = awgk::launch_table_prep(t, s)) != cudaSuccess) return cuda_fail(e, "static operand launch");
+    if ((e = awgk::launch_table_gemm(t, s)) != cudaSuccess) return cuda_fail(e, "static GEMM launch");
+    if (all_static) {
+      if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
+      if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
+      h->timed = true;
+      h->have_done = true;
+      h->cursor = c + m;
+      continue;
+    }
+    if ((st = render_direct(h, m, of, oq, stream, q_stride, h->d_base, 1))) return st;
+  }
   return AWG_OK;
 }
 
@@ -967,6 +1054,7 @@ void awg_destroy(awg_t* h) {
   cudaFree(h->d_act);
   cudaFree(h->d_recs);
   cudaFree(h->d_periodic);
+  cudaFree(h->d_base);
   cudaFree(h->d_seq_recs);
   cudaFree(h->d_seq_act);
   cudaFree(h->d_seq_exit);
@@ -1193,6 +1281,16 @@ int awg_set_sine_mode(awg_t* h, int32_t mode) {
 
 int32_t awg_sine_mode(const awg_t* h) { return h ? h->sine_mode : -1; }
 
+int awg_set_static_engine(awg_t* h, int32_t engine) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (engine != AWG_STATIC_DIRECT && engine != AWG_STATIC_GEMM_BF16 && engine != AWG_STATIC_GEMM_FP16)
+    return fail(AWG_EINVAL, "unknown static engine");
+  h->static_engine = engine;
+  return AWG_OK;
+}
+
+int32_t awg_static_engine(const awg_t* h) { return h ? h->static_engine : -1; }
+
 int awg_set_periodic(awg_t* h, int32_t log2_len, int32_t method, void* stream) {
   if (!h) return fail(AWG_EINVAL, "null handle");
   if (log2_len < 12 || log2_len > 30) return fail(AWG_EINVAL, "log2_len must be 12..30");
@@ -1234,6 +1332,7 @@ int awg_set_periodic(awg_t* h, int32_t log2_len, int32_t method, void* stream) {
   tmp->K = h->K;
   tmp->split = h->split;
   tmp->sine_mode = h->sine_mode;
+  tmp->static_engine = h->static_engine;
   tmp->full_scale = h->full_scale;
   tmp->fs_explicit = true;
   st = upload_tones(tmp);
@@ -1307,7 +1406,7 @@ int awg_render_chunks(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, v
   if (!out) return fail(AWG_EINVAL, "null output");
   if (chunk > (INT64_MAX - h->cursor) / n_chunks) return fail(AWG_EINVAL, "sample index overflow");
   if (chunk / awgk::TILE + 2 > (int64_t)(INT32_MAX / awgk::MAX_SPLIT)) return fail(AWG_EINVAL, "chunk too long");
-  if (n_chunks == 1 || h->profiling || h->periodic_start >= 0) {
+  if (n_chunks == 1 || h->profiling || h->periodic_start >= 0 || h->static_engine != AWG_STATIC_DIRECT) {
     // per-call profiling events would split the pipeline; a periodic tail is replayed per chunk
     for (int32_t c = 0; c < n_chunks; ++c) {
       const int st = render_impl(h, chunk, nullptr, out + (size_t)c * (size_t)chunk, stream);
@@ -1423,6 +1522,10 @@ int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q
   t.precision = precision;
   t.b_hi = h->d_gemm;
   t.b_lo = h->d_gemm + b_elems;
+  t.row_base = 0;
+  t.win_start = 0;
+  t.win_end = (int64_t)M * 256;
+  t.window_mode = 0;
   t.out_q = out_q;
   t.out_f = out_f;
   t.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;

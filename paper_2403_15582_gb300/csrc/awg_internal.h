@@ -47,6 +47,42 @@ constexpr int32_t TONE_LINEAR = 2;   // linear chirp: differences of order >= 3 
 constexpr int32_t TONE_AMP_RAMP = 4;      // the amplitude ramps (see ToneRec::a_ns)
 constexpr int32_t TONE_AMP_MINJERK = 8;   // ... along the minimum-jerk profile (else linear)
 
+#if defined(__CUDACC__)
+#define AWG_HD __host__ __device__
+#else
+#define AWG_HD
+#endif
+
+// Static segments per 4096-sample tile (the tensor-core static engine): tone t is static with a
+// constant amplitude over the tile [T0, T0 + TILE) in segment seg (0: before its chirp, or the
+// only one; 1: after its chirp).  Returns the segment's phase reference, frequency word and
+// amplitude.  A function of the tile and the tone state only, so the split between the engines
+// does not depend on how the stream is cut into calls.
+AWG_HD inline bool tile_segment_static(const ToneRec& t, int64_t T0, int seg, uint64_t* phi, uint64_t* F, float* A) {
+  const int64_t T1 = T0 + TILE - 1;
+  if (seg == 0) {
+    if (t.slot >= 0 && T1 >= t.n_s) return false;
+    *phi = t.phi_ref;
+    *F = t.F;
+  } else {
+    if (t.slot < 0 || T0 <= t.n_e) return false;
+    *phi = t.phi_post_ref;
+    *F = t.F_end;
+  }
+  *A = t.A;
+  if (t.flags & TONE_AMP_RAMP) {
+    if (T1 <= t.a_ns) *A = t.A;
+    else if (T0 >= t.a_ns + t.a_L) *A = t.A_end;
+    else return false;
+  }
+  return true;
+}
+AWG_HD inline bool tile_static(const ToneRec& t, int64_t T0) {
+  uint64_t phi, F;
+  float A;
+  return tile_segment_static(t, T0, 0, &phi, &F, &A) || tile_segment_static(t, T0, 1, &phi, &F, &A);
+}
+
 // Per-chirp record (one per live slot): the 192-bit forward-difference words.
 struct alignas(16) ChirpRec {
   uint64_t d[21];         // d_0..d_6, 3 little-endian limbs each
@@ -110,6 +146,10 @@ struct RenderArgs {
   // (no data from the preceding kernel); each CTA adds 1 to *exit_ctr once its samples are stored
   int32_t pdl;
   unsigned long long* exit_ctr;
+  // tensor-core static engine (otherwise null / 0): tones static over the window are skipped here
+  // (their sum comes from the table GEMM) and base[n - win_start] is added before quantising
+  const float* base;
+  int32_t skip_static;
 };
 
 struct PhaseArgs {
@@ -166,8 +206,12 @@ cudaError_t noalloc_scratch(int device, TileRec** recs, int32_t** act);
 struct TableArgs2 {
   const ToneRec* tones;
   int32_t K;
-  int64_t M;              // rows: record length / 256
+  int64_t M;              // rows of 256 samples
   int32_t nb_log2;        // log2 of the columns (8: 256 samples per row)
+  int64_t row_base;       // absolute row index of row 0 (sample row_base * 256)
+  int64_t win_start, win_end;   // absolute samples stored (out[n - win_start])
+  int32_t window_mode;    // 1: static engine: per tone two segments (4 columns), each taken only
+                          //    in the 4096-sample tiles where it is static (tile_segment_static)
   int32_t precision;      // 0 BF16, 1 FP16 hi+lo operands
   void* b_hi;             // 256 x Kp (the A operand is generated inside the GEMM kernel)
   void* b_lo;
@@ -177,6 +221,7 @@ struct TableArgs2 {
   int32_t* status;
 };
 size_t table_kp(int K);  // padded inner dimension (2K rounded up to the K tile)
+size_t table_kp_window(int K);   // the same for the static engine's 4 columns per tone
 cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s);   // B operand halves
 cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s);   // tensor-core GEMM + epilogue
 

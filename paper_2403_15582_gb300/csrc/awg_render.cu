@@ -502,7 +502,7 @@ struct alignas(16) Desc {
   int32_t kind;
   float c, s;     // DESC_STATIC_ROT: cos and sin of the per-sample phase step
 };
-enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_STATIC_ROT = 4 };
+enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_STATIC_ROT = 4, DESC_SKIP = 5 };
 
 
 // One CTA's share of one tile: tones [K crank / split, K (crank+1) / split) of window tile `tile`
@@ -587,6 +587,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
       }
       // an amplitude ramp inside the tile: the general per-sample path
       if (ramp && T0 + TILE - 1 > tr.a_ns && T0 < tr.a_ns + tr.a_L) d.kind = DESC_MIXED;
+      if (a.skip_static && tile_static(tr, T0)) d.kind = DESC_SKIP;   // summed by the tensor-core engine
       s_desc[b][tid] = d;
     }
     const unsigned mask = __ballot_sync(0xffffffffu, need);
@@ -628,6 +629,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
         const Desc& d = s_desc[b][i];
         const int kind = d.kind;
         const float A = d.A;
+        if (kind == DESC_SKIP) continue;
         if (kind == DESC_STATIC) {
           uint32_t p = (uint32_t)((mac_u32(d.p0 + P_OFFSET, d.F, run_off)) >> 32) + HALF_TURN;
           const uint32_t f = static_f(d.F);
@@ -735,6 +737,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     if (u < per && sidx < hi) {
       const int64_t n = T0 + sidx;
       if (n >= a.win_start && n < a.win_end) {
+        if (a.base) xs[u] += a.base[n - a.win_start];
         float q = rintf(xs[u] * a.scale);
         q = fminf(fmaxf(q, -32767.f), 32767.f);
         if (a.out_q) a.out_q[(n - a.win_start) * (a.q_stride ? a.q_stride : 1)] = (int16_t)q;

@@ -123,6 +123,9 @@ struct TableGemmArgs {
   const ToneRec* tones;  // A operand source: phase word, frequency word, amplitude
   int32_t K;
   int32_t nb_log2;       // row n1 starts at sample n1 << nb_log2
+  int64_t row_base;      // absolute row of tile row 0 of tile 0
+  int64_t win_start, win_end;
+  int32_t window_mode;
 };
 
 template <typename T>
@@ -159,15 +162,30 @@ __device__ __forceinline__ float2 unpack2<__half>(uint32_t u) {
 template <typename T>
 __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint32_t row0, int g, int lane,
                                            uint32_t tile_hi, uint32_t tile_lo) {
-  const int k = kt0 + lane;
+  // table mode: lane j = tone kt0 + j (one (sin, cos) pair per tone); static engine: lane j = tone
+  // kt0 / 2 + j / 2, segment j % 2 (two pairs per tone), zero in tiles where it is not static
+  const int k = a.window_mode ? (kt0 >> 1) + (lane >> 1) : kt0 + lane;
+  const int seg = lane & 1;
   uint64_t w = 0, step = 0;
   float amp = 0.f;
   if (k < a.K) {
-    const ToneRec* t = a.tones + k;
-    const uint64_t f8 = __ldg(&t->F) << a.nb_log2;
-    w = __ldg(&t->phi_ref) + (uint64_t)(row0 + (uint32_t)g) * f8;
+    uint64_t phi, F;
+    float A;
+    if (a.window_mode) {
+      const ToneRec& t = a.tones[k];
+      phi = seg ? t.phi_post_ref : t.phi_ref;
+      F = seg ? t.F_end : t.F;
+      A = 1.f;   // per row below
+    } else {
+      const ToneRec* t = a.tones + k;
+      phi = __ldg(&t->phi_ref);
+      F = __ldg(&t->F);
+      A = __ldg(&t->A);
+    }
+    const uint64_t f8 = F << a.nb_log2;
+    w = phi + (uint64_t)(a.row_base + (int64_t)row0 + g) * f8;
     step = f8 << 2;
-    amp = __ldg(&t->A);
+    amp = A;
   }
   const uint32_t col = (uint32_t)(lane & 3) * 4u;
   const uint32_t chunk = (uint32_t)(lane >> 2);
@@ -176,7 +194,17 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
     const uint32_t r = (uint32_t)(g + 4 * i);
     float sn, cs;
     __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
-    const float sv = amp * sn, cv = amp * cs;
+    float a_row = amp;
+    if (a.window_mode) {   // the row's tile decides whether this segment is summed here
+      a_row = 0.f;
+      if (k < a.K) {
+        uint64_t p2, f2;
+        float A2;
+        const int64_t T0 = ((a.row_base + (int64_t)row0 + (int64_t)r) << a.nb_log2) & ~(int64_t)(TILE - 1);
+        if (tile_segment_static(a.tones[k], T0, seg, &p2, &f2, &A2)) a_row = A2;
+      }
+    }
+    const float sv = a_row * sn, cv = a_row * cs;
     const uint32_t hv = pack2<T>(sv, cv);
     const float2 h = unpack2<T>(hv);
     const uint32_t lv = pack2<T>(sv - h.x, cv - h.y);
@@ -344,9 +372,10 @@ __global__ void __launch_bounds__(192, 1)
     const int row = r_lo + e / TN, col = e % TN;
     float x = 0.f;
     for (int c = 0; c < split; ++c) x += cluster.map_shared_rank(part, c)[row * PART_STRIDE + col];
-    const int64_t n = (int64_t)(row0 + row) * TN + col;
-    if (a.out_q) a.out_q[n] = (int16_t)fminf(fmaxf(rintf(x * a.scale), -32767.f), 32767.f);
-    if (a.out_f) a.out_f[n] = x;
+    const int64_t n = (a.row_base + row0 + row) * TN + col;   // absolute sample
+    if (n < a.win_start || n >= a.win_end) continue;
+    if (a.out_q) a.out_q[n - a.win_start] = (int16_t)fminf(fmaxf(rintf(x * a.scale), -32767.f), 32767.f);
+    if (a.out_f) a.out_f[n - a.win_start] = x;
   }
   cluster.sync();   // remote reads done before any CTA of the cluster exits
 }
@@ -390,13 +419,18 @@ __device__ __forceinline__ void split_store(T* hi, T* lo, int64_t i, float v) {
 
 // Bt[n2][2k] = cos b_k(n2), Bt[n2][2k+1] = sin b_k(n2) (the B operand stored K-major).
 template <typename T>
-__global__ void prep_b_kernel(const ToneRec* tones, int K, int64_t Kp, T* hi, T* lo) {
+__global__ void prep_b_kernel(const ToneRec* tones, int K, int64_t Kp, T* hi, T* lo, int window_mode) {
   const int64_t pairs = Kp / 2;
   const int64_t total = (int64_t)TN * pairs;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n2 = i / pairs, k = i - n2 * pairs;
     float s = 0.f, c = 0.f;
-    if (k < K) sincos_word((uint64_t)n2 * tones[k].F, &s, &c);
+    // static engine: pair k = (tone k / 2, segment k % 2), the segment's frequency word
+    const int64_t tone = window_mode ? k >> 1 : k;
+    if (tone < K) {
+      const uint64_t F = (window_mode && (k & 1)) ? tones[tone].F_end : tones[tone].F;
+      sincos_word((uint64_t)n2 * F, &s, &c);
+    }
     split_store<T>(hi, lo, n2 * Kp + 2 * k, c);
     split_store<T>(hi, lo, n2 * Kp + 2 * k + 1, s);
   }
@@ -420,21 +454,23 @@ cudaError_t encode_2d(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt,
 }  // namespace
 
 size_t table_kp(int K) { return (((size_t)2 * K + TK - 1) / TK) * TK; }
+size_t table_kp_window(int K) { return (((size_t)4 * K + TK - 1) / TK) * TK; }
 
 cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s) {
-  const int64_t Kp = (int64_t)table_kp(t.K);
+  const int64_t Kp = (int64_t)(t.window_mode ? table_kp_window(t.K) : table_kp(t.K));
   const int threads = 256;
   const int blocks = 152 * 4;
   if (t.precision == 0)
-    prep_b_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(t.tones, t.K, Kp, (__nv_bfloat16*)t.b_hi, (__nv_bfloat16*)t.b_lo);
+    prep_b_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(t.tones, t.K, Kp, (__nv_bfloat16*)t.b_hi,
+                                                           (__nv_bfloat16*)t.b_lo, t.window_mode);
   else
-    prep_b_kernel<__half><<<blocks, threads, 0, s>>>(t.tones, t.K, Kp, (__half*)t.b_hi, (__half*)t.b_lo);
+    prep_b_kernel<__half><<<blocks, threads, 0, s>>>(t.tones, t.K, Kp, (__half*)t.b_hi, (__half*)t.b_lo, t.window_mode);
   return cudaGetLastError();
 }
 
 cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   const int64_t M = t.M;
-  const int64_t Kp = (int64_t)table_kp(t.K);
+  const int64_t Kp = (int64_t)(t.window_mode ? table_kp_window(t.K) : table_kp(t.K));
   const bool bf16 = (t.precision == 0);
   cudaError_t e;
   static EncodeTiledFn enc = nullptr;
@@ -459,6 +495,10 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   ga.tones = t.tones;
   ga.K = t.K;
   ga.nb_log2 = t.nb_log2;
+  ga.row_base = t.row_base;
+  ga.win_start = t.win_start;
+  ga.win_end = t.win_end;
+  ga.window_mode = t.window_mode;
   // instruction descriptor: FP32 accumulate, A/B BF16 (1) or FP16 (0), both K-major, N/8, M/16
   const uint32_t fmt = bf16 ? 1u : 0u;
   ga.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
@@ -470,7 +510,7 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   // K split over a cluster of up to 4 CTAs per 128-row tile
   const unsigned split = (unsigned)(ga.n_kb < 4 ? ga.n_kb : 4);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(M / TM) * split, 1, 1);
+  cfg.gridDim = dim3((unsigned)((M + TM - 1) / TM) * split, 1, 1);
   cfg.blockDim = dim3(192, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;

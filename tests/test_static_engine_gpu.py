@@ -1,0 +1,167 @@
+"""The tensor-core static engine: in each 4096-sample tile the tones that are static there (either
+segment of a chirped tone, constant amplitude) are summed by the split-precision table GEMM (rows of
+256 samples aligned to absolute indices), the rest by the render kernel, which adds the GEMM's FP32
+sum before quantising.  Parity against the oracle (int16 within 1 LSB, FP32
+within the GEMM's and the render's bounds), for static combs at any frequency far into the stream
+and for windows where chirps and amplitude ramps run beside static tones; the same samples
+however the stream is cut into calls."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NTHREADS = os.cpu_count() or 1
+FS = 280e6
+
+
+@pytest.fixture(scope="module")
+def awg(awglib):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return awglib
+
+
+def gemm_bound(amps, precision_fp16):
+    """Table GEMM bound (see the table tests) for the engine's two column pairs per tone: hi+lo
+    operands (3 u^2 per product), FP32 accumulation of 6 x 2K products, operand sines <= 5.1e-7,
+    over 2 sum |A| (a tone's two segments never both count in one tile)."""
+    u = 2.0**-11 if precision_fp16 else 2.0**-8
+    S = float(np.sum(np.abs(amps)))
+    return 2 * S * (3 * u * u + 6 * 2 * len(amps) * 2.0**-24 + 5.1e-7)
+
+
+def direct_bound(amps, split):
+    K = len(amps)
+    S = float(np.sum(np.abs(amps)))
+    return S * (5e-6 + (K / max(split, 1) + split + 2) * 2.0**-24)
+
+
+def render(s, n, n0=None):
+    if n0 is not None:
+        s.seek(n0)
+    q = torch.empty(n, dtype=torch.int16, device="cuda")
+    x = torch.empty(n, dtype=torch.float32, device="cuda")
+    s.render_f32(n, x, q)
+    torch.cuda.synchronize()
+    assert s.device_status() == 0
+    return q.cpu().numpy(), x.cpu().numpy()
+
+
+@pytest.mark.parametrize("engine", [1, 2])
+def test_static_comb_any_frequency_far_into_the_stream(awg, oracle, engine):
+    rng = np.random.default_rng(engine)
+    K = 500
+    f = rng.uniform(0, FS, K)
+    a = rng.uniform(-1, 1, K)
+    th = rng.uniform(0, 2 * np.pi, K)
+    s = awg.Synth(FS)
+    s.set_tones(f, a, th)
+    s.set_static_engine(engine)
+    assert s.static_engine == engine
+    n0, n = (1 << 35) + 123, 100_001
+    q, x = render(s, n, n0)
+    w = oracle.make_waveform(FS, f, a, th)
+    x_ref = oracle.render(w, n0, n, nthreads=NTHREADS)
+    err = float(np.max(np.abs(x.astype(np.float64) - x_ref)))
+    assert err <= gemm_bound(a, engine == 1), err
+    q_ref = oracle.quantize(x_ref, w.full_scale())
+    assert np.max(np.abs(q.astype(np.int32) - q_ref)) <= 1
+
+
+def test_hybrid_window_with_chirps_and_ramps(awg, oracle):
+    rng = np.random.default_rng(5)
+    K = 300
+    f = rng.uniform(1e6, 139e6, K)
+    a = rng.uniform(0.2, 1.0, K)
+    th = rng.uniform(0, 2 * np.pi, K)
+    chirps = [dict(tone=int(t), f_start=float(f[t]), f_end=float(rng.uniform(1e6, 139e6)),
+                   duration=float(rng.integers(2000, 30000)) / FS, profile=int(t % 2),
+                   start_sample=int(rng.integers(0, 40000))) for t in rng.choice(K, 40, replace=False)]
+    ramps = [dict(tone=int(t), amp_end=float(rng.uniform(0, 1)), duration=float(rng.integers(500, 20000)) / FS,
+                  profile=int(t % 2), start_sample=int(rng.integers(0, 40000))) for t in rng.choice(K, 30, replace=False)]
+    s = awg.Synth(FS)
+    s.set_tones(f, a, th)
+    s.set_chirp_list(chirps)
+    s.set_ramp_list(ramps)
+    s.set_full_scale(2.0 * float(np.sum(a)))
+    s.set_static_engine(awg.STATIC_GEMM_FP16)
+    n = 80_000
+    q, x = render(s, n, 0)
+    w = oracle.add_ramps(oracle.make_waveform(FS, f, a, th, chirps), ramps)
+    x_ref = oracle.render(w, 0, n, nthreads=NTHREADS)
+    amax = np.abs(a).copy()
+    for r in ramps:
+        amax[r["tone"]] = max(amax[r["tone"]], abs(r["amp_end"]))
+    err = float(np.max(np.abs(x.astype(np.float64) - x_ref)))
+    assert err <= gemm_bound(amax, True) + direct_bound(amax, s.tone_split), err
+    q_ref = oracle.quantize(x_ref, s.full_scale)
+    assert np.max(np.abs(q.astype(np.int32) - q_ref)) <= 1
+
+
+def test_same_samples_however_the_stream_is_cut(awg):
+    rng = np.random.default_rng(9)
+    K = 1000
+    f = rng.uniform(1e6, 139e6, K)
+    a = rng.uniform(0.2, 1.0, K) / K
+    th = rng.uniform(0, 2 * np.pi, K)
+    chirps = [dict(tone=int(t), f_start=float(f[t]), f_end=float(rng.uniform(1e6, 139e6)),
+                   duration=float(rng.integers(2000, 30000)) / FS, profile=int(t % 2),
+                   start_sample=int(rng.integers(0, 150000))) for t in rng.choice(K, 50, replace=False)]
+
+    def make():
+        s = awg.Synth(FS)
+        s.set_tones(f, a, th)
+        s.set_chirp_list(chirps)
+        s.set_static_engine(awg.STATIC_GEMM_FP16)
+        return s
+
+    n = 300_000
+    ref = torch.empty(n, dtype=torch.int16, device="cuda")
+    make().render(n, ref)
+    s = make()
+    got = torch.empty(n, dtype=torch.int16, device="cuda")
+    c = 0
+    for piece in (1, 255, 257, 4096, 70_001, 1 << 16):
+        s.render(piece, got[c:])
+        c += piece
+    s.render_chunks(1 << 14, 5, got[c:])
+    c += 5 << 14
+    s.render(n - c, got[c:])
+    torch.cuda.synchronize()
+    assert np.array_equal(ref.cpu().numpy(), got.cpu().numpy())
+    # channel multiplexing with the engine
+    s2, s3 = make(), make()
+    mux = torch.empty(2 * n, dtype=torch.int16, device="cuda")
+    awg.render_multiplexed([s2, s3], n, mux)
+    torch.cuda.synchronize()
+    m = mux.cpu().numpy()
+    assert np.array_equal(m[0::2], ref.cpu().numpy()) and np.array_equal(m[1::2], ref.cpu().numpy())
+
+
+def test_ten_thousand_tone_comb(awg, oracle):
+    rng = np.random.default_rng(11)
+    K = 10_000
+    f = 80e6 + 1e4 * rng.permutation(10_000)[:K].astype(np.float64) + rng.uniform(-3e3, 3e3, K)
+    a = np.full(K, 1.0 / K)
+    th = rng.uniform(0, 2 * np.pi, K)
+    s = awg.Synth(FS)
+    s.set_tones(f, a, th)
+    s.set_static_engine(awg.STATIC_GEMM_FP16)
+    n = 1 << 20
+    q = torch.empty(n, dtype=torch.int16, device="cuda")
+    s.render(n, q)
+    torch.cuda.synchronize()
+    w = oracle.make_waveform(FS, f, a, th)
+    idx = np.unique(rng.integers(0, n, 300))
+    q_ref = oracle.quantize(oracle.render_at(w, idx, nthreads=NTHREADS), w.full_scale())
+    assert np.max(np.abs(q.cpu().numpy()[idx].astype(np.int32) - q_ref)) <= 1
+
+
+def test_engine_validation(awg):
+    s = awg.Synth(FS)
+    with pytest.raises(awg.AwgError):
+        s.set_static_engine(3)
+    assert s.static_engine == awg.STATIC_DIRECT
