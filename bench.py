@@ -177,15 +177,16 @@ def run_reference(args, wk):
     return 0
 
 
-def stream_leg(awg, fs: float, stream, seconds: float = 1.0, n_slots: int = 4, prefill: int = 2):
+def stream_leg(awg, fs: float, stream, seconds: float = 1.0, n_slots: int = 4, prefill: int = 2, engine: int = 0):
     """Continuous stream of 10,000 tones whose groups of 100 ramp in turn (1 ms linear ramps),
     2^20-sample chunks through the pinned ring with a real-time host sink: underruns and chunk
-    latency."""
+    latency (engine: the static-tone engine, direct or tensor-core GEMM)."""
     from paper_2403_15582_gb300 import workloads as wl
     from paper_2403_15582_gb300.stream import run_stream
     wk = wl.stream_rotating(seed=0, fs=fs, seconds=seconds)
     synth = awg.Synth(fs)
     synth.set_tones(wk.freq_hz, wk.amp, wk.phase_rad)
+    synth.set_static_engine(engine)
     ring = awg.Ring(synth, wk.chunk, n_slots)
     n_chunks = -(-wk.n_samples // wk.chunk)
     st = run_stream(synth, ring, wk.chirps, n_chunks, stream, prefill=prefill)
@@ -194,7 +195,7 @@ def stream_leg(awg, fs: float, stream, seconds: float = 1.0, n_slots: int = 4, p
     return {"tones": wk.K, "fs_hz": fs, "chunk": wk.chunk, "chunks": int(st["played"]), "underruns": int(st["underruns"]),
             "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"]},
             "min_lead_ms": st["lead_min_ms"], "playback_ms": st["chunk_playback_ms"], "slots": n_slots,
-            "required_tone_samples_per_s": wk.K * fs}
+            "required_tone_samples_per_s": wk.K * fs, "static_engine": ["direct", "gemm_fp16", "gemm_bf16"][engine]}
 
 
 def measured_peaks():
@@ -272,8 +273,10 @@ def static_leg(awg, stream, reps: int = 5):
             synth.set_ramp_list(ramps)
         q = torch.empty(n, dtype=torch.int16, device="cuda")
         res = {}
-        for mode, label in ((awg.SINE_SFU, "sfu"), (awg.SINE_ROTATOR, "rotator")):
+        for mode, engine, label in ((awg.SINE_SFU, awg.STATIC_DIRECT, "sfu"), (awg.SINE_ROTATOR, awg.STATIC_DIRECT, "rotator"),
+                                    (awg.SINE_SFU, awg.STATIC_GEMM_FP16, "gemm_fp16")):
             synth.set_sine_mode(mode)
+            synth.set_static_engine(engine)
             synth.seek(0)
             synth.render(n, q, stream)      # warm-up
             synth.profile_begin()
@@ -282,7 +285,18 @@ def static_leg(awg, stream, reps: int = 5):
                 synth.render(n, q, stream)
             torch.cuda.synchronize()
             _, rend, _ = synth.profile_end()
-            ms = float(np.min(rend))
+            ms = float(np.min(rend)) if len(rend) else float("nan")
+            if engine != awg.STATIC_DIRECT:   # the GEMM path has no profiling split: time the call
+                ts = []
+                for _ in range(reps):
+                    synth.seek(0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    synth.render(n, q, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = float(np.min(ts))
             res[label] = {"render_ms": ms, "tone_samples_per_s": len(fr) * n / (ms * 1e-3)}
         out[name] = res
         synth.close()
@@ -552,6 +566,7 @@ def main():
         line["served"] = {f"rho{r}": served_leg(awg, rho=r) for r in (0.5, 0.8, 1.0)}
     if not args.no_stream:
         line["stream"] = {f"{int(fs_/1e6)}MSps": stream_leg(awg, fs_, stream) for fs_ in (280e6, 50e6)}
+        line["stream"]["280MSps_gemm"] = stream_leg(awg, 280e6, stream, engine=awg.STATIC_GEMM_FP16)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = oracle_window_rate(wk, args.cpu_seconds)
     print(json.dumps(line), flush=True)

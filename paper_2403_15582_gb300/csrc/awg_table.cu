@@ -168,6 +168,10 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
   const int seg = lane & 1;
   uint64_t w = 0, step = 0;
   float amp = 0.f;
+  // static engine: the tiles [T0, T0 + TILE) where this (tone, segment) is static are those with
+  // seg_lo <= T0 <= seg_hi outside (ramp_lo, ramp_hi); amplitude A before the ramp, A_end after
+  int64_t seg_lo = 0, seg_hi = -1, ramp_lo = INT64_MAX, ramp_hi = INT64_MIN;
+  float amp_end = 0.f;
   if (k < a.K) {
     uint64_t phi, F;
     float A;
@@ -175,7 +179,20 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
       const ToneRec& t = a.tones[k];
       phi = seg ? t.phi_post_ref : t.phi_ref;
       F = seg ? t.F_end : t.F;
-      A = 1.f;   // per row below
+      A = t.A;
+      amp_end = t.A;
+      if (seg == 0) {
+        seg_lo = INT64_MIN;
+        seg_hi = t.slot >= 0 ? t.n_s - TILE : INT64_MAX;      // T0 + TILE - 1 < n_s
+      } else if (t.slot >= 0) {
+        seg_lo = t.n_e + 1;                                   // T0 > n_e
+        seg_hi = INT64_MAX;
+      }
+      if (t.flags & TONE_AMP_RAMP) {                          // not static: T0 + TILE - 1 > a_ns and T0 < a_ns + a_L
+        ramp_lo = t.a_ns - TILE + 2;
+        ramp_hi = t.a_ns + t.a_L - 1;
+        amp_end = t.A_end;
+      }
     } else {
       const ToneRec* t = a.tones + k;
       phi = __ldg(&t->phi_ref);
@@ -196,13 +213,10 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
     __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
     float a_row = amp;
     if (a.window_mode) {   // the row's tile decides whether this segment is summed here
-      a_row = 0.f;
-      if (k < a.K) {
-        uint64_t p2, f2;
-        float A2;
-        const int64_t T0 = ((a.row_base + (int64_t)row0 + (int64_t)r) << a.nb_log2) & ~(int64_t)(TILE - 1);
-        if (tile_segment_static(a.tones[k], T0, seg, &p2, &f2, &A2)) a_row = A2;
-      }
+      const int64_t T0 = ((a.row_base + (int64_t)row0 + (int64_t)r) << a.nb_log2) & ~(int64_t)(TILE - 1);
+      const bool in_seg = T0 >= seg_lo && T0 <= seg_hi;
+      const bool ramping = T0 >= ramp_lo && T0 <= ramp_hi;
+      a_row = (in_seg && !ramping) ? (T0 > ramp_hi ? amp_end : amp) : 0.f;
     }
     const float sv = a_row * sn, cv = a_row * cs;
     const uint32_t hv = pack2<T>(sv, cv);
