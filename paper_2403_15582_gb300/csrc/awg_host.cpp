@@ -370,6 +370,9 @@ struct awg {
   int32_t static_engine = AWG_STATIC_DIRECT;
   float* d_base = nullptr;             // tensor-core engine: FP32 sum of the window's static tones
   size_t cap_base = 0;
+  int32_t* d_list = nullptr;           // tensor-core engine: tones not static in some tile of the window
+  size_t cap_list = 0;
+  std::vector<int32_t> list;
   // periodic hand-off: from sample periodic_start on, x[n] = periodic table[n mod 2^periodic_log2]
   int16_t* d_periodic = nullptr;
   size_t cap_periodic = 0;
@@ -567,7 +570,8 @@ int build_exact_tables(awg_t* h) {
 }
 
 int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride,
-                  const float* base, int32_t skip_static);
+                  const float* base, int32_t skip_static, const int32_t* tone_list = nullptr, int32_t n_list = 0,
+                  int32_t list_split = 0, const int32_t* list_bounds = nullptr);
 int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride);
 
 int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride = 1) {
@@ -578,7 +582,8 @@ int render_impl(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream,
 }
 
 int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride,
-                  const float* base, int32_t skip_static) {
+                  const float* base, int32_t skip_static, const int32_t* tone_list, int32_t n_list,
+                  int32_t list_split, const int32_t* list_bounds) {
   if (!h) return fail(AWG_EINVAL, "null handle");
   if (n < 0) return fail(AWG_EINVAL, "sample count must be >= 0");
   if (n == 0) return AWG_OK;
@@ -670,6 +675,12 @@ int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
   ra.q_stride = q_stride;
   ra.base = base;
   ra.skip_static = skip_static;
+  ra.tone_list = tone_list;
+  ra.n_list = n_list;
+  if (tone_list) {
+    ra.split = list_split;
+    for (int r = 0; r <= list_split; ++r) ra.bounds[r] = list_bounds[r];
+  }
   ra.tile0 = tile0;
   ra.n_tiles = n_tiles;
   ra.win_start = c;
@@ -709,16 +720,40 @@ int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
   const int64_t PIECE = (int64_t)1 << 26;
   for (int64_t off = 0; off < n; off += PIECE) {
     const int64_t m = std::min(PIECE, n - off), c = h->cursor;
-    // every tone static (one segment, constant amplitude) in every tile the piece touches: the
-    // GEMM writes the output itself
+    // the tones that are not static (tile_segment_static) in some tile the piece touches: a chirp
+    // or an amplitude ramp meets the tile span.  The render visits only these, in ascending order,
+    // and still skips them in the tiles where they are static.  None: the GEMM writes the output.
     const int64_t t_first = c / awgk::TILE, t_last = (c + m - 1) / awgk::TILE;
-    bool all_static = q_stride == 1 && h->K > 0;
-    for (size_t k = 0; k < h->tones.size() && all_static; ++k) {
+    const int64_t s0 = t_first * awgk::TILE, s1 = (t_last + 1) * awgk::TILE - 1;
+    h->list.clear();
+    int32_t n_flagged = 0;
+    for (size_t k = 0; k < h->tones.size(); ++k) {
       const ToneRec& t = h->tones[k];
-      const int64_t s0 = t_first * awgk::TILE, s1 = (t_last + 1) * awgk::TILE - 1;
-      if (t.slot >= 0 && !(s1 < t.n_s || s0 > t.n_e)) all_static = false;
-      if ((t.flags & awgk::TONE_AMP_RAMP) && !(s1 <= t.a_ns || s0 >= t.a_ns + t.a_L)) all_static = false;
+      n_flagged += (t.slot >= 0 || (t.flags & awgk::TONE_AMP_RAMP)) ? 1 : 0;
+      if ((t.slot >= 0 && !(s1 < t.n_s || s0 > t.n_e)) ||
+          ((t.flags & awgk::TONE_AMP_RAMP) && !(s1 <= t.a_ns || s0 >= t.a_ns + t.a_L)))
+        h->list.push_back((int32_t)k);
     }
+    // The render's split and its CTAs' tone ranges come from the tones that hold a chirp or a ramp
+    // at all (they change only when chirps, ramps or tones are set, never while rendering): about
+    // the same number of them in each range.  With every tone holding one this is the plain split.
+    const int32_t list_split = awgk::tone_split_for(n_flagged);
+    int32_t bounds[awgk::MAX_SPLIT + 1];
+    bounds[0] = 0;
+    bounds[list_split] = h->K;
+    for (int32_t r = 1, p = 0, k = 0; r < list_split; ++r) {
+      // the first tone of range r: the flagged tone at position floor(n_flagged r / list_split)
+      const int32_t want = (int32_t)((int64_t)n_flagged * r / list_split);
+      for (; k < h->K; ++k) {
+        const ToneRec& t = h->tones[(size_t)k];
+        if (t.slot >= 0 || (t.flags & awgk::TONE_AMP_RAMP)) {
+          if (p == want) break;
+          ++p;
+        }
+      }
+      bounds[r] = k;
+    }
+    const bool all_static = q_stride == 1 && h->K > 0 && h->list.empty();
     int16_t* oq = out_q ? out_q + (size_t)off * (size_t)q_stride : nullptr;
     float* of = out_f ? out_f + off : nullptr;
     int st;
@@ -759,7 +794,19 @@ int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
       h->cursor = c + m;
       continue;
     }
-    if ((st = render_direct(h, m, of, oq, stream, q_stride, h->d_base, 1))) return st;
+    // (a list of all K tones is left out: one bulk copy per stage instead of one per tone)
+    const int32_t n_list = (int32_t)h->list.size();
+    const bool use_list = n_list < h->K;
+    if (use_list) {
+      if ((st = ensure(&h->d_list, &h->cap_list, std::max<size_t>(1, (size_t)n_list), h, "tone list"))) return st;
+      if (n_list > 0 &&
+          (e = cudaMemcpyAsync(h->d_list, h->list.data(), (size_t)n_list * sizeof(int32_t), cudaMemcpyHostToDevice,
+                               s)) != cudaSuccess)
+        return cuda_fail(e, "tone list upload");
+    }
+    if ((st = render_direct(h, m, of, oq, stream, q_stride, h->d_base, 1, use_list ? h->d_list : nullptr, n_list,
+                            list_split, bounds)))
+      return st;
   }
   return AWG_OK;
 }
@@ -1055,6 +1102,7 @@ void awg_destroy(awg_t* h) {
   cudaFree(h->d_recs);
   cudaFree(h->d_periodic);
   cudaFree(h->d_base);
+  cudaFree(h->d_list);
   cudaFree(h->d_seq_recs);
   cudaFree(h->d_seq_act);
   cudaFree(h->d_seq_exit);

@@ -150,6 +150,12 @@ struct RenderArgs {
   // (their sum comes from the table GEMM) and base[n - win_start] is added before quantising
   const float* base;
   int32_t skip_static;
+  // tones to visit (sorted, n_list of them; null: all K): CTA crank of a tile takes the listed
+  // tones of [bounds[crank], bounds[crank + 1]) in ascending order (bounds[0] = 0,
+  // bounds[split] = K); without a list it takes all of [K crank / split, K (crank + 1) / split)
+  const int32_t* tone_list;
+  int32_t n_list;
+  int32_t bounds[MAX_SPLIT + 1];
 };
 
 struct PhaseArgs {

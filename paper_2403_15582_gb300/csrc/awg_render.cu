@@ -506,7 +506,8 @@ enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_
 
 
 // One CTA's share of one tile: tones [K crank / split, K (crank+1) / split) of window tile `tile`
-// of the render described by `a`, then the cluster-wide sum and the store of this CTA's slice.
+// of the render described by `a` (or the listed tones of its bounds), then the cluster-wide sum
+// and the store of this CTA's slice.
 __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile, const int crank, const int split) {
   __shared__ alignas(16) ToneRec s_tone[2][STAGE];
   __shared__ alignas(16) TileRec s_rec[2][STAGE];
@@ -519,9 +520,24 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   const int64_t T0 = (a.tile0 + tile) * (int64_t)TILE;
   const int64_t n0 = T0 + (int64_t)tid * RUN;
   const uint32_t run_off = (uint32_t)(tid * RUN);
-  const int k_begin = (int)((int64_t)a.K * crank / split);
-  const int k_end = (int)((int64_t)a.K * (crank + 1) / split);
-  const int n_stages = (k_end - k_begin + STAGE - 1) / STAGE;
+  // positions [l_begin, l_end) of the visit: the CTA's range of tones, or of the tone list
+  int l_begin = (int)((int64_t)a.K * crank / split);
+  int l_end = (int)((int64_t)a.K * (crank + 1) / split);
+  if (a.tone_list) {
+    const int k_begin = a.bounds[crank], k_end = a.bounds[crank + 1];
+    auto lower = [&](int key) {
+      int lo = 0, hi = a.n_list;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a.tone_list[mid] < key) lo = mid + 1;
+        else hi = mid;
+      }
+      return lo;
+    };
+    l_begin = lower(k_begin);
+    l_end = lower(k_end);
+  }
+  const int n_stages = (l_end - l_begin + STAGE - 1) / STAGE;
 
   float acc[RUN];
 #pragma unroll
@@ -542,19 +558,27 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
 
   // thread 0 issues the tone copies and counts the issues per barrier (for a bounded drain)
   uint32_t issued = 0;   // 8-bit issue count per barrier
+  // warp 0: one bulk copy of the stage's contiguous tone records, or one per listed tone
   auto issue_tones = [&](int st) {
-    const int kb = k_begin + st * STAGE;
-    const uint32_t bytes = (uint32_t)min(STAGE, k_end - kb) * (uint32_t)sizeof(ToneRec);
+    const int lb = l_begin + st * STAGE;
+    const int cnt = min(STAGE, l_end - lb);
     fence_proxy_async();
-    mbar_arrive_expect_tx(&s_bar[st & 1], bytes);
-    bulk_g2s(&s_tone[st & 1][0], a.tones + kb, bytes, &s_bar[st & 1]);
-    issued += 1u << (8 * (st & 1));
+    if (tid == 0) {
+      mbar_arrive_expect_tx(&s_bar[st & 1], (uint32_t)cnt * (uint32_t)sizeof(ToneRec));
+      issued += 1u << (8 * (st & 1));
+    }
+    __syncwarp();
+    if (!a.tone_list) {
+      if (tid == 0) bulk_g2s(&s_tone[st & 1][0], a.tones + lb, (uint32_t)cnt * (uint32_t)sizeof(ToneRec), &s_bar[st & 1]);
+    } else if (tid < cnt) {
+      bulk_g2s(&s_tone[st & 1][tid], a.tones + a.tone_list[lb + tid], (uint32_t)sizeof(ToneRec), &s_bar[st & 1]);
+    }
   };
   // warp 0, once the stage's tones have landed: descriptors, and the records of tones that
   // chirp inside this tile
   auto prepare_stage = [&](int st) {
     const int b = st & 1;
-    const int cnt = min(STAGE, k_end - (k_begin + st * STAGE));
+    const int cnt = min(STAGE, l_end - (l_begin + st * STAGE));
     bool need = false;
     const TileRec* src = nullptr;
     if (tid < cnt) {
@@ -602,7 +626,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
 
   bool ok = true;
   if (n_stages > 0) {
-    if (tid == 0) {
+    if (tid < 32) {
       issue_tones(0);
       if (n_stages > 1) issue_tones(1);
     }
@@ -624,7 +648,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     ok &= mbar_wait(&s_bar[b], par);
     ok &= mbar_wait(&s_bar[2 + b], par);
     if (ok) {
-      const int cnt = min(STAGE, k_end - (k_begin + st * STAGE));
+      const int cnt = min(STAGE, l_end - (l_begin + st * STAGE));
       for (int i = 0; i < cnt; ++i) {
         const Desc& d = s_desc[b][i];
         const int kind = d.kind;
@@ -694,7 +718,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
       fail_stage = st;
       break;
     }
-    if (tid == 0 && st + 2 < n_stages) issue_tones(st + 2);
+    if (tid < 32 && st + 2 < n_stages) issue_tones(st + 2);
   }
   if (fail_stage >= 0) {
     // report, then let every copy still in flight land (bounded) before shared memory goes away

@@ -141,6 +141,51 @@ def test_same_samples_however_the_stream_is_cut(awg):
     assert np.array_equal(m[0::2], ref.cpu().numpy()) and np.array_equal(m[1::2], ref.cpu().numpy())
 
 
+def test_flagged_tones_over_several_ctas(awg, oracle):
+    """400 tones hold a chirp or a ramp (the render's list split over 5 CTAs per tile, ranges from
+    the flagged tones), starting at different times so that windows list different tones: the
+    oracle at sampled indices, and the same samples however the stream is cut."""
+    rng = np.random.default_rng(13)
+    K, n = 4000, 400_000
+    f = rng.uniform(1e6, 139e6, K)
+    a = rng.uniform(0.2, 1.0, K) / 100
+    th = rng.uniform(0, 2 * np.pi, K)
+    picked = rng.choice(K, 400, replace=False)
+    chirps = [dict(tone=int(t), f_start=float(f[t]), f_end=float(rng.uniform(1e6, 139e6)),
+                   duration=float(rng.integers(2000, 60000)) / FS, profile=int(t % 2),
+                   start_sample=int(rng.integers(0, n - 60000))) for t in picked[:300]]
+    ramps = [dict(tone=int(t), amp_end=float(rng.uniform(0, 0.01)), duration=float(rng.integers(500, 40000)) / FS,
+                  profile=int(t % 2), start_sample=int(rng.integers(0, n - 40000))) for t in picked[300:]]
+
+    def make():
+        s = awg.Synth(FS)
+        s.set_tones(f, a, th)
+        s.set_chirp_list(chirps)
+        s.set_ramp_list(ramps)
+        s.set_full_scale(0.5 * float(np.sum(a)))
+        s.set_static_engine(awg.STATIC_GEMM_FP16)
+        return s
+
+    ref = torch.empty(n, dtype=torch.int16, device="cuda")
+    make().render(n, ref)
+    s = make()
+    got = torch.empty(n, dtype=torch.int16, device="cuda")
+    c = 0
+    for piece in (4095, 4097, 50_000, 12_345, 100_000):
+        s.render(piece, got[c:])
+        c += piece
+    s.render_chunks(1 << 13, 7, got[c:])
+    c += 7 << 13
+    s.render(n - c, got[c:])
+    torch.cuda.synchronize()
+    r = ref.cpu().numpy()
+    assert np.array_equal(r, got.cpu().numpy())
+    w = oracle.add_ramps(oracle.make_waveform(FS, f, a, th, chirps), ramps)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 400), [0, n - 1]]))
+    q_ref = oracle.quantize(oracle.render_at(w, idx, nthreads=NTHREADS), 0.5 * float(np.sum(a)))
+    assert np.max(np.abs(r[idx].astype(np.int32) - q_ref)) <= 1
+
+
 def test_ten_thousand_tone_comb(awg, oracle):
     rng = np.random.default_rng(11)
     K = 10_000
