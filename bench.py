@@ -515,7 +515,7 @@ def main():
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_total = max_over_ranks(sum(e2e_ms), dist, "cuda")
     e2e_value = world * work_per_step * args.steps / (e2e_total * 1e-3)
-    h2d = K * (2 * 80 + 208)     # tone records twice (set_tones, set_chirps) + chirp records
+    h2d = K * (2 * 96 + 208)     # 96-B tone records twice (set_tones, set_chirps) + 208-B chirp records
 
     if rank != 0:
         if dist is not None:
