@@ -36,6 +36,7 @@ MASK64 = (1 << 64) - 1
 MASK192 = (1 << 192) - 1
 PROFILE_LINEAR = 0
 PROFILE_MINJERK = 1
+PROFILE_EXPONENTIAL = 2
 MAX_CHIRP_SAMPLES = (1 << 28) - 1
 
 
@@ -75,7 +76,7 @@ def lib():
         L.oracle_phase_words_seq.argtypes = [u64, u64, i32, i64, i64, P, u64, i64, i64, P]
         L.oracle_phase_words_at.argtypes = [u64, u64, i32, i64, i64, P, u64, P, i64, P]
         L.oracle_cascade_at.argtypes = [P, i64, P]
-        L.oracle_chirp_end_word.argtypes = [u64, u64, i64, i64, P]
+        L.oracle_chirp_end_word.argtypes = [u64, u64, i32, i64, i64, P]
         L.oracle_chirp_end_word.restype = u64
         L.oracle_quantize.argtypes = [P, i64, dbl, P]
         _lib = L
@@ -163,6 +164,19 @@ def chirp_coefficients(F_start: int, F_end: int, L: int, profile: int) -> list[i
         ck = sum(((-1) ** (k - j)) * math.comb(k, j) * vals[j] for j in range(k + 1))
         d.append(round(ck * (1 << 128)) & MASK192)
     return d
+
+
+def chirp_state(F_start: int, F_end: int, L: int, profile: int):
+    """(has_chirp, d) of a chirp for the C oracle.  Polynomial profiles: (1, d_0..d_6).
+    Exponential (named in Sec. II, formula not printed; see exp_offset in awg_oracle.c): (2, d)
+    with d_0 = F_start and d_1 = F_end, which must both be > 0 (the frequency ratio)."""
+    if profile == PROFILE_EXPONENTIAL:
+        if not (1 <= L <= MAX_CHIRP_SAMPLES):
+            raise ValueError("chirp length out of range")
+        if F_start <= 0 or F_end <= 0:
+            raise ValueError("an exponential chirp needs f_start, f_end > 0")
+        return 2, [int(F_start), int(F_end), 0, 0, 0, 0, 0]
+    return 1, chirp_coefficients(F_start, F_end, L, profile)
 
 
 def cascade_state(d: Sequence[int], m: int) -> list[int]:
@@ -259,10 +273,9 @@ def make_waveform(fs: float, freq_hz, amp, phase_rad, chirps=None, grid_log2: Op
         Fs_ = freq_word(c["f_start"], fs)
         Fe_ = freq_word(c["f_end"], fs)
         L = chirp_length(c["duration"], fs)
-        w.has_chirp[k] = 1
+        w.has_chirp[k], w.d[k] = chirp_state(Fs_, Fe_, L, int(c["profile"]))
         w.n_s[k] = int(c.get("start_sample", 0))
         w.L[k] = L
-        w.d[k] = chirp_coefficients(Fs_, Fe_, L, int(c["profile"]))
         w.F_end[k] = Fe_
     return w
 
@@ -371,7 +384,7 @@ def cascade_state_c(d: Sequence[int], m: int) -> list[int]:
 def chirp_end_word(w: Waveform, k: int) -> int:
     """Phi at the last chirp sample m = L (the post-chirp anchor of Eq. freqchirp case 2)."""
     F, phi, hc, ns, L, d, Fe = _tone_args(w, k)
-    return int(lib().oracle_chirp_end_word(F, phi, ns, L, _p(d)))
+    return int(lib().oracle_chirp_end_word(F, phi, hc, ns, L, _p(d)))
 
 
 def make_waveform_window(fs: float, freq_hz, amp, phase_rad, chirps, n0: int, N: int) -> Waveform:
@@ -399,8 +412,8 @@ def make_waveform_window(fs: float, freq_hz, amp, phase_rad, chirps, n0: int, N:
                 w.F[k] = w.F_end[k]
                 w.phi_ref[k] = (end - n_e * w.F_end[k]) % (1 << 64)
                 w.has_chirp[k] = 0
-            w.has_chirp[k], w.n_s[k], w.L[k] = 1, ns, L
-            w.d[k] = chirp_coefficients(Fs_, Fe_, L, int(c["profile"]))
+            w.has_chirp[k], w.d[k] = chirp_state(Fs_, Fe_, L, int(c["profile"]))
+            w.n_s[k], w.L[k] = ns, L
             w.F_end[k] = Fe_
             if ns + L >= n0:
                 break

@@ -18,8 +18,10 @@
  *                 chirp phase polynomial (Eq. freqchirp, case 1, and its linear analogue), scaled
  *                 by 2^128 and rounded; they are derived with exact rationals in oracle/__init__.py.
  *                 d_0 carries the rounding offset 2^127, so top64() rounds to nearest.
+ *   exponential:  (has_chirp == 2) Phi(n_s + m) = Phi_start + R(m), R the integral of a frequency
+ *                 that moves geometrically from F_start to F_end (see exp_offset).
  *   after chirp:  Phi(n) = Phi_end + (n - n_s - L) * F_end   (Eq. freqchirp, case 2),
- *                 Phi_end = Phi(n_s + L) from the cascade.
+ *                 Phi_end = Phi(n_s + L) from the cascade (or from R(L)).
  *   amplitude:    A_k, or a ramp a_k(n) from A_k to A_end (see amp_at) for a_j[i] of
  *                 Eq. dynamicandstatic.
  * Sine is libm sin() in FP64 of the signed turn u = (int64)Phi * 2^-64, the sum runs over
@@ -111,12 +113,48 @@ static void cascade_step(u192 acc[7]) {
   for (int k = 0; k < 6; k++) acc[k] = add192(acc[k], acc[k + 1]);
 }
 
+/*
+ * Exponential chirp (Sec. II names exponential chirps beside the minimum-jerk one but prints no
+ * formula).  Reading: the instantaneous frequency moves geometrically, F(t) = F_start r^(t/L)
+ * words per sample with r = F_end / F_start (both > 0), and the phase offset is its integral
+ *     R(m) = F_start L (r^(m/L) - 1) / ln r          (F_start m when r = 1),
+ * rounded to the nearest word, mod 2^64.  Evaluated in long double (expm1l, logl): unlike the
+ * polynomial chirps this is not an exact-integer definition; its error is a few 1e-10 turn at the
+ * largest phases, far below any rendering tolerance.
+ */
+static uint64_t ld_to_word(long double R) {
+  const long double two64 = 18446744073709551616.0L;
+  long double r = fmodl(R, two64); /* exact; the sign of R */
+  if (r < 0) r += two64;
+  r = floorl(r + 0.5L);
+  if (r >= two64) r -= two64;
+  return (uint64_t)r;
+}
+
+/* Planted-mistake switch for the pin tests only (0: the definition above).  1: F_start and F_end
+ * swapped; 2: m off by one; 3: exp instead of expm1 (a constant offset); 4: log2 instead of ln;
+ * 5: L + 1 instead of L. */
+int oracle_exp_plant = 0;
+
+static uint64_t exp_offset(uint64_t F0, uint64_t F1, int64_t L, int64_t m) {
+  if (F0 == F1) return (uint64_t)m * F0;
+  if (oracle_exp_plant == 1) { uint64_t t = F0; F0 = F1; F1 = t; }
+  if (oracle_exp_plant == 2) m += 1;
+  if (oracle_exp_plant == 5) L += 1;
+  long double lam = oracle_exp_plant == 4 ? log2l((long double)F1 / (long double)F0)
+                                          : logl((long double)F1 / (long double)F0);
+  long double e = oracle_exp_plant == 3 ? expl(lam * (long double)m / (long double)L)
+                                        : expm1l(lam * (long double)m / (long double)L);
+  long double R = (long double)F0 * (long double)L * e / lam;
+  return ld_to_word(R);
+}
+
 typedef struct {
   uint64_t F, phi_ref;          /* static segment: Phi(n) = phi_ref + n F */
   double A;
-  int32_t has_chirp;
+  int32_t has_chirp;            /* 0 none, 1 polynomial (cascade), 2 exponential */
   int64_t n_s, L;               /* chirp covers samples n_s .. n_s+L (m = 0..L) */
-  const uint64_t* d;            /* 7 x 3 limbs */
+  const uint64_t* d;            /* 7 x 3 limbs (exponential: d_0 = F_start, d_1 = F_end) */
   uint64_t phi_start, phi_end, F_end;
   int32_t has_ramp, ramp_prof;  /* amplitude ramp a_j[i] of Eq. dynamicandstatic (0: none) */
   int64_t a_ns, a_L;            /* the amplitude moves from A to A_end over samples a_ns .. a_ns+a_L */
@@ -144,6 +182,7 @@ static uint64_t phase_closed(const tone_t* t, int64_t n) {
   if (!t->has_chirp || n < t->n_s) return t->phi_ref + (uint64_t)n * t->F;
   int64_t m = n - t->n_s;
   if (m > t->L) return t->phi_end + (uint64_t)(m - t->L) * t->F_end;
+  if (t->has_chirp == 2) return t->phi_start + exp_offset(t->d[0], t->d[3], t->L, m);
   u192 acc[7];
   cascade_at(t->d, m, acc);
   return t->phi_start + acc[0].w[2];
@@ -169,11 +208,12 @@ static void gen_init(gen_t* g, const tone_t* t, int64_t n) {
     g->phi = t->phi_end + (uint64_t)(n - t->n_s - t->L) * t->F_end;
   } else {
     g->seg = 1;
-    cascade_at(t->d, n - t->n_s, g->acc);
+    if (t->has_chirp == 1) cascade_at(t->d, n - t->n_s, g->acc);
   }
 }
 
 static uint64_t gen_phase(const gen_t* g) {
+  if (g->seg == 1 && g->t->has_chirp == 2) return phase_closed(g->t, g->n);   /* no recurrence */
   return g->seg == 1 ? g->t->phi_start + g->acc[0].w[2] : g->phi;
 }
 
@@ -183,7 +223,7 @@ static void gen_advance(gen_t* g) {
   if (g->seg == 0) {
     if (t->has_chirp && next == t->n_s) {
       g->seg = 1;
-      cascade_at(t->d, 0, g->acc);
+      if (t->has_chirp == 1) cascade_at(t->d, 0, g->acc);
     } else {
       g->phi += t->F;
     }
@@ -191,7 +231,7 @@ static void gen_advance(gen_t* g) {
     if (next - t->n_s > t->L) {
       g->seg = 2;
       g->phi = t->phi_end + t->F_end; /* one sample past the chirp end */
-    } else {
+    } else if (t->has_chirp == 1) {
       cascade_step(g->acc);
     }
   } else {
@@ -224,7 +264,9 @@ static void build_tones(int K, const uint64_t* F, const uint64_t* phi_ref, const
     t->d = d + 21 * (size_t)k;
     t->F_end = F_end[k];
     t->phi_start = t->phi_ref + (uint64_t)t->n_s * t->F;
-    if (t->has_chirp) {
+    if (t->has_chirp == 2) {
+      t->phi_end = t->phi_start + exp_offset(t->d[0], t->d[3], t->L, t->L);
+    } else if (t->has_chirp) {
       u192 acc[7];
       cascade_at(t->d, t->L, acc);
       t->phi_end = t->phi_start + acc[0].w[2];
@@ -262,8 +304,9 @@ void oracle_amp_at(double A, int32_t profile, int64_t a_ns, int64_t a_L, double 
 }
 
 /* Post-chirp anchor Phi_end = Phi(n_s + L), for tests and for the host bookkeeping of tests. */
-uint64_t oracle_chirp_end_word(uint64_t F, uint64_t phi_ref, int64_t n_s, int64_t L,
+uint64_t oracle_chirp_end_word(uint64_t F, uint64_t phi_ref, int32_t has_chirp, int64_t n_s, int64_t L,
                                const uint64_t* d) {
+  if (has_chirp == 2) return phi_ref + (uint64_t)n_s * F + exp_offset(d[0], d[3], L, L);
   u192 acc[7];
   cascade_at(d, L, acc);
   return phi_ref + (uint64_t)n_s * F + acc[0].w[2];

@@ -451,3 +451,94 @@ def test_amp_ramp_seen_through_the_render(oracle):
     x = oracle.render(w, 0, 6000)
     n = np.arange(0, 6000, 4)
     assert np.array_equal(x[n], oracle.amp_at(0.3, 1, 800, 4000, 0.9, n))
+
+
+# ---------------------------------------------------------------------------------------------
+# exponential chirps (named in Sec. II, formula not printed): the frequency moves geometrically
+# from F_start to F_end, the phase is its integral
+# ---------------------------------------------------------------------------------------------
+EXP = 2
+
+
+def _exp_wave(oracle, fs, f0, f1, L, n_s=0, phase=0.0):
+    return oracle.make_waveform(fs, [f0], [1.0], [phase], chirps=[dict(tone=0, f_start=f0, f_end=f1, duration=L / fs,
+                                                                        profile=EXP, start_sample=n_s)])
+
+
+def _exp_checks(oracle, fs=280e6, cases=((90e6, 150e6, 100_000), (179e6, 81e6, 60_000), (1e6, 60e6, 200_000))):
+    """Worst violation of each exponential-chirp pin, relative to its tolerance (<= 1 passes)."""
+    worst = {"law": 0.0, "reversal": 0.0, "taylor": 0.0, "ends": 0.0}
+    for f0, f1, L in cases:
+        F0, F1 = oracle.freq_word(f0, fs), oracle.freq_word(f1, fs)
+        r = F1 / F0
+        alpha = math.log(r) / L
+        w = _exp_wave(oracle, fs, f0, f1, L)
+        ph0 = int(w.phi_ref[0])
+        ms = np.array(sorted({0, 1, L // 3, L // 2, L - 2, L - 1} | set(range(0, L, L // 7))), dtype=np.int64)
+        a = oracle.phase_words_at(w, 0, ms)
+        b = oracle.phase_words_at(w, 0, ms + 1)
+        # (1) per-sample increments follow the geometric law: the integral of F0 r^(t/L) over one
+        # sample is F(m + 1/2) sinh(alpha/2) / (alpha/2) = F(m + 1/2) (1 + alpha^2/24 + ...)
+        for m, x, y in zip(ms, a, b):
+            delta = (int(y) - int(x)) % TWO64
+            Fm = F0 * r ** ((m + 0.5) / L)
+            worst["law"] = max(worst["law"], abs(delta / Fm - 1 - alpha * alpha / 24) / (alpha**4 + 2e-13))
+        # (2) time reversal: R_{0->1}(m) + R_{1->0}(L - m) = R_{0->1}(L) (the same frequency curve
+        # read backwards covers the rest of the phase)
+        wr = _exp_wave(oracle, fs, f1, f0, L)
+        phr = int(wr.phi_ref[0])
+        total = (int(oracle.phase_words_at(w, 0, [L])[0]) - ph0) % TWO64
+        rev = oracle.phase_words_at(wr, 0, L - ms)
+        for x, y in zip(a, rev):
+            s = ((int(x) - ph0) + (int(y) - phr)) % TWO64
+            worst["reversal"] = max(worst["reversal"], abs(_sdiff(s, total)) / 2**20)
+        # (4) the end: Phi(L) is the post-chirp anchor, then steps of exactly F_end
+        tail = oracle.phase_words_seq(w, 0, L - 1, 4)
+        inc = [(int(tail[i + 1]) - int(tail[i])) % TWO64 for i in range(3)]
+        ok = inc[1] == F1 and inc[2] == F1 and abs(inc[0] / (F1 * r ** (-0.5 / L)) - 1 - alpha * alpha / 24) < alpha**4 + 2e-13
+        ok = ok and int(tail[1]) == oracle.chirp_end_word(w, 0)
+        worst["ends"] = max(worst["ends"], 0.0 if ok else 2.0)
+    # (3) near r = 1 the exponential chirp is the (exactly pinned) linear chirp plus the Taylor
+    # terms of the exponential in x = D / F_start: R_exp - R_lin = F_s L [x^2 (u^3/6 - u^2/4) +
+    # x^3 (u^2/6 - u^3/6 + u^4/24)] + O(x^4), u = m / L
+    fs, L = 280e6, 100_000
+    for f0, f1 in ((100e6, 100.003e6), (120e6, 119.9955e6)):
+        F0, F1 = oracle.freq_word(f0, fs), oracle.freq_word(f1, fs)
+        x = Fraction(F1 - F0, F0)
+        we = _exp_wave(oracle, fs, f0, f1, L)
+        wl = oracle.make_waveform(fs, [f0], [1.0], [0.0], chirps=[dict(tone=0, f_start=f0, f_end=f1, duration=L / fs,
+                                                                        profile=0, start_sample=0)])
+        ms = np.arange(0, L + 1, L // 10, dtype=np.int64)
+        pe, pl = oracle.phase_words_at(we, 0, ms), oracle.phase_words_at(wl, 0, ms)
+        for m, e, l in zip(ms, pe, pl):
+            u = Fraction(int(m), L)
+            corr = F0 * L * (x**2 * (u**3 / 6 - u**2 / 4) + x**3 * (u**2 / 6 - u**3 / 6 + u**4 / 24))
+            worst["taylor"] = max(worst["taylor"], abs(_sdiff(e, (int(l) + round(corr)) % TWO64)) / 2**22)
+    return worst
+
+
+def test_exp_chirp_pins(oracle):
+    worst = _exp_checks(oracle)
+    assert all(v <= 1 for v in worst.values()), worst
+    # r = 1: the static tone's words exactly
+    fs = 280e6
+    w = _exp_wave(oracle, fs, 77e6, 77e6, 5000, n_s=300, phase=1.1)
+    s = oracle.make_waveform(fs, [77e6], [1.0], [1.1])
+    assert np.array_equal(oracle.phase_words_seq(w, 0, 0, 6000), oracle.phase_words_seq(s, 0, 0, 6000))
+    # sequential and closed-form paths agree, and a zero frequency is refused
+    w = _exp_wave(oracle, fs, 30e6, 90e6, 7000, n_s=123, phase=0.7)
+    assert np.array_equal(oracle.phase_words_seq(w, 0, 0, 7500), oracle.phase_words_at(w, 0, np.arange(7500)))
+    with pytest.raises(ValueError):
+        _exp_wave(oracle, fs, 0.0, 90e6, 7000)
+
+
+@pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5])
+def test_exp_pins_catch_planted_mistakes(oracle, mutant):
+    import ctypes
+    knob = ctypes.c_int.in_dll(oracle.lib(), "oracle_exp_plant")
+    knob.value = mutant
+    try:
+        worst = _exp_checks(oracle)
+    finally:
+        knob.value = 0
+    assert max(worst.values()) > 1, worst
