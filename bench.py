@@ -323,6 +323,42 @@ def static_leg(awg, stream, reps: int = 5):
     return out
 
 
+def chirp_profile_leg(awg, stream, wk, reps: int = 3):
+    """The C2 record (1000 tones chirping 80-180 MHz over 35 ms) with every chirp on one profile:
+    linear, minimum-jerk, exponential; pipelined chunk renders, best of reps, L2 flushed before
+    each."""
+    import numpy as np
+    import torch
+    N, chunk = wk.n_samples, wk.chunk
+    n_full, tail = N // chunk, N % chunk
+    tone, f0, f1, dur, _, start = wk.chirp_arrays()
+    out = torch.empty(N, dtype=torch.int16, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    for prof, label in ((awg.PROFILE_LINEAR, "linear"), (awg.PROFILE_MINJERK, "minjerk"),
+                        (awg.PROFILE_EXPONENTIAL, "exponential")):
+        synth = awg.Synth(wk.fs)
+        synth.set_tones(wk.freq_hz, wk.amp, wk.phase_rad)
+        synth.set_chirps(tone, f0, f1, dur, np.full(len(tone), prof, dtype=np.int32), start)
+        ts = []
+        for r in range(reps + 1):
+            synth.seek(0)
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            synth.render_chunks(chunk, n_full, out, stream)
+            if tail:
+                synth.render(tail, out[n_full * chunk:], stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                ts.append(e0.elapsed_time(e1))
+        ms = float(np.min(ts))
+        res[label] = {"ms": ms, "tone_samples_per_s": wk.K * N / (ms * 1e-3), "device_status": synth.device_status()}
+        synth.close()
+    return res
+
+
 def periodic_leg(awg, stream, reps: int = 5):
     """Periodic hand-off: the 10,000-tone 2^24-sample table (split-precision GEMM, FP16) set up
     once, then replayed for 2^28 samples; replay rate against the measured HBM copy bandwidth
@@ -411,6 +447,7 @@ def main():
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-static", action="store_true")
     ap.add_argument("--no-periodic", action="store_true")
+    ap.add_argument("--no-profiles", action="store_true")
     ap.add_argument("--table-case", default="10000,24",
                     help="tones,log2 samples of the table leg (a smaller case for profiling)")
     args = ap.parse_args()
@@ -555,6 +592,8 @@ def main():
         "kernel_ms_per_step": {"prep": float(np.sum(prep_ms)) / args.steps,
                                "render": float(np.sum(render_ms)) / args.steps},
     }
+    if not args.no_profiles:
+        line["chirp_profiles"] = chirp_profile_leg(awg, stream, wk)
     if not args.no_static:
         line["static"] = static_leg(awg, stream)
     if not args.no_periodic:

@@ -48,7 +48,7 @@ enum {
   AWG_ESTATE = -6     /* call not valid in the handle's current state */
 };
 
-enum { AWG_PROFILE_LINEAR = 0, AWG_PROFILE_MINJERK = 1 };
+enum { AWG_PROFILE_LINEAR = 0, AWG_PROFILE_MINJERK = 1, AWG_PROFILE_EXPONENTIAL = 2 };
 
 /* Version of this ABI (major*10000 + minor*100 + patch). */
 int awg_version(void);
@@ -84,7 +84,12 @@ int awg_chirp_length(double duration_s, double fs_hz, int64_t* out_L);
  * in words relative to its start (min-jerk: P(m) = F_start m + D (5 m^4 L^2 - 6 m^5 L + 2 m^6) /
  * (2 L^5), Eq. freqchirp; linear: P(m) = F_start m + D m^2 / (2L), D = F_end - F_start as a
  * signed integer), d_k = rint_half_even(Delta^k P(0) * 2^128) mod 2^192 for k >= 1 and
- * d_0 = 2^127.  out: 21 uint64, little-endian limbs, d_0 first. */
+ * d_0 = 2^127.  out: 21 uint64, little-endian limbs, d_0 first.
+ * AWG_PROFILE_EXPONENTIAL (Sec. II names exponential chirps; the phase is the integral of
+ * F(t) = F_start r^(t/L), r = F_end / F_start, i.e. R(m) = C (e^(alpha m) - 1) words with
+ * alpha = ln(r) / L and C = F_start / alpha): out[0] = F_start, out[1] = F_end and the IEEE
+ * doubles alpha, C, e^alpha - 1 as bit patterns in out[2..4]; the rest 0.  EINVAL if F_start or
+ * F_end is 0.  With F_start == F_end the chirp is the linear one (the same phase). */
 int awg_chirp_coeffs(uint64_t F_start, uint64_t F_end, int64_t L, int32_t profile, uint64_t* out21);
 
 /* ------------------------------------------------------------------------------------------
@@ -109,7 +114,10 @@ int awg_set_tones_grid(awg_t* h, const double* freq_hz, int32_t log2_len, const 
 
 /* Schedule n chirps.  Chirp i moves tone[i] from f_start[i] to f_end[i] (Hz, each in [0, fs))
  * over duration[i] seconds (L = rint(duration fs) samples, 1 <= L < 2^28) with the given
- * profile, starting at absolute sample start_sample[i] from the tone's phase at that sample
+ * profile (AWG_PROFILE_LINEAR, AWG_PROFILE_MINJERK, or AWG_PROFILE_EXPONENTIAL: the frequency
+ * moves geometrically, both ends > 0 Hz; its phase is evaluated in FP64, within a few 1e-9 turn
+ * of the exact integral, where the polynomial profiles are exact integers), starting at absolute
+ * sample start_sample[i] from the tone's phase at that sample
  * (a start frequency that differs from the tone's current frequency is a frequency step).
  * A tone holds one chirp at a time: a new chirp on a tone is accepted once the render cursor
  * has passed that tone's previous chirp (previous n_s + L < cursor); the previous chirp's end

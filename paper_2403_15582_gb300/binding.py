@@ -14,7 +14,7 @@ PREC_BF16, PREC_FP16 = 0, 1
 SINE_SFU, SINE_ROTATOR = 0, 1
 PERIODIC_DIRECT, PERIODIC_GEMM_BF16, PERIODIC_GEMM_FP16 = 0, 1, 2
 STATIC_DIRECT, STATIC_GEMM_FP16, STATIC_GEMM_BF16 = 0, 1, 2
-PROFILE_LINEAR, PROFILE_MINJERK = 0, 1
+PROFILE_LINEAR, PROFILE_MINJERK, PROFILE_EXPONENTIAL = 0, 1, 2
 
 # (name, restype, argtypes) of every symbol declared in include/awg.h
 P, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double

@@ -263,8 +263,52 @@ int chirp_length_impl(double dur, double fs, int64_t* L) {
 //   min-jerk  P(m) = F_start m + D (5 L^2 m^4 - 6 L m^5 + 2 m^6) / (2 L^5)
 //   linear    P(m) = F_start m + D m^2 / (2 L)
 // Delta^k P(0) = F_start [k = 1] + D N_k / (2 L^pw) with N_k built from Delta^k[m^p](0).
+uint64_t bits_of(double x) {
+  uint64_t b;
+  std::memcpy(&b, &x, sizeof(b));
+  return b;
+}
+
+// x rounded to the nearest word, mod 2^64: the double's exact value M 2^sh (M its 53-bit integer
+// mantissa) reduced by shifting.
+uint64_t word_of_double(double x) {
+  int e;
+  const double fr = std::frexp(std::fabs(x), &e);   // |x| = fr 2^e, fr in [1/2, 1)
+  if (fr == 0 || !std::isfinite(x)) return 0;
+  const uint64_t M = (uint64_t)std::ldexp(fr, 53);
+  const int sh = e - 53;
+  uint64_t v = 0;
+  if (sh >= 64) v = 0;
+  else if (sh >= 0) v = M << sh;
+  else if (sh > -54) v = (M + (1ull << (-sh - 1))) >> (-sh);
+  return x < 0 ? (uint64_t)0 - v : v;
+}
+
+// Exponential chirp from F0 to F1 (both > 0, F0 != F1) over L samples: the frequency
+// F0 e^(alpha t) with alpha = ln(F1/F0) / L, phase offset R(m) = C (e^(alpha m) - 1), C = F0 / alpha.
+struct ExpParams {
+  double alpha, C, q;   // q = e^alpha - 1
+};
+ExpParams exp_params(uint64_t F0, uint64_t F1, int64_t L) {
+  const double diff = F1 >= F0 ? (double)(F1 - F0) : -(double)(F0 - F1);   // exact difference, rounded once
+  ExpParams p;
+  p.alpha = std::log1p(diff / (double)F0) / (double)L;
+  p.C = (double)F0 / p.alpha;
+  p.q = std::expm1(p.alpha);
+  return p;
+}
+
 int chirp_coeffs_impl(uint64_t F0, uint64_t F1, int64_t L, int profile, W192 d[7]) {
   if (L < 1 || L > (1 << 28) - 1) return fail(AWG_EINVAL, "chirp length must be 1 .. 2^28-1 samples");
+  if (profile == AWG_PROFILE_EXPONENTIAL) {
+    if (F0 == 0 || F1 == 0) return fail(AWG_EINVAL, "an exponential chirp needs f_start, f_end > 0");
+    if (F0 == F1) return chirp_coeffs_impl(F0, F1, L, AWG_PROFILE_LINEAR, d);   // the same phase
+    const ExpParams e = exp_params(F0, F1, L);
+    for (int k = 0; k < 7; ++k) d[k] = W192{{0, 0, 0}};
+    d[0] = W192{{F0, F1, bits_of(e.alpha)}};
+    d[1] = W192{{bits_of(e.C), bits_of(e.q), 0}};
+    return AWG_OK;
+  }
   if (profile != AWG_PROFILE_LINEAR && profile != AWG_PROFILE_MINJERK) return fail(AWG_EINVAL, "unknown chirp profile");
   const s128 D = (s128)F1 - (s128)F0;
   d[0] = W192{{0, 1ull << 63, 0}};   // 2^127: rounding offset of the top 64 bits
@@ -301,8 +345,26 @@ uint64_t chirp_offset_word(const W192 d[7], int64_t m) {
 
 // Chirps whose neglected 4th..6th-order phase terms over one 32-sample run could exceed 512 units
 // of 2^-32 turn (1.2e-7 turn) are rendered from a per-sample table of exact phases instead.
+// Phase offset at the end of an exponential chirp, R(L), the same FP64 formula as the render's.
+uint64_t exp_end_offset(uint64_t F0, uint64_t F1, int64_t L) {
+  const ExpParams e = exp_params(F0, F1, L);
+  return word_of_double(e.C * std::expm1(e.alpha * (double)L));
+}
+
+// Whether a chirp takes the per-sample table: the render's 32-bit run cascade drops the phase
+// differences of order 4..6 inside a run of 32 samples; above 2^-23 turn the table is used.
+// Exponential chirps: the tile polynomial also drops orders >= 7 over a tile of 4096 samples,
+// C(4095, 7) |Delta^7 R| <= 3.8e21 F_max |q|^6 (twice that for the tail of the series), with a
+// budget of 2^-26 turn.
 bool needs_exact(uint64_t F0, uint64_t F1, int64_t L, int profile) {
-  if (profile == AWG_PROFILE_LINEAR) return false;
+  if (profile == AWG_PROFILE_EXPONENTIAL && F0 != F1) {
+    const double q = std::fabs(exp_params(F0, F1, L).q);
+    const double Fm = (double)std::max(F0, F1) * (1.0 + q);
+    const double tile = 2.0 * 3.8e21 * Fm * q * q * q * q * q * q;
+    const double run = 31465.0 * Fm * q * q * q + 169911.0 * Fm * q * q * q * q + 736281.0 * Fm * q * q * q * q * q;
+    return tile > 274877906944.0 /* 2^38 */ || run > 512.0 * 4294967296.0 || 4096.0 * q > 1.0;
+  }
+  if (profile == AWG_PROFILE_LINEAR || profile == AWG_PROFILE_EXPONENTIAL) return false;
   double D = std::fabs((double)F1 - (double)F0);
   double l = (double)L;
   double bound = 31465.0 * 60.0 * D / (l * l * l) + 169911.0 * 360.0 * D / (l * l * l * l) +
@@ -1157,7 +1219,11 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     st = chirp_length_impl(duration_s[i], h->fs, &p.L);
     if (st) return st;
     p.profile = profile[i];
-    if (p.profile != AWG_PROFILE_LINEAR && p.profile != AWG_PROFILE_MINJERK) return fail(AWG_EINVAL, "unknown chirp profile");
+    if (p.profile != AWG_PROFILE_LINEAR && p.profile != AWG_PROFILE_MINJERK && p.profile != AWG_PROFILE_EXPONENTIAL)
+      return fail(AWG_EINVAL, "unknown chirp profile");
+    if (p.profile == AWG_PROFILE_EXPONENTIAL && (p.F0 == 0 || p.F1 == 0))
+      return fail(AWG_EINVAL, "an exponential chirp needs f_start, f_end > 0");
+    if (p.profile == AWG_PROFILE_EXPONENTIAL && p.F0 == p.F1) p.profile = AWG_PROFILE_LINEAR;   // the same phase
     p.ns = start_sample[i];
     if (p.ns < h->cursor) return fail(AWG_EINVAL, "chirp starts before the render cursor");
     if (p.ns > INT64_MAX / 2) return fail(AWG_EINVAL, "chirp start too large");
@@ -1180,7 +1246,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     for (size_t i = lo; i < hi; ++i) {
       const Pending& p = pend[i];
       (void)chirp_coeffs_impl(p.F0, p.F1, p.L, p.profile, co[i].d);   // validated above
-      co[i].end_offset = chirp_offset_word(co[i].d, p.L);
+      co[i].end_offset = p.profile == AWG_PROFILE_EXPONENTIAL ? exp_end_offset(p.F0, p.F1, p.L)
+                                                               : chirp_offset_word(co[i].d, p.L);
       co[i].exact = needs_exact(p.F0, p.F1, p.L, p.profile);
     }
   };
@@ -1225,7 +1292,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     c.n_s = p.ns;
     c.L = p.L;
     c.tone = p.tone;
-    c.flags = (co[pi].exact ? awgk::TONE_EXACT : 0) | (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0);
+    c.flags = (co[pi].exact ? awgk::TONE_EXACT : 0) | (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0) |
+              (p.profile == AWG_PROFILE_EXPONENTIAL ? awgk::TONE_EXP : 0);
     const uint64_t phi_end = c.phi_start + co[pi].end_offset;
     t.slot = slot;
     t.n_s = p.ns;

@@ -46,6 +46,8 @@ constexpr int32_t TONE_EXACT = 1;    // chirp read from a per-sample table of ex
 constexpr int32_t TONE_LINEAR = 2;   // linear chirp: differences of order >= 3 are exactly zero
 constexpr int32_t TONE_AMP_RAMP = 4;      // the amplitude ramps (see ToneRec::a_ns)
 constexpr int32_t TONE_AMP_MINJERK = 8;   // ... along the minimum-jerk profile (else linear)
+constexpr int32_t TONE_EXP = 16;          // exponential chirp: ChirpRec::d[0..4] hold F_start, F_end
+                                          // and the doubles alpha, C, e^alpha - 1 (bit patterns)
 
 #if defined(__CUDACC__)
 #define AWG_HD __host__ __device__

@@ -102,9 +102,34 @@ __device__ __forceinline__ U192 dword(const ChirpRec& c, int i) {
   return U192{c.d[3 * i], c.d[3 * i + 1], c.d[3 * i + 2]};
 }
 
+// x 2^64 rounded to an integer, mod 2^128 (two's complement): the double's exact value M 2^e
+// (M its 53-bit integer mantissa) shifted into Q64.64.  Zero for |x| < 2^-65.
+__device__ __forceinline__ unsigned __int128 q64_of(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return 0;
+  const uint64_t M = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = ex - 1075 + 64;
+  unsigned __int128 v;
+  if (sh >= 128) v = 0;
+  else if (sh >= 0) v = (unsigned __int128)M << sh;
+  else if (sh > -54) v = ((unsigned __int128)M + ((unsigned __int128)1 << (-sh - 1))) >> (-sh);
+  else v = 0;
+  return (b >> 63) ? (unsigned __int128)0 - v : v;
+}
+
+// Exponential chirp (TONE_EXP): the phase offset R(m) = C (e^(alpha m) - 1) words (the integral of
+// the frequency F_start e^(alpha t)), FP64, rounded to the word.
+__device__ __forceinline__ uint64_t exp_chirp_offset(const ChirpRec& c, int64_t m) {
+  const double alpha = __longlong_as_double((long long)c.d[2]);
+  const double C = __longlong_as_double((long long)c.d[3]);
+  return (uint64_t)((q64_of(C * expm1(alpha * (double)m)) + ((unsigned __int128)1 << 63)) >> 64);
+}
+
 // Exact phase word of a chirp at offset m from its start: Phi(n_s) + top64(sum_i d_i C(m, i)).
-// d_0 carries the 2^127 rounding offset.
+// d_0 carries the 2^127 rounding offset.  (Exponential chirps: Phi(n_s) + R(m).)
 __device__ uint64_t exact_chirp_word(const ChirpRec& c, int64_t m, const uint64_t (*inv)[3]) {
+  if (c.flags & TONE_EXP) return c.phi_start + exp_chirp_offset(c, m);
   U192 b[7];
   binomials(m, inv, b);
   U192 s = {0, 0, 0};
@@ -324,30 +349,17 @@ __device__ __forceinline__ uint64_t round_q64(unsigned __int128 v) {
   return (uint64_t)((v + ((unsigned __int128)1 << 63)) >> 64);
 }
 
-// DEG = 2 (linear chirps) or 6 (minimum-jerk).  The unit-stride differences at the tile start
-// are exact (192-bit); the stride-RUN transform that follows only needs the word-level result,
-// so it runs on the upper 128 bits (error < W 2^-64 word per term, below 2^-20 word).
+// The stride-RUN records of a tile from the unit-stride forward differences h[1..DEG] of the
+// chirp phase at the tile start (Q64.64 words, mod 2^128) and its phase word B0.
 template <int DEG>
-__device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const PrepArgs& a, TileRec& out) {
-  U192 bin[DEG + 1];
-  binomials_deg<DEG>(m, a.inv_odd, bin);
-  U192 acc[DEG + 1];
-#pragma unroll
-  for (int k = 0; k <= DEG; ++k) {
-    U192 s = {0, 0, 0};
-#pragma unroll
-    for (int i = k; i <= DEG; ++i) s = add192(s, mul192(dword(c, i), bin[i - k]));
-    acc[k] = s;
-  }
-  unsigned __int128 h[DEG + 1];
-#pragma unroll
-  for (int k = 0; k <= DEG; ++k) h[k] = hi128(acc[k]);
+__device__ __forceinline__ void stride_records(const unsigned __int128* h, uint64_t B0, const PrepArgs& a,
+                                               TileRec& out) {
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
     unsigned __int128 s = 0;
 #pragma unroll
     for (int i = q; i <= DEG; ++i) s += h[i] * (unsigned __int128)(__int128)a.W[q][i];
-    out.B[q] = (q == 0) ? c.phi_start + acc[0].w2 : (q <= DEG ? round_q64(s) : 0);   // acc_0 holds 2^127
+    out.B[q] = (q == 0) ? B0 : (q <= DEG ? round_q64(s) : 0);
   }
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
@@ -370,6 +382,47 @@ __device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const Pre
     for (int i = q; i + 3 <= DEG; ++i) s += h[i + 3] * (unsigned __int128)(__int128)a.W[q][i];
     out.H[q] = (q + 3 <= DEG) ? round_q64(s) : 0;
   }
+}
+
+// DEG = 2 (linear chirps) or 6 (minimum-jerk).  The unit-stride differences at the tile start
+// are exact (192-bit); the stride-RUN transform that follows only needs the word-level result,
+// so it runs on the upper 128 bits (error < W 2^-64 word per term, below 2^-20 word).
+template <int DEG>
+__device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const PrepArgs& a, TileRec& out) {
+  U192 bin[DEG + 1];
+  binomials_deg<DEG>(m, a.inv_odd, bin);
+  U192 acc[DEG + 1];
+#pragma unroll
+  for (int k = 0; k <= DEG; ++k) {
+    U192 s = {0, 0, 0};
+#pragma unroll
+    for (int i = k; i <= DEG; ++i) s = add192(s, mul192(dword(c, i), bin[i - k]));
+    acc[k] = s;
+  }
+  unsigned __int128 h[DEG + 1];
+#pragma unroll
+  for (int k = 0; k <= DEG; ++k) h[k] = hi128(acc[k]);
+  stride_records<DEG>(h, c.phi_start + acc[0].w2, a, out);   // acc_0 holds 2^127
+}
+
+// Exponential chirps: the unit forward differences of R(m) = C (e^(alpha m) - 1) at the tile
+// start are C e^(alpha m) q^k (k >= 1, q = e^alpha - 1), in FP64 (a few 1e-10 turn), cut after
+// order 6: the set-up gives a chirp a per-sample table instead when the dropped orders could
+// reach 2^-26 turn over a tile.
+__device__ __forceinline__ void prep_exp(const ChirpRec& c, int64_t m, const PrepArgs& a, TileRec& out) {
+  const double alpha = __longlong_as_double((long long)c.d[2]);
+  const double C = __longlong_as_double((long long)c.d[3]);
+  const double q = __longlong_as_double((long long)c.d[4]);
+  const double e1 = expm1(alpha * (double)m);
+  unsigned __int128 h[7];
+  h[0] = q64_of(C * e1);
+  double g = C * (e1 + 1.0) * q;
+#pragma unroll
+  for (int k = 1; k <= 6; ++k) {
+    h[k] = q64_of(g);
+    g *= q;
+  }
+  stride_records<6>(h, c.phi_start + (uint64_t)((h[0] + ((unsigned __int128)1 << 63)) >> 64), a, out);
 }
 
 // Programmatic dependent launch (pipelined chunk sequences): the next kernel in the stream may
@@ -402,6 +455,7 @@ __global__ void __launch_bounds__(128) prep_kernel(const __grid_constant__ PrepA
   const int64_t T0 = (a.tile0 + t) * (int64_t)TILE;
   TileRec out;
   if (c.flags & TONE_LINEAR) prep_one<2>(c, T0 - c.n_s, a, out);
+  else if (c.flags & TONE_EXP) prep_exp(c, T0 - c.n_s, a, out);
   else prep_one<6>(c, T0 - c.n_s, a, out);
   a.recs[(int64_t)(a.act_base + ai) * a.n_tiles + t] = out;
 }

@@ -82,7 +82,29 @@ def test_chirp_coefficient_errors(awglib):
     with pytest.raises(awglib.AwgError):
         awglib.chirp_coeffs(1, 2, 1 << 28, 1)
     with pytest.raises(awglib.AwgError):
-        awglib.chirp_coeffs(1, 2, 100, 2)
+        awglib.chirp_coeffs(1, 2, 100, 3)
+    with pytest.raises(awglib.AwgError):       # exponential chirps need both ends > 0
+        awglib.chirp_coeffs(0, 2, 100, 2)
+    with pytest.raises(awglib.AwgError):
+        awglib.chirp_coeffs(5, 0, 100, 2)
+
+
+def test_exponential_chirp_parameters(awglib):
+    """The exponential profile's words: F_start, F_end and the doubles alpha = ln(F_end/F_start)/L,
+    C = F_start/alpha and e^alpha - 1 (bit patterns); equal ends give the linear profile's words."""
+    import math
+    import struct
+    M = 1 << 64
+    for F0, F1, L in ((1 << 62, 3 << 61, 100_000), (M - 1, 12345678901234, 7), (1 << 40, (1 << 40) + 1, (1 << 28) - 1)):
+        w = awglib.chirp_coeffs(F0, F1, L, 2)
+        limbs = [(w[k] >> (64 * j)) & (M - 1) for k in range(7) for j in range(3)]
+        assert limbs[0] == F0 and limbs[1] == F1 and not any(limbs[5:])
+        alpha, C, q = (struct.unpack("<d", struct.pack("<Q", v))[0] for v in limbs[2:5])
+        lam = math.log(F1 / F0) if abs(F1 / F0 - 1) > 1e-3 else math.log1p((F1 - F0) / F0)
+        assert abs(alpha * L / lam - 1) < 1e-13
+        assert abs(C * alpha / F0 - 1) < 1e-15
+        assert abs(q / math.expm1(alpha) - 1) < 1e-15
+    assert awglib.chirp_coeffs(777, 777, 500, 2) == awglib.chirp_coeffs(777, 777, 500, 0)
 
 
 def test_bad_arguments_rejected_without_gpu(awglib):
