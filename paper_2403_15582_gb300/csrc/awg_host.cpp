@@ -432,6 +432,11 @@ struct awg {
   int32_t static_engine = AWG_STATIC_DIRECT;
   float* d_base = nullptr;             // tensor-core engine: FP32 sum of the window's static tones
   size_t cap_base = 0;
+  // split sums without clusters: two scratch buffers (alternating between consecutive launches)
+  // of part_tiles x part_split partial tiles each, and a 64-bit counter per tile per buffer
+  float* d_part = nullptr;
+  unsigned long long* d_tctr = nullptr;
+  int32_t part_tiles = 0, part_split = 0, ctr_split = 0;
   int32_t* d_list = nullptr;           // tensor-core engine: tones not static in some tile of the window
   size_t cap_list = 0;
   std::vector<int32_t> list;
@@ -498,6 +503,44 @@ int ensure(T** ptr, size_t* cap, size_t need, awg_t* h, const char* what) {
   *cap = ncap;
   return AWG_OK;
 }
+
+// Scratch for launches of up to `tiles` tiles with tone split `split` (> 1): two buffers of
+// part_tiles x part_split partial tiles (capacities) and part_tiles tile counters each.  The
+// counters count every CTA of every launch, and a CTA is the last of its tile when its count is
+// split - 1 mod split; so they are zeroed when allocated and whenever the split changes.
+constexpr int32_t SPLIT_LAUNCH_TILES = 512;   // tiles per render launch when the split sums in scratch
+int ensure_split_scratch(awg_t* h, int32_t tiles, int32_t split) {
+  if (tiles <= h->part_tiles && split <= h->part_split && split == h->ctr_split) return AWG_OK;
+  int st = wait_idle(h);
+  if (st) return st;
+  cudaError_t e = cudaSuccess;
+  if (tiles > h->part_tiles || split > h->part_split) {
+    const int32_t nt = std::max(tiles, h->part_tiles), ns = std::max(split, h->part_split);
+    cudaFree(h->d_part);
+    cudaFree(h->d_tctr);
+    h->d_part = nullptr;
+    h->d_tctr = nullptr;
+    h->part_tiles = h->part_split = 0;
+    e = cudaMalloc((void**)&h->d_part, (size_t)2 * nt * ns * awgk::TILE * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_tctr, (size_t)2 * nt * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AWG_ENOMEM, "cudaMalloc split scratch");
+    }
+    h->part_tiles = nt;
+    h->part_split = ns;
+  }
+  if ((e = cudaMemset(h->d_tctr, 0, (size_t)2 * h->part_tiles * sizeof(unsigned long long))) != cudaSuccess)
+    return cuda_fail(e, "split counters");
+  h->ctr_split = split;
+  return AWG_OK;
+}
+
+// Scratch buffer b (0 or 1) of the split sums.
+float* split_part(awg_t* h, int b) {
+  return h->d_part + (size_t)b * (size_t)h->part_tiles * (size_t)h->part_split * awgk::TILE;
+}
+unsigned long long* split_ctr(awg_t* h, int b) { return h->d_tctr + (size_t)b * (size_t)h->part_tiles; }
 
 int upload_tones(awg_t* h) {
   int st = ensure(&h->d_tones, &h->cap_tones, std::max<size_t>(1, h->tones.size()), h, "tones");
@@ -689,6 +732,12 @@ int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
   }
   int st = ensure(&h->d_recs, &h->cap_recs, std::max<size_t>(1, active.size() * (size_t)n_tiles), h, "tile records");
   if (st) return st;
+  // With a split, the window goes out in launches of at most SPLIT_LAUNCH_TILES tiles, chained by
+  // programmatic dependent launch, on alternating scratch buffers.
+  const int32_t split_used = tone_list ? list_split : h->split;
+  const bool scratch = split_used > 1;
+  const int32_t per_launch = scratch ? std::min(n_tiles, SPLIT_LAUNCH_TILES) : n_tiles;
+  if (scratch && (st = ensure_split_scratch(h, per_launch, split_used))) return st;
 
   // The chirp tile set-up runs in stream order right before the render.  (Running it on a second
   // stream, overlapped with the previous render, takes SM slots from the render and pushes its
@@ -743,17 +792,31 @@ int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
     ra.split = list_split;
     for (int r = 0; r <= list_split; ++r) ra.bounds[r] = list_bounds[r];
   }
-  ra.tile0 = tile0;
-  ra.n_tiles = n_tiles;
-  ra.win_start = c;
-  ra.win_end = c + n;
-  ra.out_q = out_q;
-  ra.out_f = out_f;
   ra.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
   ra.status = h->d_status;
   std::memcpy(ra.inv_odd, h->inv_odd, sizeof(ra.inv_odd));
-  if ((e = awgk::launch_render(ra, s)) != cudaSuccess) return cuda_fail(e, "render launch");
-  ++launches;
+  for (int32_t t0 = 0, i = 0; t0 < n_tiles; t0 += per_launch, ++i) {
+    awgk::RenderArgs rs = ra;
+    const int32_t nt = std::min(per_launch, n_tiles - t0);
+    const int64_t w0 = std::max(c, (tile0 + t0) * (int64_t)awgk::TILE);
+    const int64_t w1 = std::min(c + n, (tile0 + t0 + nt) * (int64_t)awgk::TILE);
+    rs.tile0 = tile0 + t0;
+    rs.n_tiles = nt;
+    rs.rec_stride = n_tiles;
+    rs.rec_tile0 = t0;
+    rs.win_start = w0;
+    rs.win_end = w1;
+    rs.out_q = out_q ? out_q + (size_t)(w0 - c) * (size_t)(q_stride ? q_stride : 1) : nullptr;
+    rs.out_f = out_f ? out_f + (w0 - c) : nullptr;
+    rs.base = base ? base + (w0 - c) : nullptr;
+    if (scratch) {
+      rs.part = split_part(h, i & 1);
+      rs.tile_ctr = split_ctr(h, i & 1);
+      rs.pdl = n_tiles > per_launch ? (i == 0 ? 1 : 2) : 0;
+    }
+    if ((e = awgk::launch_render(rs, s)) != cudaSuccess) return cuda_fail(e, "render launch");
+    ++launches;
+  }
   if (pe[3]) {
     if ((e = cudaEventRecord(pe[3], s)) != cudaSuccess) return cuda_fail(e, "event");
     ++h->prof_calls;
@@ -1016,6 +1079,7 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
   }
   int st = ensure(&h->d_seq_recs, &h->cap_seq_recs, max_recs, h, "tile records");
   if (st) return st;
+  if (h->split > 1 && (st = ensure_split_scratch(h, (int32_t)(chunk / awgk::TILE + 2), h->split))) return st;
   st = ensure(&h->d_seq_act, &h->cap_seq_act, std::max<size_t>(1, h->chirps.size()), h, "slot map");
   if (st) return st;
   if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
@@ -1064,6 +1128,10 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
       std::memcpy(ra.inv_odd, h->inv_odd, sizeof(ra.inv_odd));
       ra.pdl = c == g0 ? 1 : 2;
       ra.exit_ctr = h->d_seq_exit;
+      if (h->split > 1) {   // alternating scratch (see tile_epilogue_split)
+        ra.part = split_part(h, c & 1);
+        ra.tile_ctr = split_ctr(h, c & 1);
+      }
       if ((e = awgk::launch_render(ra, s)) != cudaSuccess) return cuda_fail(e, "render launch");
       h->seq_exit_target += (unsigned long long)ra.n_tiles * (unsigned long long)h->split;
     }
@@ -1165,6 +1233,8 @@ void awg_destroy(awg_t* h) {
   cudaFree(h->d_periodic);
   cudaFree(h->d_base);
   cudaFree(h->d_list);
+  cudaFree(h->d_part);
+  cudaFree(h->d_tctr);
   cudaFree(h->d_seq_recs);
   cudaFree(h->d_seq_act);
   cudaFree(h->d_seq_exit);
@@ -1522,8 +1592,10 @@ int awg_render_chunks(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, v
   if (!out) return fail(AWG_EINVAL, "null output");
   if (chunk > (INT64_MAX - h->cursor) / n_chunks) return fail(AWG_EINVAL, "sample index overflow");
   if (chunk / awgk::TILE + 2 > (int64_t)(INT32_MAX / awgk::MAX_SPLIT)) return fail(AWG_EINVAL, "chunk too long");
-  if (n_chunks == 1 || h->profiling || h->periodic_start >= 0 || h->static_engine != AWG_STATIC_DIRECT) {
-    // per-call profiling events would split the pipeline; a periodic tail is replayed per chunk
+  if (n_chunks == 1 || h->profiling || h->periodic_start >= 0 || h->static_engine != AWG_STATIC_DIRECT ||
+      (h->split > 1 && chunk / awgk::TILE + 2 > SPLIT_LAUNCH_TILES)) {
+    // per-call profiling events would split the pipeline; a periodic tail is replayed per chunk;
+    // chunks above SPLIT_LAUNCH_TILES tiles go out in several launches each
     for (int32_t c = 0; c < n_chunks; ++c) {
       const int st = render_impl(h, chunk, nullptr, out + (size_t)c * (size_t)chunk, stream);
       if (st) return st;

@@ -144,8 +144,9 @@ struct RenderArgs {
   int32_t rec_stride;
   int32_t rec_tile0;
   // pipelined chunk sequences (otherwise 0 / null): pdl 1 waits for the preceding kernel (the
-  // records' set-up) and then lets the next kernel launch early; pdl 2 only lets it launch early
-  // (no data from the preceding kernel); each CTA adds 1 to *exit_ctr once its samples are stored
+  // records' set-up) and then lets the next kernel launch early; pdl 2 lets it launch early and
+  // reads nothing the preceding kernel writes (with split scratch, it waits for that kernel before
+  // reusing the scratch); each CTA adds 1 to *exit_ctr once its samples are stored
   int32_t pdl;
   unsigned long long* exit_ctr;
   // tensor-core static engine (otherwise null / 0): tones static over the window are skipped here
@@ -158,6 +159,11 @@ struct RenderArgs {
   const int32_t* tone_list;
   int32_t n_list;
   int32_t bounds[MAX_SPLIT + 1];
+  // split sums without clusters (render_split_kernel; null: cluster reduction): partial tiles
+  // part[(tile split + rank) TILE + sample] and one counter per tile (a multiple of split between
+  // launches: every CTA adds 1)
+  float* part;
+  unsigned long long* tile_ctr;
 };
 
 struct PhaseArgs {

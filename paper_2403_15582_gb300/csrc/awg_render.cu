@@ -559,9 +559,65 @@ struct alignas(16) Desc {
 enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_STATIC_ROT = 4, DESC_SKIP = 5 };
 
 
+// Scale, round half to even, clamp and store sample T0 + sidx of a tile (inside the window),
+// after adding the tensor-core engine's static sum when there is one.
+__device__ __forceinline__ void store_sample(const RenderArgs& a, int64_t n, float x) {
+  if (n < a.win_start || n >= a.win_end) return;
+  if (a.base) x += a.base[n - a.win_start];
+  float q = rintf(x * a.scale);
+  q = fminf(fmaxf(q, -32767.f), 32767.f);
+  if (a.out_q) a.out_q[(n - a.win_start) * (a.q_stride ? a.q_stride : 1)] = (int16_t)q;
+  if (a.out_f) a.out_f[n - a.win_start] = x;
+}
+
+// Sum over the split without clusters.  Thread t holds samples 32 t .. 32 t + 31 of the tile in
+// acc.  With split 1 it stores them; otherwise the CTA writes them to its partial tile
+// a.part[(tile split + crank) TILE ...] and counts itself in on a.tile_ctr[tile]; the CTA that
+// brings the count to split - 1 (mod split) is the last of the tile: it sums the split's partials
+// in rank order (as the cluster reduction does: the same FP32 sums) and stores all 4096 samples.
+// In a pipelined sequence (pdl 2) the scratch of this launch was used two launches back: waiting
+// for the preceding launch to complete (which waited for the one before) makes it free.
+__device__ __forceinline__ void tile_epilogue_split(const RenderArgs& a, int tile, int crank, int split, int64_t T0,
+                                                 const float (&acc)[RUN]) {
+  const int tid = threadIdx.x;
+  __shared__ int s_last;
+  if (split == 1) {
+#pragma unroll
+    for (int u = 0; u < RUN; ++u) store_sample(a, T0 + tid * RUN + u, 0.f + acc[u]);
+  } else {
+    if (a.pdl == 2) pdl_wait();
+    float4* dst = reinterpret_cast<float4*>(a.part + ((int64_t)tile * split + crank) * TILE + tid * RUN);
+#pragma unroll
+    for (int j = 0; j < RUN / 4; ++j) __stcg(dst + j, make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]));
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(&a.tile_ctr[tile], 1ull) % (unsigned long long)split == (unsigned long long)(split - 1);
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      const float* src = a.part + (int64_t)tile * split * TILE;
+      for (int u = 0; u < RUN; ++u) {
+        const int sidx = u * NT + tid;
+        float x = 0.f;
+        for (int c = 0; c < split; ++c) x += __ldcg(src + (int64_t)c * TILE + sidx);
+        store_sample(a, T0 + sidx, x);
+      }
+    }
+  }
+  if (a.exit_ctr) {   // this CTA's samples (if any) are stored and visible
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) atomicAdd(a.exit_ctr, 1ull);
+  }
+}
+
 // One CTA's share of one tile: tones [K crank / split, K (crank+1) / split) of window tile `tile`
-// of the render described by `a` (or the listed tones of its bounds), then the cluster-wide sum
-// and the store of this CTA's slice.
+// of the render described by `a` (or the listed tones of its bounds), then the sum over the split
+// and the store.  CLUSTER: the split's CTAs form a thread-block cluster, sum through distributed
+// shared memory in rank order and each stores a slice.  Otherwise each CTA writes its partial
+// tile to a.part and the last of the split to finish (a counter per tile) sums the partials in
+// rank order and stores the whole tile: the same sums, and no CTA waits for the others.
+template <bool CLUSTER>
 __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile, const int crank, const int split) {
   __shared__ alignas(16) ToneRec s_tone[2][STAGE];
   __shared__ alignas(16) TileRec s_rec[2][STAGE];
@@ -786,6 +842,10 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     __syncthreads();
   }
 
+  if (!CLUSTER) {
+    tile_epilogue_split(a, tile, crank, split, T0, acc);
+    return;
+  }
   // partial sums -> shared memory ([r][thread]), then the cluster-wide sum in rank order
 #pragma unroll
   for (int r = 0; r < RUN; ++r) s_red[r * NT + tid] = acc[r];
@@ -832,7 +892,12 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
 
 __global__ void __launch_bounds__(NT, 5) render_kernel(const __grid_constant__ RenderArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
-  render_tile(a, blockIdx.x / a.split, (int)cluster.block_rank(), a.split);
+  render_tile<true>(a, blockIdx.x / a.split, (int)cluster.block_rank(), a.split);
+}
+
+// The same without clusters (a.part set): CTA blockIdx.x takes rank blockIdx.x % split.
+__global__ void __launch_bounds__(NT, 5) render_split_kernel(const __grid_constant__ RenderArgs a) {
+  render_tile<false>(a, blockIdx.x / a.split, blockIdx.x % a.split, a.split);
 }
 
 // Several renders in one grid (continuous batching): cluster i renders window tile items[i].y of
@@ -842,7 +907,7 @@ __global__ void __launch_bounds__(NT, 5) render_batch_kernel(const RenderArgs* _
   cg::cluster_group cluster = cg::this_cluster();
   const int split = (int)cluster.num_blocks();
   const int2 it = items[blockIdx.x / split];
-  render_tile(reqs[it.x], it.y, (int)cluster.block_rank(), split);
+  render_tile<true>(reqs[it.x], it.y, (int)cluster.block_rank(), split);
 }
 
 // Exact phase words of the first n tones at one sample (test hook).
@@ -879,6 +944,7 @@ __global__ void trace_kernel(const __grid_constant__ TraceArgs a) {
 
 cudaError_t render_setup_attributes() {
   cudaError_t e = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  // the epilogue's shared flag is below the carve-out either way; no attribute for render_split_kernel
   if (e == cudaSuccess) e = cudaFuncSetAttribute(render_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
@@ -965,6 +1031,11 @@ cudaError_t launch_render(const RenderArgs& a, cudaStream_t s) {
   attr[0].val.clusterDim.z = 1;
   attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[1].val.programmaticStreamSerializationAllowed = 1;
+  if (a.part) {   // no cluster: the split sums through the scratch partials
+    cfg.attrs = attr + 1;
+    cfg.numAttrs = a.pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, render_split_kernel, a);
+  }
   cfg.attrs = attr;
   cfg.numAttrs = a.pdl ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, render_kernel, a);
