@@ -5,10 +5,10 @@ Workload (the one the headline metric is quoted on): 1000 tones, each chirped fr
 frequency to a seeded target in 80-180 MHz over 35 ms at 280 MS/s (9.8M samples); even tones
 linear, odd tones minimum-jerk; amplitudes U[0.5, 1]/1000; int16 output in 2^18-sample chunks.
 
-One step = the whole record rendered chunk by chunk through the C ABI: awg_render_chunks over the
-37 full chunks (one chirp tile set-up per group of chunks, one render kernel per chunk with its
-fused quantise-and-store, consecutive renders overlapping on the device), then the last, shorter
-chunk through awg_render.  `value` is tone-samples per second with the tone state resident on the
+One step = the whole record rendered chunk by chunk through the C ABI: awg_render_stream over the
+37 full chunks and the last, shorter one (one chirp tile set-up per group of chunks, one render
+kernel per chunk with its fused quantise-and-store, consecutive renders overlapping on the
+device).  `value` is tone-samples per second with the tone state resident on the
 device; `e2e` repeats the step through the public API from host arrays (set_tones + set_chirps,
 then rendering straight into pinned host memory).  The CPU oracle is timed on the host cores on a
 bounded window of the same workload (`cpu_baseline`); `--impl reference` times only that oracle.
@@ -41,8 +41,8 @@ SFU_SIN_PER_CLK_SM = 16
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 # DRAM traffic (read + write) of one render launch (2^18-sample chunk, 1000 chirping tones) from
-# the ncu capture summarised in profiles/render_kernel_chirp1000_chunk2e18.md (cold cache).
-RENDER_TRAFFIC_BYTES = 11.419648e6   # ncu dram__bytes_read+write of one 2^18-sample render launch
+# the ncu capture summarised in profiles/render_split_kernel_chirp1000_chunk2e18.md (cold cache).
+RENDER_TRAFFIC_BYTES = 11.448064e6   # ncu dram__bytes_read+write of one 2^18-sample render launch
 
 CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
                 "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
@@ -330,7 +330,6 @@ def chirp_profile_leg(awg, stream, wk, reps: int = 3):
     import numpy as np
     import torch
     N, chunk = wk.n_samples, wk.chunk
-    n_full, tail = N // chunk, N % chunk
     tone, f0, f1, dur, _, start = wk.chirp_arrays()
     out = torch.empty(N, dtype=torch.int16, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -346,9 +345,7 @@ def chirp_profile_leg(awg, stream, wk, reps: int = 3):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            synth.render_chunks(chunk, n_full, out, stream)
-            if tail:
-                synth.render(tail, out[n_full * chunk:], stream)
+            synth.render_stream(N, chunk, out, stream)
             e1.record(stream)
             torch.cuda.synchronize()
             if r:
@@ -487,10 +484,8 @@ def main():
     n_full, tail = N // chunk, N % chunk
 
     def render_record(dst):
-        # the chunk loop as one pipelined sequence of chunk renders, then the short last chunk
-        synth.render_chunks(chunk, n_full, dst, stream)
-        if tail:
-            synth.render(tail, dst[n_full * chunk:], stream)
+        # the chunk loop as one pipelined sequence of chunk renders, the short last chunk included
+        synth.render_stream(N, chunk, dst, stream)
 
     def step_device():
         synth.seek(0)
@@ -512,6 +507,7 @@ def main():
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
+    launches0 = synth.launch_count
     for i in range(args.steps):
         flush.zero_()
         ev[i][0].record(stream)
@@ -520,9 +516,9 @@ def main():
     torch.cuda.synchronize()
     barrier()
     sampler.stop()
-    # our kernels per step: the chirp set-up of the chunk sequence, one render per full chunk, the
-    # join, and the last chunk's set-up and render
-    launches = args.steps * (1 + n_full + 1 + (2 if tail else 0))
+    # our kernels in the timed steps (the library's own count): per group of chunks one chirp
+    # set-up and one join, and one render per chunk
+    launches = synth.launch_count - launches0
     # kernel split and per-chunk latency: the same chunks rendered one call at a time with the
     # library's profiling events (separately from the timed steps; events split the pipeline)
     synth.profile_begin()
@@ -581,7 +577,7 @@ def main():
                              "playback_ms": 1e3 * chunk / wk.fs},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tsin/s",
                      "frac": achieved / peak, "traffic": RENDER_TRAFFIC_BYTES,
-                     "kernel": "render_kernel", "peak_source": "16 SFU sin/clk/SM x 152 SMs x 2070 MHz",
+                     "kernel": "render_split_kernel", "peak_source": "16 SFU sin/clk/SM x 152 SMs x 2070 MHz",
                      "basis": "timed steps: sines / step time (pipelined chunk renders, set-up included)",
                      "isolated_launch": {"achieved": achieved_isolated, "frac": achieved_isolated / peak,
                                          "basis": "chunk-by-chunk pass: sines / render kernel event time"}},

@@ -227,14 +227,26 @@ int awg_render_multiplexed(awg_t* const* handles, int32_t n_channels, int64_t n,
 
 /* Render n_chunks consecutive chunks of `chunk` samples (the chunk loop of Sec. IV: the cursor
  * advances chunk by chunk) into out[0 .. n_chunks * chunk), with the same samples as n_chunks
- * calls of awg_render.  The chunks are issued as one pipelined sequence: the chirp set-up of chunk
- * c+1 and the start of its render overlap the end of chunk c's render on the device (programmatic
- * dependent launch; two record buffers used alternately, guarded by device counters), and a final
- * join kernel restores plain stream order for later work on `stream`.  out is device memory or
- * mapped pinned host memory.  AWG_EINVAL for chunk < 1, n_chunks < 0 or overflow.  A wait that
- * times out inside the sequence (about 2 s) sets the device status to AWG_ETIMEOUT (see
- * awg_device_status). */
+ * calls of awg_render.  The chunks are issued as one pipelined sequence: the chunks go in groups
+ * whose chirp tile records fit a fixed budget (2M records); one set-up launch per group computes
+ * the records of all its chunks, then the chunk renders follow with programmatic dependent
+ * launch, so that each render starts while the one before drains; a join kernel (a bounded wait
+ * on a device counter of finished render CTAs) ends each group and restores plain stream order
+ * for later work on `stream`.  out is device memory or mapped pinned host memory.  AWG_EINVAL for
+ * chunk < 1, n_chunks < 0 or overflow.  A wait that times out inside the sequence (about 2 s)
+ * sets the device status to AWG_ETIMEOUT (see awg_device_status). */
 int awg_render_chunks(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, void* stream);
+
+/* Render n samples from the cursor as consecutive chunks of `chunk` samples, the last one shorter
+ * when chunk does not divide n, in one pipelined sequence as awg_render_chunks (the short last
+ * chunk included, so that its render overlaps the one before).  out[0 .. n).  The same samples as
+ * awg_render of n samples.  AWG_EINVAL for chunk < 1, n < 0 or overflow. */
+int awg_render_stream(awg_t* h, int64_t n, int64_t chunk, int16_t* out, void* stream);
+
+/* Number of kernels the handle has launched so far (every render, set-up, join, table and replay
+ * kernel, including those of set-up calls and test hooks); -1 for a null handle.  Read it before
+ * and after a region to count that region's launches. */
+int64_t awg_launch_count(const awg_t* h);
 
 /* Phase words Phi_k(sample) of the first n tones (n <= tone count), computed on the device by the
  * exact closed form (192-bit, the function that seeds every render tile) and copied to

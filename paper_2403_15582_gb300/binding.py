@@ -64,6 +64,8 @@ SIGNATURES = [
     ("awg_render", ctypes.c_int, [P, i64, P, P]),
     ("awg_render_f32", ctypes.c_int, [P, i64, P, P, P]),
     ("awg_render_chunks", ctypes.c_int, [P, i64, i32, P, P]),
+    ("awg_render_stream", ctypes.c_int, [P, i64, i64, P, P]),
+    ("awg_launch_count", i64, [P]),
     ("awg_render_multiplexed", ctypes.c_int, [P, i32, i64, P, P]),
     ("awg_phase_words", ctypes.c_int, [P, i64, P, i32]),
     ("awg_render_phases", ctypes.c_int, [P, i32, i64, i32, P]),
@@ -281,6 +283,15 @@ class Synth:
     def render_chunks(self, chunk: int, n_chunks: int, out, stream=None):
         """n_chunks consecutive chunks of `chunk` samples into out, as one pipelined sequence."""
         _check(lib().awg_render_chunks(self._h, int(chunk), int(n_chunks), _ptr(out), _stream_ptr(stream)))
+
+    @property
+    def launch_count(self) -> int:
+        """Kernels this handle has launched so far."""
+        return int(lib().awg_launch_count(self._h))
+
+    def render_stream(self, n: int, chunk: int, out, stream=None):
+        """n samples as pipelined chunks of `chunk` samples (the last one shorter)."""
+        _check(lib().awg_render_stream(self._h, int(n), int(chunk), _ptr(out), _stream_ptr(stream)))
 
     def table_gemm(self, log2_len: int, precision: int, out_q=None, out_f=None, stream=None):
         _check(lib().awg_table_gemm(self._h, int(log2_len), int(precision), _ptr(out_q), _ptr(out_f), _stream_ptr(stream)))

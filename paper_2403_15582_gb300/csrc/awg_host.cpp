@@ -437,6 +437,7 @@ struct awg {
   float* d_part = nullptr;
   unsigned long long* d_tctr = nullptr;
   int32_t part_tiles = 0, part_split = 0, ctr_split = 0;
+  int64_t n_launches = 0;              // kernels this handle has launched
   int32_t* d_list = nullptr;           // tensor-core engine: tones not static in some tile of the window
   size_t cap_list = 0;
   std::vector<int32_t> list;
@@ -479,6 +480,12 @@ void fill_constants(awg_t* h) {
     W192 x = w_inverse_odd(odd[i]);
     for (int j = 0; j < 3; ++j) h->inv_odd[i][j] = x.w[j];
   }
+}
+
+// A kernel launch of the handle, counted (awg_launch_count).
+inline cudaError_t counted(awg_t* h, cudaError_t e) {
+  ++h->n_launches;
+  return e;
 }
 
 int wait_idle(awg_t* h) {
@@ -664,7 +671,7 @@ int build_exact_tables(awg_t* h) {
     ta.slot = (int32_t)sl;
     ta.out = h->d_tab + off;
     std::memcpy(ta.inv_odd, h->inv_odd, sizeof(ta.inv_odd));
-    cudaError_t e = awgk::launch_exact_table(ta, c.L, h->priv);
+    cudaError_t e = counted(h, awgk::launch_exact_table(ta, c.L, h->priv));
     if (e != cudaSuccess) return cuda_fail(e, "exact table launch");
     h->tones[(size_t)c.tone].tab_off = (int32_t)off;
     off += (size_t)c.L + 1;
@@ -705,8 +712,8 @@ int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
     const int64_t c = h->cursor, n2 = n - n1;
     cudaError_t e;
     if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
-    if ((e = awgk::launch_replay(h->d_periodic, h->periodic_log2, c, n2, out_q + (size_t)n1 * (size_t)q_stride,
-                                 q_stride, s)) != cudaSuccess)
+    if ((e = counted(h, awgk::launch_replay(h->d_periodic, h->periodic_log2, c, n2, out_q + (size_t)n1 * (size_t)q_stride,
+                                 q_stride, s))) != cudaSuccess)
       return cuda_fail(e, "replay launch");
     if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
     if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
@@ -768,7 +775,7 @@ int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
     std::memcpy(pa.W, h->W, sizeof(pa.W));
     std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
     for (int i = 0; i < pa.n_active; ++i) pa.slots[i] = active[b + (size_t)i];
-    if ((e = awgk::launch_prep(pa, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+    if ((e = counted(h, awgk::launch_prep(pa, s))) != cudaSuccess) return cuda_fail(e, "prep launch");
     ++launches;
   }
   if (pe[1] && (e = cudaEventRecord(pe[1], s)) != cudaSuccess) return cuda_fail(e, "event");
@@ -814,7 +821,7 @@ int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
       rs.tile_ctr = split_ctr(h, i & 1);
       rs.pdl = n_tiles > per_launch ? (i == 0 ? 1 : 2) : 0;
     }
-    if ((e = awgk::launch_render(rs, s)) != cudaSuccess) return cuda_fail(e, "render launch");
+    if ((e = counted(h, awgk::launch_render(rs, s))) != cudaSuccess) return cuda_fail(e, "render launch");
     ++launches;
   }
   if (pe[3]) {
@@ -909,8 +916,8 @@ int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
     t.status = h->d_status;
     cudaError_t e;
     if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
-    if ((e = awgk::launch_table_prep(t, s)) != cudaSuccess) return cuda_fail(e, "static operand launch");
-    if ((e = awgk::launch_table_gemm(t, s)) != cudaSuccess) return cuda_fail(e, "static GEMM launch");
+    if ((e = counted(h, awgk::launch_table_prep(t, s))) != cudaSuccess) return cuda_fail(e, "static operand launch");
+    if ((e = counted(h, awgk::launch_table_gemm(t, s))) != cudaSuccess) return cuda_fail(e, "static GEMM launch");
     if (all_static) {
       if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
       if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
@@ -987,7 +994,7 @@ int awgk::prepare_render(awg_t* h, int64_t n, int16_t* out_q, float* out_f, cuda
     std::memcpy(pa.W, h->W, sizeof(pa.W));
     std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
     for (int i = 0; i < pa.n_active; ++i) pa.slots[i] = active[b + (size_t)i];
-    cudaError_t e = awgk::launch_prep(pa, s);
+    cudaError_t e = counted(h, awgk::launch_prep(pa, s));
     if (e != cudaSuccess) return cuda_fail(e, "prep launch");
   }
   std::memset(ra, 0, sizeof(*ra));
@@ -1040,7 +1047,13 @@ std::vector<int32_t> active_slots(const awg_t* h, int64_t c, int64_t n, int64_t*
 // chunk complete.
 constexpr size_t SEQ_RECORD_BUDGET = (size_t)1 << 21;   // 2M records (352 MiB) per group
 
-int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, cudaStream_t s) {
+int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, cudaStream_t s, int64_t tail = 0) {
+  // chunks 0 .. n_chunks - 1 of `chunk` samples, then (tail > 0) one of `tail` samples
+  const int64_t n_total = (int64_t)n_chunks * chunk + tail;
+  if (tail > 0) ++n_chunks;
+  auto span = [&](int32_t a, int32_t b) {   // samples of chunks a .. b - 1
+    return std::min((int64_t)b * chunk, n_total) - (int64_t)a * chunk;
+  };
   cudaError_t e;
   if (!h->d_seq_exit) {
     if (cudaMalloc((void**)&h->d_seq_exit, sizeof(unsigned long long)) != cudaSuccess)
@@ -1062,11 +1075,11 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
     Group g;
     g.g0 = g0;
     g.g1 = g0 + 1;
-    g.active = active_slots(h, c0 + (int64_t)g0 * chunk, chunk, &g.tile0, &g.n_tiles);
+    g.active = active_slots(h, c0 + (int64_t)g0 * chunk, span(g0, g0 + 1), &g.tile0, &g.n_tiles);
     while (g.g1 < n_chunks) {
       int64_t t0;
       int32_t nt;
-      std::vector<int32_t> a2 = active_slots(h, c0 + (int64_t)g0 * chunk, (int64_t)(g.g1 + 1 - g0) * chunk, &t0, &nt);
+      std::vector<int32_t> a2 = active_slots(h, c0 + (int64_t)g0 * chunk, span(g0, g.g1 + 1), &t0, &nt);
       if (a2.size() * (size_t)nt > SEQ_RECORD_BUDGET || nt > INT32_MAX / awgk::MAX_SPLIT) break;
       g.active.swap(a2);
       g.tile0 = t0;
@@ -1101,11 +1114,11 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
       std::memcpy(pa.W, h->W, sizeof(pa.W));
       std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
       for (int i = 0; i < pa.n_active; ++i) pa.slots[i] = active[b + (size_t)i];
-      if ((e = awgk::launch_prep(pa, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+      if ((e = counted(h, awgk::launch_prep(pa, s))) != cudaSuccess) return cuda_fail(e, "prep launch");
     }
     for (int32_t c = g0; c < g1; ++c) {
-      const int64_t wc = c0 + (int64_t)c * chunk;
-      const int64_t t_first = wc / awgk::TILE, t_last = (wc + chunk - 1) / awgk::TILE;
+      const int64_t wc = c0 + (int64_t)c * chunk, len = span(c, c + 1);
+      const int64_t t_first = wc / awgk::TILE, t_last = (wc + len - 1) / awgk::TILE;
       awgk::RenderArgs ra;
       std::memset(&ra, 0, sizeof(ra));
       ra.tones = h->d_tones;
@@ -1121,7 +1134,7 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
       ra.tile0 = t_first;
       ra.n_tiles = (int32_t)(t_last - t_first + 1);
       ra.win_start = wc;
-      ra.win_end = wc + chunk;
+      ra.win_end = wc + len;
       ra.out_q = out + (size_t)c * (size_t)chunk;
       ra.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
       ra.status = h->d_status;
@@ -1132,17 +1145,17 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
         ra.part = split_part(h, c & 1);
         ra.tile_ctr = split_ctr(h, c & 1);
       }
-      if ((e = awgk::launch_render(ra, s)) != cudaSuccess) return cuda_fail(e, "render launch");
+      if ((e = counted(h, awgk::launch_render(ra, s))) != cudaSuccess) return cuda_fail(e, "render launch");
       h->seq_exit_target += (unsigned long long)ra.n_tiles * (unsigned long long)h->split;
     }
-    if ((e = awgk::launch_join(h->d_seq_exit, h->seq_exit_target, h->d_status, s)) != cudaSuccess)
+    if ((e = counted(h, awgk::launch_join(h->d_seq_exit, h->seq_exit_target, h->d_status, s))) != cudaSuccess)
       return cuda_fail(e, "join launch");
   }
   if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
   if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
   h->timed = true;
   h->have_done = true;
-  h->cursor = c0 + (int64_t)n_chunks * chunk;
+  h->cursor = c0 + n_total;
   return AWG_OK;
 }
 
@@ -1605,6 +1618,29 @@ int awg_render_chunks(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, v
   return render_chunks_impl(h, chunk, n_chunks, out, (cudaStream_t)stream);
 }
 
+int64_t awg_launch_count(const awg_t* h) { return h ? h->n_launches : -1; }
+
+int awg_render_stream(awg_t* h, int64_t n, int64_t chunk, int16_t* out, void* stream) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (chunk < 1 || n < 0) return fail(AWG_EINVAL, "chunk must be >= 1 and n >= 0");
+  if (n == 0) return AWG_OK;
+  if (!out) return fail(AWG_EINVAL, "null output");
+  if (h->cursor > INT64_MAX - n) return fail(AWG_EINVAL, "sample index overflow");
+  if (chunk / awgk::TILE + 2 > (int64_t)(INT32_MAX / awgk::MAX_SPLIT)) return fail(AWG_EINVAL, "chunk too long");
+  if (n / chunk > (int64_t)INT32_MAX - 1) return fail(AWG_EINVAL, "too many chunks");
+  const int32_t full = (int32_t)(n / chunk);
+  const int64_t tail = n - (int64_t)full * chunk;
+  if (full + (tail > 0 ? 1 : 0) <= 1 || h->profiling || h->periodic_start >= 0 || h->static_engine != AWG_STATIC_DIRECT ||
+      (h->split > 1 && chunk / awgk::TILE + 2 > SPLIT_LAUNCH_TILES)) {
+    for (int64_t c = 0; c < n; c += chunk) {
+      const int st = render_impl(h, std::min(chunk, n - c), nullptr, out + c, stream);
+      if (st) return st;
+    }
+    return AWG_OK;
+  }
+  return render_chunks_impl(h, chunk, full, out, (cudaStream_t)stream, tail);
+}
+
 int awg_phase_words(awg_t* h, int64_t sample, uint64_t* out_host, int32_t n) {
   if (!h) return fail(AWG_EINVAL, "null handle");
   if (n < 0 || n > h->K) return fail(AWG_EINVAL, "tone count out of range");
@@ -1620,7 +1656,7 @@ int awg_phase_words(awg_t* h, int64_t sample, uint64_t* out_host, int32_t n) {
   pa.sample = sample;
   pa.out = h->d_words;
   std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
-  cudaError_t e = awgk::launch_phase_words(pa, h->priv);
+  cudaError_t e = counted(h, awgk::launch_phase_words(pa, h->priv));
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, h->d_words, (size_t)n * 8, cudaMemcpyDeviceToHost, h->priv);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->priv);
   if (e != cudaSuccess) return cuda_fail(e, "phase words");
@@ -1656,7 +1692,7 @@ int awg_render_phases(awg_t* h, int32_t tone, int64_t n0, int32_t count, uint32_
     std::memcpy(pa.W, h->W, sizeof(pa.W));
     std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
     pa.slots[0] = t.slot;
-    e = awgk::launch_prep(pa, h->priv);
+    e = counted(h, awgk::launch_prep(pa, h->priv));
   }
   awgk::TraceArgs ta;
   ta.tones = h->d_tones;
@@ -1670,7 +1706,7 @@ int awg_render_phases(awg_t* h, int32_t tone, int64_t n0, int32_t count, uint32_
   ta.n_tiles = n_tiles;
   ta.out = h->d_trace;
   std::memcpy(ta.inv_odd, h->inv_odd, sizeof(ta.inv_odd));
-  if (e == cudaSuccess) e = awgk::launch_trace(ta, h->priv);
+  if (e == cudaSuccess) e = counted(h, awgk::launch_trace(ta, h->priv));
   if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, h->d_trace, (size_t)count * 4, cudaMemcpyDeviceToHost, h->priv);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->priv);
   if (e != cudaSuccess) return cuda_fail(e, "render phases");
@@ -1731,10 +1767,10 @@ int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q
   }
   if (e == cudaSuccess) e = cudaEventRecord(h->ev0, s);
   if (e == cudaSuccess && pe[0]) e = cudaEventRecord(pe[0], s);
-  if (e == cudaSuccess) e = awgk::launch_table_prep(t, s);
+  if (e == cudaSuccess) e = counted(h, awgk::launch_table_prep(t, s));
   if (e == cudaSuccess && pe[1]) e = cudaEventRecord(pe[1], s);
   if (e == cudaSuccess && pe[2]) e = cudaEventRecord(pe[2], s);
-  if (e == cudaSuccess) e = awgk::launch_table_gemm(t, s);
+  if (e == cudaSuccess) e = counted(h, awgk::launch_table_gemm(t, s));
   if (e == cudaSuccess && pe[3]) e = cudaEventRecord(pe[3], s);
   if (e == cudaSuccess && pe[3]) {
     ++h->prof_calls;
@@ -1797,14 +1833,14 @@ int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream) {
     pa.slots[pa.n_active++] = (int32_t)sl;
     if (pa.n_active == awgk::MAX_ACTIVE_PER_LAUNCH) {
       pa.act_base = batch_base;
-      if ((e = awgk::launch_prep(pa, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+      if ((e = counted(h, awgk::launch_prep(pa, s))) != cudaSuccess) return cuda_fail(e, "prep launch");
       batch_base += pa.n_active;
       pa.n_active = 0;
     }
   }
   if (pa.n_active > 0) {
     pa.act_base = batch_base;
-    if ((e = awgk::launch_prep(pa, s)) != cudaSuccess) return cuda_fail(e, "prep launch");
+    if ((e = counted(h, awgk::launch_prep(pa, s))) != cudaSuccess) return cuda_fail(e, "prep launch");
   }
   awgk::RenderArgs ra;
   std::memset(&ra, 0, sizeof(ra));
@@ -1825,7 +1861,7 @@ int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream) {
   ra.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
   ra.status = h->d_status;
   std::memcpy(ra.inv_odd, h->inv_odd, sizeof(ra.inv_odd));
-  if ((e = awgk::launch_render(ra, s)) != cudaSuccess) return cuda_fail(e, "render launch");
+  if ((e = counted(h, awgk::launch_render(ra, s))) != cudaSuccess) return cuda_fail(e, "render launch");
   if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
   if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
   h->timed = true;

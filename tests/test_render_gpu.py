@@ -243,6 +243,16 @@ def test_render_chunks_pipelined_equals_chunk_by_chunk(awg, oracle):
     assert s2.device_status() == 0 and s2.cursor == total
     r, g = ref.cpu().numpy(), got.cpu().numpy()
     assert np.array_equal(r, g)   # chunk invariance: the chunking differs, the samples do not
+    # awg_render_stream: chunks that do not divide the window, the short last one in the sequence
+    s3 = make()
+    got3 = torch.full((total,), 12345, dtype=torch.int16, device="cuda")
+    before = s3.launch_count
+    s3.render_stream(123_457, 50_000, got3)
+    s3.render_stream(total - 123_457, 70_001, got3[123_457:])
+    torch.cuda.synchronize()
+    assert s3.device_status() == 0 and s3.cursor == total
+    assert np.array_equal(r, got3.cpu().numpy())
+    assert s3.launch_count - before >= 3 + (total - 123_457 + 70_000) // 70_001
     w = oracle.make_waveform_window(fs, f, a, th, chirps, 0, total)
     idx = np.unique(rng.integers(0, total, 400))
     q_ref = oracle.quantize(oracle.render_at(w, idx, nthreads=NTHREADS), w.full_scale())
