@@ -204,7 +204,11 @@ cudaError_t launch_replay(const int16_t* tab, int32_t log2_len, int64_t c, int64
 cudaError_t launch_join(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status,
                         cudaStream_t s);
 // items[i] = (request index into reqs, window tile); every request has split == `split`.
-cudaError_t launch_render_batch(const RenderArgs* reqs, const int2* items, int n_items, int split, cudaStream_t s);
+// Several renders in one launch (tiles items[i] = (request, tile) of the requests reqs[]; all of
+// tone split `split`); every request carries split scratch (part, tile_ctr with n_tiles zeroed
+// counters).
+cudaError_t launch_render_batch_split(const RenderArgs* reqs, const int2* items, int n_items, int split,
+                                      cudaStream_t s);
 cudaError_t launch_phase_words(const PhaseArgs& a, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, cudaStream_t s);
 cudaError_t render_setup_attributes();

@@ -595,13 +595,17 @@ __device__ __forceinline__ void tile_epilogue_split(const RenderArgs& a, int til
     __syncthreads();
     if (s_last) {
       __threadfence();
-      const float* src = a.part + (int64_t)tile * split * TILE;
-      for (int u = 0; u < RUN; ++u) {
-        const int sidx = u * NT + tid;
-        float x = 0.f;
-        for (int c = 0; c < split; ++c) x += __ldcg(src + (int64_t)c * TILE + sidx);
-        store_sample(a, T0 + sidx, x);
+      // rank by rank, 32 independent loads per thread in flight (sample u NT + tid)
+      const float* src = a.part + (int64_t)tile * split * TILE + tid;
+      float xs[RUN];
+#pragma unroll
+      for (int u = 0; u < RUN; ++u) xs[u] = 0.f;
+      for (int c = 0; c < split; ++c) {
+#pragma unroll
+        for (int u = 0; u < RUN; ++u) xs[u] += __ldcg(src + (int64_t)c * TILE + u * NT);
       }
+#pragma unroll
+      for (int u = 0; u < RUN; ++u) store_sample(a, T0 + u * NT + tid, xs[u]);
     }
   }
   if (a.exit_ctr) {   // this CTA's samples (if any) are stored and visible
@@ -900,14 +904,14 @@ __global__ void __launch_bounds__(NT, 5) render_split_kernel(const __grid_consta
   render_tile<false>(a, blockIdx.x / a.split, blockIdx.x % a.split, a.split);
 }
 
-// Several renders in one grid (continuous batching): cluster i renders window tile items[i].y of
-// request items[i].x; every request of the launch has the same tone split (= the cluster size).
-__global__ void __launch_bounds__(NT, 5) render_batch_kernel(const RenderArgs* __restrict__ reqs,
-                                                               const int2* __restrict__ items) {
-  cg::cluster_group cluster = cg::this_cluster();
-  const int split = (int)cluster.num_blocks();
+// Several renders in one grid (continuous batching): CTA group i (split CTAs) renders window tile
+// items[i].y of request items[i].x; every request of the launch has the same tone split.  The
+// split sums through each request's scratch (reqs[i].part and .tile_ctr, counters zero at
+// launch); CTA blockIdx.x takes rank blockIdx.x % split.
+__global__ void __launch_bounds__(NT, 5) render_batch_split_kernel(const RenderArgs* __restrict__ reqs,
+                                                                     const int2* __restrict__ items, int split) {
   const int2 it = items[blockIdx.x / split];
-  render_tile<true>(reqs[it.x], it.y, (int)cluster.block_rank(), split);
+  render_tile<false>(reqs[it.x], it.y, (int)(blockIdx.x % split), split);
 }
 
 // Exact phase words of the first n tones at one sample (test hook).
@@ -944,26 +948,14 @@ __global__ void trace_kernel(const __grid_constant__ TraceArgs a) {
 
 cudaError_t render_setup_attributes() {
   cudaError_t e = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  // the epilogue's shared flag is below the carve-out either way; no attribute for render_split_kernel
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(render_batch_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
 }
 
-cudaError_t launch_render_batch(const RenderArgs* reqs, const int2* items, int n_items, int split, cudaStream_t s) {
+cudaError_t launch_render_batch_split(const RenderArgs* reqs, const int2* items, int n_items, int split,
+                                      cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(n_items * split), 1, 1);
-  cfg.blockDim = dim3(NT, 1, 1);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = (unsigned)split;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, render_batch_kernel, reqs, items);
+  render_batch_split_kernel<<<(unsigned)(n_items * split), NT, 0, s>>>(reqs, items, split);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {

@@ -108,6 +108,9 @@ double percentile(std::vector<double> v, double q) {
 
 constexpr int NSETS = 3;       // rounds in flight, each on its own stream with its own buffers
 constexpr int RESIDENT = 5;    // render CTAs resident per SM
+// partial tiles of the split sums per round set, allocated up front (256 MiB each): a round of a
+// full 2 ms horizon at ~3e12 tone-samples/s is ~15,000 CTAs of 96 tones; larger rounds grow it
+constexpr size_t PART_TILES = 16384;
 
 struct awg_server {
   double fs = 0;
@@ -140,6 +143,11 @@ struct awg_server {
   awgk::TileRec* d_arena[NSETS] = {};
   int32_t* d_act[NSETS] = {};
   size_t cap_reqs[NSETS] = {}, cap_items[NSETS] = {}, cap_arena[NSETS] = {}, cap_act[NSETS] = {};
+  // split sums of the batched renders: partial tiles (items x split x TILE floats) and a counter
+  // per item, per set
+  float* d_part[NSETS] = {};
+  unsigned long long* d_tctr[NSETS] = {};
+  size_t cap_part[NSETS] = {}, cap_tctr[NSETS] = {};
   std::deque<Round> flight;
   int64_t round_seq = 0;
   double queued_work = 0;      // tone-samples issued and not yet accounted complete
@@ -473,6 +481,36 @@ bool issue_round(awg_server_t* s, Round* rd) {
   }
   rd->rec.pieces = (int32_t)rd->pieces.size();
   rd->rec.tiles = (int32_t)n_items;
+  // the split sums' scratch: piece i's partial tiles and tile counters after those of pieces < i
+  size_t part_need = 0, ctr_need = 0;
+  for (size_t i = 0; i < rd->pieces.size(); ++i) {
+    part_need += (size_t)ra[i].n_tiles * (size_t)ra[i].split * awgk::TILE;
+    ctr_need += (size_t)ra[i].n_tiles;
+  }
+  if (ok && part_need > s->cap_part[set]) {   // the set's previous round is complete
+    const size_t ncap = std::max(part_need, 2 * s->cap_part[set]);
+    float* a = nullptr;
+    if (cudaMalloc((void**)&a, ncap * sizeof(float)) != cudaSuccess) return false;
+    cudaFree(s->d_part[set]);
+    s->d_part[set] = a;
+    s->cap_part[set] = ncap;
+  }
+  if (ok && ctr_need > s->cap_tctr[set]) {
+    const size_t ncap = std::max(ctr_need, 2 * s->cap_tctr[set]);
+    unsigned long long* a = nullptr;
+    if (cudaMalloc((void**)&a, ncap * sizeof(unsigned long long)) != cudaSuccess) return false;
+    cudaFree(s->d_tctr[set]);
+    s->d_tctr[set] = a;
+    s->cap_tctr[set] = ncap;
+  }
+  size_t part_off = 0, ctr_off = 0;
+  for (size_t i = 0; i < rd->pieces.size(); ++i) {
+    ra[i].part = s->d_part[set] + part_off;
+    ra[i].tile_ctr = s->d_tctr[set] + ctr_off;
+    part_off += (size_t)ra[i].n_tiles * (size_t)ra[i].split * awgk::TILE;
+    ctr_off += (size_t)ra[i].n_tiles;
+  }
+  ok = ok && cudaMemsetAsync(s->d_tctr[set], 0, ctr_need * sizeof(unsigned long long), st) == cudaSuccess;
   ok = ok && grow(&s->d_reqs[set], &s->h_reqs[set], &s->cap_reqs[set], rd->pieces.size()) &&
        grow(&s->d_items[set], &s->h_items[set], &s->cap_items[set], n_items);
   if (!ok) return false;
@@ -490,8 +528,8 @@ bool issue_round(awg_server_t* s, Round* rd) {
     size_t e = b, items = 0;
     while (e < rd->pieces.size() && rd->pieces[e].r->split == rd->pieces[b].r->split)
       items += (size_t)ra[e++].n_tiles;
-    ok = awgk::launch_render_batch(s->d_reqs[set], s->d_items[set] + item0, (int)items, rd->pieces[b].r->split,
-                                   st) == cudaSuccess;
+    ok = awgk::launch_render_batch_split(s->d_reqs[set], s->d_items[set] + item0, (int)items,
+                                         rd->pieces[b].r->split, st) == cudaSuccess;
     item0 += items;
     b = e;
   }
@@ -729,11 +767,14 @@ awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes,
     if (!grow(&s->d_reqs[i], &s->h_reqs[i], &s->cap_reqs[i], 1024) ||
         !grow(&s->d_items[i], &s->h_items[i], &s->cap_items[i], 1 << 16) ||
         cudaMalloc((void**)&s->d_arena[i], (1u << 16) * sizeof(awgk::TileRec)) != cudaSuccess ||
-        cudaMalloc((void**)&s->d_act[i], (1u << 16) * sizeof(int32_t)) != cudaSuccess) {
+        cudaMalloc((void**)&s->d_act[i], (1u << 16) * sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc((void**)&s->d_part[i], (size_t)PART_TILES * awgk::TILE * sizeof(float)) != cudaSuccess ||
+        cudaMalloc((void**)&s->d_tctr[i], (1u << 16) * sizeof(unsigned long long)) != cudaSuccess) {
       e = cudaErrorMemoryAllocation;
       break;
     }
-    s->cap_arena[i] = s->cap_act[i] = 1u << 16;
+    s->cap_arena[i] = s->cap_act[i] = s->cap_tctr[i] = 1u << 16;
+    s->cap_part[i] = (size_t)PART_TILES * awgk::TILE;
   }
   if (e != cudaSuccess) awgk::set_error(AWG_ENOMEM, "staging buffers");
   if (e != cudaSuccess || calibrate(s) != AWG_OK) {
@@ -766,6 +807,8 @@ void awg_server_destroy(awg_server_t* s) {
   for (int i = 0; i < NSETS; ++i) {
     cudaFree(s->d_arena[i]);
     cudaFree(s->d_act[i]);
+    cudaFree(s->d_part[i]);
+    cudaFree(s->d_tctr[i]);
     cudaFree(s->d_reqs[i]);
     cudaFree(s->d_items[i]);
     cudaFreeHost(s->h_reqs[i]);
