@@ -228,7 +228,7 @@ int awg_render_multiplexed(awg_t* const* handles, int32_t n_channels, int64_t n,
 /* Render n_chunks consecutive chunks of `chunk` samples (the chunk loop of Sec. IV: the cursor
  * advances chunk by chunk) into out[0 .. n_chunks * chunk), with the same samples as n_chunks
  * calls of awg_render.  The chunks are issued as one pipelined sequence: the chunks go in groups
- * whose chirp tile records fit a fixed budget (2M records); one set-up launch per group computes
+ * whose chirp tile records fit a fixed budget (4M records); one set-up launch per group computes
  * the records of all its chunks, then the chunk renders follow with programmatic dependent
  * launch, so that each render starts while the one before drains; a join kernel (a bounded wait
  * on a device counter of finished render CTAs) ends each group and restores plain stream order

@@ -1045,7 +1045,7 @@ std::vector<int32_t> active_slots(const awg_t* h, int64_t c, int64_t n, int64_t*
 // (stream order, then a bounded wait on a device counter of render CTAs that stored their
 // samples) ends each group, so the next group's set-up and later work on the stream see every
 // chunk complete.
-constexpr size_t SEQ_RECORD_BUDGET = (size_t)1 << 21;   // 2M records (352 MiB) per group
+constexpr size_t SEQ_RECORD_BUDGET = (size_t)1 << 22;   // 4M records (704 MiB) per group
 
 int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, cudaStream_t s, int64_t tail = 0) {
   // chunks 0 .. n_chunks - 1 of `chunk` samples, then (tail > 0) one of `tail` samples
