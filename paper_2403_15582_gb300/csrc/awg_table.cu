@@ -159,12 +159,12 @@ __device__ __forceinline__ float2 unpack2<__half>(uint32_t u) {
 // 4 (j mod 4) of 16-byte chunk j / 4 of the row, which the 128-byte swizzle moves to chunk
 // (j / 4) ^ (row mod 8).  The sine and cosine take the top 32 bits of the phase word as a signed
 // turn on the SFU (|error| < 5e-7).
-template <typename T>
+template <typename T, bool WINDOW>
 __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint32_t row0, int g, int lane,
                                            uint32_t tile_hi, uint32_t tile_lo) {
   // table mode: lane j = tone kt0 + j (one (sin, cos) pair per tone); static engine: lane j = tone
   // kt0 / 2 + j / 2, segment j % 2 (two pairs per tone), zero in tiles where it is not static
-  const int k = a.window_mode ? (kt0 >> 1) + (lane >> 1) : kt0 + lane;
+  const int k = WINDOW ? (kt0 >> 1) + (lane >> 1) : kt0 + lane;
   const int seg = lane & 1;
   uint64_t w = 0, step = 0;
   float amp = 0.f;
@@ -175,7 +175,7 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
   if (k < a.K) {
     uint64_t phi, F;
     float A;
-    if (a.window_mode) {
+    if (WINDOW) {
       const ToneRec& t = a.tones[k];
       phi = seg ? t.phi_post_ref : t.phi_ref;
       F = seg ? t.F_end : t.F;
@@ -212,7 +212,7 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
     float sn, cs;
     __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
     float a_row = amp;
-    if (a.window_mode) {   // the row's tile decides whether this segment is summed here
+    if (WINDOW) {   // the row's tile decides whether this segment is summed here
       const int64_t T0 = ((a.row_base + (int64_t)row0 + (int64_t)r) << a.nb_log2) & ~(int64_t)(TILE - 1);
       const bool in_seg = T0 >= seg_lo && T0 <= seg_hi;
       const bool ramping = T0 >= ramp_lo && T0 <= ramp_hi;
@@ -229,7 +229,7 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
   }
 }
 
-template <typename T>
+template <typename T, bool WINDOW>
 __global__ void __launch_bounds__(192, 1)
     table_gemm_kernel(const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
                       const __grid_constant__ TableGemmArgs a) {
@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(192, 1)
         }
         if (s_fail) break;
         const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
-        gen_a_tile<T>(a, (kb0 + kb) * (TK / 2), (uint32_t)row0, g, lane, st, st + A_TILE);
+        gen_a_tile<T, WINDOW>(a, (kb0 + kb) * (TK / 2), (uint32_t)row0, g, lane, st, st + A_TILE);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full0 + 8 * s) : "memory");
@@ -518,7 +518,10 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   ga.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
   const size_t smem = (size_t)NSTAGE * STAGE_BYTES + 1024;
   static_assert((size_t)TM * PART_STRIDE * 4 <= (size_t)NSTAGE * STAGE_BYTES, "partial tile fits in the stages");
-  auto kern = bf16 ? table_gemm_kernel<__nv_bfloat16> : table_gemm_kernel<__half>;
+  // the static engine's window mode is a separate instantiation, so that the table keeps its lean
+  // A-operand generator
+  auto kern = t.window_mode ? (bf16 ? table_gemm_kernel<__nv_bfloat16, true> : table_gemm_kernel<__half, true>)
+                            : (bf16 ? table_gemm_kernel<__nv_bfloat16, false> : table_gemm_kernel<__half, false>);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   // K split over a cluster of up to 4 CTAs per 128-row tile
