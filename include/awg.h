@@ -181,9 +181,10 @@ int32_t awg_sine_mode(const awg_t* h);
  * on the tensor cores by the table GEMM of awg_table_gemm, over 256-sample rows aligned to
  * absolute sample indices (x[256 r + c] = sum_k [A_k sin a_k(r)] cos b_k(c) + [A_k cos a_k(r)]
  * sin b_k(c) from exact phase words, split-precision operands, FP32 accumulation; two column
- * pairs per tone, one per segment); the remaining tones go through the render kernel, which adds
- * the GEMM's FP32 sum before quantising.  Within one engine a sample's value
- * does not depend on how the stream is cut into calls.  Output stays within 1 LSB of the oracle;
+ * pairs per tone, one per segment, or one pair while no tone of the handle has ever held a chirp
+ * or a ramp); the remaining tones go through the render kernel, which adds the GEMM's FP32 sum
+ * before quantising.  Within one engine, and between calls that set tones, chirps or ramps, a
+ * sample's value does not depend on how the stream is cut into calls.  Output stays within 1 LSB of the oracle;
  * it is not bit-identical to the direct engine.  awg_render_chunks renders chunk by chunk with a
  * GEMM engine; awg_render_noalloc always uses the direct engine.  AWG_EINVAL for other values. */
 enum { AWG_STATIC_DIRECT = 0, AWG_STATIC_GEMM_FP16 = 1, AWG_STATIC_GEMM_BF16 = 2 };
