@@ -524,10 +524,44 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
                             : (bf16 ? table_gemm_kernel<__nv_bfloat16, false> : table_gemm_kernel<__half, false>);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // K split over a cluster of up to 4 CTAs per 128-row tile
-  const unsigned split = (unsigned)(ga.n_kb < 4 ? ga.n_kb : 4);
+  // K split over a cluster of 1, 2 or 4 CTAs per 128-row tile, whichever finishes first by a
+  // simple model: waves of co-resident clusters (a cluster of 4 leaves SMs of some GPCs idle: 36
+  // clusters = 144 CTAs at once on 152 SMs, against 76 clusters of 2) times the K blocks per CTA
+  // plus an epilogue worth about 8 K blocks
+  const int64_t tiles = (M + TM - 1) / TM;
+  static int active[5] = {0, 0, 0, 0, 0};
+  unsigned split = 1;
+  double best = 1e300;
+  for (unsigned c = 1; c <= 4; c *= 2) {
+    if ((int)c > ga.n_kb) break;
+    if (!active[c]) {
+      cudaLaunchConfig_t q = {};
+      q.gridDim = dim3(c, 1, 1);
+      q.blockDim = dim3(192, 1, 1);
+      q.dynamicSmemBytes = smem;
+      cudaLaunchAttribute qa[1];
+      qa[0].id = cudaLaunchAttributeClusterDimension;
+      qa[0].val.clusterDim.x = c;
+      qa[0].val.clusterDim.y = 1;
+      qa[0].val.clusterDim.z = 1;
+      q.attrs = qa;
+      q.numAttrs = 1;
+      int n = 0;
+      if (cudaOccupancyMaxActiveClusters(&n, (const void*)kern, &q) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+      }
+      active[c] = n;
+    }
+    const double waves = (double)((tiles + active[c] - 1) / active[c]);
+    const double t = waves * ((double)ga.n_kb / c + 8.0);
+    if (t < best) {
+      best = t;
+      split = c;
+    }
+  }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)((M + TM - 1) / TM) * split, 1, 1);
+  cfg.gridDim = dim3((unsigned)tiles * split, 1, 1);
   cfg.blockDim = dim3(192, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
