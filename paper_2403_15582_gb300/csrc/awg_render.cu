@@ -975,10 +975,20 @@ __global__ void replay_kernel(const int16_t* __restrict__ tab, uint64_t mask, in
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   int64_t done = 0;
   if (vec) {
+    // four 16-byte vectors in flight per thread; streaming stores keep the table resident in L2
     const int64_t nv = n / 8;
-    for (int64_t v = t0; v < nv; v += step) {
-      const uint64_t src = ((uint64_t)c + (uint64_t)v * 8u) & mask;
-      reinterpret_cast<uint4*>(out)[v] = *reinterpret_cast<const uint4*>(tab + src);
+    for (int64_t v0 = t0; v0 < nv; v0 += 4 * step) {
+      uint4 x[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t v = v0 + j * step;
+        if (v < nv) x[j] = __ldg(reinterpret_cast<const uint4*>(tab + (((uint64_t)c + (uint64_t)v * 8u) & mask)));
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t v = v0 + j * step;
+        if (v < nv) __stcs(reinterpret_cast<uint4*>(out) + v, x[j]);
+      }
     }
     done = nv * 8;
   }
