@@ -7,6 +7,9 @@
 #include <cstdint>
 #include <cstring>
 #include <string>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -510,6 +513,78 @@ int ensure(T** ptr, size_t* cap, size_t need, awg_t* h, const char* what) {
   *cap = ncap;
   return AWG_OK;
 }
+
+// Host worker threads for the set-up arithmetic of large chirp batches, started once per process
+// (starting threads per call cost more than the work at 1000 chirps).  parallel_for(n, fn) runs
+// fn(lo, hi) over [0, n) in `parts` ranges, one on the calling thread, and returns when all are
+// done.  Calls are serialised.
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool pool;
+    return pool;
+  }
+  size_t threads() const { return workers_.size() + 1; }
+  void parallel_for(size_t n, size_t parts, const std::function<void(size_t, size_t)>& fn) {
+    parts = std::max<size_t>(1, std::min(parts, threads()));
+    if (parts == 1) {
+      fn(0, n);
+      return;
+    }
+    std::lock_guard<std::mutex> call(call_mu_);
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      fn_ = &fn;
+      n_ = n;
+      parts_ = parts;
+      next_ = 1;
+      pending_ = parts - 1;
+      ++gen_;
+    }
+    cv_.notify_all();
+    fn(0, n / parts);   // part 0 here
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return pending_ == 0; });
+    fn_ = nullptr;
+  }
+  ~HostPool() {
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (std::thread& t : workers_) t.join();
+  }
+
+ private:
+  HostPool() {
+    const size_t n = std::min<size_t>(7, std::max(1u, std::thread::hardware_concurrency()) - 1);
+    for (size_t i = 0; i < n; ++i) workers_.emplace_back([this] { run(); });
+  }
+  void run() {
+    uint64_t seen = 0;
+    for (;;) {
+      std::unique_lock<std::mutex> lk(mu_);
+      cv_.wait(lk, [&] { return stop_ || (gen_ != seen && next_ < parts_); });
+      if (stop_) return;
+      const size_t part = next_++;
+      if (next_ >= parts_) seen = gen_;
+      const std::function<void(size_t, size_t)>* fn = fn_;
+      const size_t n = n_, parts = parts_;
+      lk.unlock();
+      (*fn)(n * part / parts, n * (part + 1) / parts);
+      lk.lock();
+      if (--pending_ == 0) done_cv_.notify_all();
+    }
+  }
+  std::vector<std::thread> workers_;
+  std::mutex mu_, call_mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(size_t, size_t)>* fn_ = nullptr;
+  size_t n_ = 0, parts_ = 0, next_ = 0, pending_ = 0;
+  uint64_t gen_ = 0;
+  bool stop_ = false;
+};
 
 // Scratch for launches of up to `tiles` tiles with tone split `split` (> 1): two buffers of
 // part_tiles x part_split partial tiles (capacities) and part_tiles tile counters each.  The
@@ -1337,15 +1412,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
       co[i].exact = needs_exact(p.F0, p.F1, p.L, p.profile);
     }
   };
-  const size_t n_threads = std::min<size_t>({8, std::max(1u, std::thread::hardware_concurrency()), pend.size() / 64 + 1});
-  if (n_threads <= 1) {
-    work(0, pend.size());
-  } else {
-    std::vector<std::thread> pool;
-    for (size_t t = 0; t < n_threads; ++t)
-      pool.emplace_back(work, pend.size() * t / n_threads, pend.size() * (t + 1) / n_threads);
-    for (std::thread& th : pool) th.join();
-  }
+  HostPool::get().parallel_for(pend.size(), pend.size() / 64 + 1, work);
   std::vector<int32_t> changed_tones, changed_slots;
   for (size_t pi = 0; pi < pend.size(); ++pi) {
     const Pending& p = pend[pi];
