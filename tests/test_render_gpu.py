@@ -416,3 +416,47 @@ def test_maximum_sizes(awg, oracle):
     got = big[torch.as_tensor(idx2, device="cuda")].cpu().numpy().astype(np.int32)
     assert np.max(np.abs(got - q2)) <= 1
     del big
+
+
+def test_split_sums_across_launches(awg, oracle):
+    """A window of more than 512 tiles with a tone split of 16 goes out in several render launches
+    chained by programmatic dependent launch on alternating scratch buffers: the same samples as
+    chunk-by-chunk and pipelined rendering, bit for bit, and within 1 LSB of the oracle."""
+    rng = np.random.default_rng(91)
+    fs, K = 280e6, 1600
+    f = rng.uniform(1e6, 139e6, K)
+    a = rng.uniform(0.2, 1.0, K) / K
+    th = rng.uniform(0, 2 * np.pi, K)
+    chirps = [dict(tone=int(t), f_start=float(f[t]), f_end=float(rng.uniform(1e6, 139e6)),
+                   duration=float(rng.uniform(1e-3, 8e-3)), profile=int(t % 3), start_sample=int(rng.integers(0, 2_000_000)))
+              for t in rng.choice(K, 300, replace=False)]
+
+    def make():
+        s = awg.Synth(fs)
+        s.set_tones(f, a, th)
+        s.set_chirp_list(chirps)
+        return s
+
+    n = 1200 * 4096 + 777              # 1201 tiles: three launches of at most 512
+    s = make()
+    assert s.tone_split == 16
+    one = torch.empty(n, dtype=torch.int16, device="cuda")
+    x = torch.empty(n, dtype=torch.float32, device="cuda")
+    s.render_f32(n, x, one)
+    s2 = make()
+    cut = torch.empty(n, dtype=torch.int16, device="cuda")
+    c = 0
+    for piece in (100_001, 3 * 1 << 20, 4096):
+        s2.render(piece, cut[c:])
+        c += piece
+    s2.render_stream(n - c, 1 << 18, cut[c:])
+    torch.cuda.synchronize()
+    assert s.device_status() == 0 and s2.device_status() == 0
+    q1 = one.cpu().numpy()
+    assert np.array_equal(q1, cut.cpu().numpy())
+    w = oracle.make_waveform(fs, f, a, th, chirps)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 300), [0, 512 * 4096 - 1, 512 * 4096, 1024 * 4096, n - 1]]))
+    x_ref = oracle.render_at(w, idx, nthreads=NTHREADS)
+    assert np.max(np.abs(x.cpu().numpy()[idx].astype(np.float64) - x_ref)) <= fp32_bound(a, 16)
+    q_ref = oracle.quantize(x_ref, w.full_scale())
+    assert np.max(np.abs(q1[idx].astype(np.int32) - q_ref)) <= 1
