@@ -348,6 +348,25 @@ uint64_t chirp_offset_word(const W192 d[7], int64_t m) {
 
 // Chirps whose neglected 4th..6th-order phase terms over one 32-sample run could exceed 512 units
 // of 2^-32 turn (1.2e-7 turn) are rendered from a per-sample table of exact phases instead.
+// Whether the third unit difference of the chirp phase stays below 2^30 words over the whole
+// chirp, so that the render's run cascade rounds h to 0 in every run (TONE_FLAT3): by the mean
+// value theorem |Delta^3 P| <= max |P'''|, which is 5.77 |D| / L^2 for the minimum-jerk profile
+// (60 max |t - 3 t^2 + 2 t^3| = 5.77 over t in [0, 1]) and F_max |e^alpha - 1|^3 (1 + |e^alpha - 1|)
+// for the exponential one; linear chirps take their own path.
+bool flat_third_difference(uint64_t F0, uint64_t F1, int64_t L, int profile) {
+  const double l = (double)L;
+  double bound;
+  if (profile == AWG_PROFILE_MINJERK) {
+    bound = 6.0 * std::fabs((double)F1 - (double)F0) / (l * l);
+  } else if (profile == AWG_PROFILE_EXPONENTIAL && F0 != F1) {
+    const double q = std::fabs(exp_params(F0, F1, L).q);
+    bound = (double)std::max(F0, F1) * q * q * q * (1.0 + q) * 1.01;
+  } else {
+    return false;
+  }
+  return bound < 1073741824.0;   // 2^30
+}
+
 // Phase offset at the end of an exponential chirp, R(L), the same FP64 formula as the render's.
 uint64_t exp_end_offset(uint64_t F0, uint64_t F1, int64_t L) {
   const ExpParams e = exp_params(F0, F1, L);
@@ -1400,7 +1419,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   struct Coeffs {
     W192 d[7];
     uint64_t end_offset;
-    bool exact;
+    bool exact, flat3;
   };
   std::vector<Coeffs> co(pend.size());
   auto work = [&](size_t lo, size_t hi) {
@@ -1410,6 +1429,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
       co[i].end_offset = p.profile == AWG_PROFILE_EXPONENTIAL ? exp_end_offset(p.F0, p.F1, p.L)
                                                                : chirp_offset_word(co[i].d, p.L);
       co[i].exact = needs_exact(p.F0, p.F1, p.L, p.profile);
+      co[i].flat3 = flat_third_difference(p.F0, p.F1, p.L, p.profile);
     }
   };
   HostPool::get().parallel_for(pend.size(), pend.size() / 64 + 1, work);
@@ -1446,7 +1466,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     c.L = p.L;
     c.tone = p.tone;
     c.flags = (co[pi].exact ? awgk::TONE_EXACT : 0) | (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0) |
-              (p.profile == AWG_PROFILE_EXPONENTIAL ? awgk::TONE_EXP : 0);
+              (p.profile == AWG_PROFILE_EXPONENTIAL ? awgk::TONE_EXP : 0) | (co[pi].flat3 ? awgk::TONE_FLAT3 : 0);
     const uint64_t phi_end = c.phi_start + co[pi].end_offset;
     t.slot = slot;
     t.n_s = p.ns;

@@ -46,6 +46,8 @@ constexpr int32_t TONE_EXACT = 1;    // chirp read from a per-sample table of ex
 constexpr int32_t TONE_LINEAR = 2;   // linear chirp: differences of order >= 3 are exactly zero
 constexpr int32_t TONE_AMP_RAMP = 4;      // the amplitude ramps (see ToneRec::a_ns)
 constexpr int32_t TONE_AMP_MINJERK = 8;   // ... along the minimum-jerk profile (else linear)
+constexpr int32_t TONE_FLAT3 = 32;        // the chirp's third unit difference stays below 2^30 words:
+                                          // the run cascade's h rounds to 0 in every run
 constexpr int32_t TONE_EXP = 16;          // exponential chirp: ChirpRec::d[0..4] hold F_start, F_end
                                           // and the doubles alpha, C, e^alpha - 1 (bit patterns)
 

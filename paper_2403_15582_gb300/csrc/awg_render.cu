@@ -205,6 +205,18 @@ __device__ __forceinline__ RunPoly poly_state(const TileRec& rc, const RunBin& b
   return pack_run(p, f, g, h);
 }
 
+// poly_state for a degree-6 chirp whose h is known to round to 0 (TONE_FLAT3): no H polynomial.
+__device__ __forceinline__ RunPoly poly_state_flat3(const TileRec& rc, const RunBin& b) {
+  uint64_t p = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.B[0], rc.B[1], b.c1), rc.B[2], b.c2), rc.B[3], b.c3), rc.B[4], b.c4),
+                       rc.B[5], b.c5) + rc.B[6] * b.c6;
+  asm volatile("" ::: "memory");
+  uint64_t f = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.E[0], rc.E[1], b.c1), rc.E[2], b.c2), rc.E[3], b.c3), rc.E[4], b.c4),
+                       rc.E[5], b.c5);
+  asm volatile("" ::: "memory");
+  uint64_t g = mac_u32(mac_u32(mac_u32(mac_u32(rc.G[0], rc.G[1], b.c1), rc.G[2], b.c2), rc.G[3], b.c3), rc.G[4], b.c4);
+  return pack_run(p, f, g, 0);
+}
+
 __device__ __forceinline__ RunPoly pack_run(uint64_t p, uint64_t f, uint64_t g, uint64_t h) {
   RunPoly r;
   r.p = (uint32_t)((p + P_OFFSET) >> 32);
@@ -556,7 +568,8 @@ struct alignas(16) Desc {
   int32_t kind;
   float c, s;     // DESC_STATIC_ROT: cos and sin of the per-sample phase step
 };
-enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_STATIC_ROT = 4, DESC_SKIP = 5 };
+enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_STATIC_ROT = 4, DESC_SKIP = 5,
+       DESC_FLAT3 = 6 };   // FLAT3: a degree-6 chirp whose h is 0 in every run (TONE_FLAT3)
 
 
 // Scale, round half to even, clamp and store sample T0 + sidx of a tile (inside the window),
@@ -717,7 +730,9 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
         d.F = 0;
         d.p0 = 0;
         const bool inside = T0 >= tr.n_s && T0 + TILE - 1 <= tr.n_e;
-        d.kind = (inside && !exact) ? ((tr.flags & TONE_LINEAR) ? DESC_LINEAR : DESC_MINJERK) : DESC_MIXED;
+        d.kind = (inside && !exact)
+                     ? ((tr.flags & TONE_LINEAR) ? DESC_LINEAR : (tr.flags & TONE_FLAT3) ? DESC_FLAT3 : DESC_MINJERK)
+                     : DESC_MIXED;
         if (!exact) {
           need = true;
           src = a.recs + (int64_t)a.act_of_slot[tr.slot] * (a.rec_stride ? a.rec_stride : a.n_tiles) + a.rec_tile0 + tile;
@@ -793,6 +808,17 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
           }
         } else if (kind == DESC_LINEAR) {
           const RunPoly q = poly_state(s_rec[b][i], rb, true);
+          uint32_t p = q.p + HALF_TURN, f = q.f;
+          const uint32_t g = q.g;
+#pragma unroll
+          for (int r = 0; r < RUN; ++r) {
+            acc[r] = fmaf(A, sin_centred(p), acc[r]);
+            p += f;
+            f += g;
+          }
+        } else if (kind == DESC_FLAT3) {
+          // the third difference rounds to 0 everywhere (set-up bound): g is constant over the run
+          const RunPoly q = poly_state_flat3(s_rec[b][i], rb);
           uint32_t p = q.p + HALF_TURN, f = q.f;
           const uint32_t g = q.g;
 #pragma unroll
