@@ -478,14 +478,34 @@ __global__ void __launch_bounds__(128) prep_kernel(const __grid_constant__ PrepA
 // Per (tone, run) contribution of one staged tone, added into the thread's RUN partial sums.
 // Amplitude a(n) of a ramping tone (TONE_AMP_RAMP): A before a_ns, A_end from a_ns + a_L on, and
 // A + (A_end - A) s(tau) between, tau = (n - a_ns) / a_L, s linear or minimum-jerk
-// (10 tau^3 - 15 tau^4 + 6 tau^5).  FP32; error <= 6e-7 |A_end - A|.
-__device__ float ramp_amp(const ToneRec& t, int64_t n) {
-  if (n <= t.a_ns) return t.A;
-  const int64_t m = n - t.a_ns;
-  if (m >= t.a_L) return t.A_end;
-  const float tau = (float)m / (float)t.a_L;
-  const float s = (t.flags & TONE_AMP_MINJERK) ? tau * tau * tau * fmaf(tau, fmaf(6.f, tau, -15.f), 10.f) : tau;
-  return fmaf(t.A_end - t.A, s, t.A);
+// (10 tau^3 - 15 tau^4 + 6 tau^5).  FP32 (tau as m times the rounded 1 / a_L); error
+// <= 6e-7 |A_end - A|.
+// Per run: the offset of the run start into the ramp and 1 / a_L; ramp_amp_at(rr, r) is a(n0 + r),
+// with tau = m (1 / a_L) in FP32 (a function of the absolute sample only, whatever the window).
+struct RampRun {
+  int64_t m0;       // n0 - a_ns
+  int64_t L;
+  float inv_L, A, A_end, dA;
+  bool minjerk;
+};
+__device__ __forceinline__ RampRun ramp_run_setup(const ToneRec& t, int64_t n0) {
+  RampRun rr;
+  rr.m0 = n0 - t.a_ns;
+  rr.L = t.a_L;
+  rr.inv_L = 1.0f / (float)t.a_L;
+  rr.A = t.A;
+  rr.A_end = t.A_end;
+  rr.dA = t.A_end - t.A;
+  rr.minjerk = (t.flags & TONE_AMP_MINJERK) != 0;
+  return rr;
+}
+__device__ __forceinline__ float ramp_amp_at(const RampRun& rr, int r) {
+  const int64_t m = rr.m0 + r;
+  if (m <= 0) return rr.A;
+  if (m >= rr.L) return rr.A_end;
+  const float tau = (float)m * rr.inv_L;
+  const float s = rr.minjerk ? tau * tau * tau * fmaf(tau, fmaf(6.f, tau, -15.f), 10.f) : tau;
+  return fmaf(rr.dA, s, rr.A);
 }
 
 __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, const RunBin& rb, float* col,
@@ -495,9 +515,7 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
   const float A = (ramp && n0 >= tr.a_ns + tr.a_L) ? tr.A_end : tr.A;
   const int tcls = classify_tile(tr, T0);
   int mode;   // 0 static before the chirp, 1 static after, 2 chirp polynomial, 3 general
-  if (ramp_run) {
-    mode = 3;
-  } else if (tcls == TILE_PRE) {
+  if (tcls == TILE_PRE) {
     mode = 0;
   } else if (tcls == TILE_POST) {
     mode = 1;
@@ -508,7 +526,24 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
     else if (n0 >= tr.n_s && last <= tr.n_e && !(tr.flags & TONE_EXACT)) mode = 2;
     else mode = 3;
   }
-  if (mode <= 1) {
+  if (ramp_run && mode <= 1) {
+    // a ramp on a static segment: stepped phase, the amplitude of ramp_amp per sample
+    const uint64_t phi = mode == 0 ? tr.phi_ref : tr.phi_post_ref;
+    const uint64_t F = mode == 0 ? tr.F : tr.F_end;
+    uint32_t p = static_p0(phi, F, n0) + HALF_TURN;
+    const uint32_t f = static_f(F);
+    const RampRun rr = ramp_run_setup(tr, n0);
+#pragma unroll
+    for (int r = 0; r < RUN; ++r) {
+      acc[r] = fmaf(ramp_amp_at(rr, r), sin_centred(p), acc[r]);
+      p += f;
+    }
+  } else if (ramp_run) {
+    mode = 3;
+  }
+  if (ramp_run) {
+    if (mode <= 1) return;
+  } else if (mode <= 1) {
     const uint64_t phi = mode == 0 ? tr.phi_ref : tr.phi_post_ref;
     const uint64_t F = mode == 0 ? tr.F : tr.F_end;
     uint32_t p = static_p0(phi, F, n0) + HALF_TURN;
@@ -518,7 +553,9 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
       acc[r] = fmaf(A, sin_centred(p), acc[r]);
       p += f;
     }
-  } else if (mode == 2) {
+    return;
+  }
+  if (mode == 2) {
     const RunPoly st = poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0);
     uint32_t p = st.p + HALF_TURN, f = st.f, g = st.g;
     const uint32_t h = st.h;
@@ -550,8 +587,9 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
       gg += st.h;
     }
     if (ramp_run) {
+      const RampRun rr = ramp_run_setup(tr, n0);
 #pragma unroll
-      for (int r = 0; r < RUN; ++r) acc[r] = fmaf(ramp_amp(tr, n0 + r), col[r * NT], acc[r]);
+      for (int r = 0; r < RUN; ++r) acc[r] = fmaf(ramp_amp_at(rr, r), col[r * NT], acc[r]);
     } else {
 #pragma unroll
       for (int r = 0; r < RUN; ++r) acc[r] = fmaf(A, col[r * NT], acc[r]);
@@ -872,51 +910,51 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     __syncthreads();
   }
 
-  if (!CLUSTER) {
+  if constexpr (!CLUSTER) {
     tile_epilogue_split(a, tile, crank, split, T0, acc);
-    return;
-  }
-  // partial sums -> shared memory ([r][thread]), then the cluster-wide sum in rank order
+  } else {
+    // partial sums -> shared memory ([r][thread]), then the cluster-wide sum in rank order
 #pragma unroll
-  for (int r = 0; r < RUN; ++r) s_red[r * NT + tid] = acc[r];
-  cluster.sync();
+    for (int r = 0; r < RUN; ++r) s_red[r * NT + tid] = acc[r];
+    cluster.sync();
 
-  // this CTA reduces and stores samples [lo, hi) of the tile; thread t takes `per` consecutive ones
-  const int lo = (int)((int64_t)TILE * crank / split), hi = (int)((int64_t)TILE * (crank + 1) / split);
-  const int per = (hi - lo + NT - 1) / NT;
-  const int s_first = lo + tid * per;
-  float xs[RUN];
+    // this CTA reduces and stores samples [lo, hi) of the tile; thread t takes `per` consecutive ones
+    const int lo = (int)((int64_t)TILE * crank / split), hi = (int)((int64_t)TILE * (crank + 1) / split);
+    const int per = (hi - lo + NT - 1) / NT;
+    const int s_first = lo + tid * per;
+    float xs[RUN];
 #pragma unroll
-  for (int u = 0; u < RUN; ++u) xs[u] = 0.f;
-  for (int c = 0; c < split; ++c) {
-    const float* rem = cluster.map_shared_rank(s_red, c);
+    for (int u = 0; u < RUN; ++u) xs[u] = 0.f;
+    for (int c = 0; c < split; ++c) {
+      const float* rem = cluster.map_shared_rank(s_red, c);
+#pragma unroll
+      for (int u = 0; u < RUN; ++u) {
+        const int sidx = s_first + u;
+        if (u < per && sidx < hi) xs[u] += rem[(sidx % RUN) * NT + sidx / RUN];
+      }
+    }
+    cluster.sync();   // remote reads done before any CTA of the cluster exits
+
+    // scale, round half to even, clamp, store the window part
 #pragma unroll
     for (int u = 0; u < RUN; ++u) {
       const int sidx = s_first + u;
-      if (u < per && sidx < hi) xs[u] += rem[(sidx % RUN) * NT + sidx / RUN];
-    }
-  }
-  cluster.sync();   // remote reads done before any CTA of the cluster exits
-
-  // scale, round half to even, clamp, store the window part
-#pragma unroll
-  for (int u = 0; u < RUN; ++u) {
-    const int sidx = s_first + u;
-    if (u < per && sidx < hi) {
-      const int64_t n = T0 + sidx;
-      if (n >= a.win_start && n < a.win_end) {
-        if (a.base) xs[u] += a.base[n - a.win_start];
-        float q = rintf(xs[u] * a.scale);
-        q = fminf(fmaxf(q, -32767.f), 32767.f);
-        if (a.out_q) a.out_q[(n - a.win_start) * (a.q_stride ? a.q_stride : 1)] = (int16_t)q;
-        if (a.out_f) a.out_f[n - a.win_start] = xs[u];
+      if (u < per && sidx < hi) {
+        const int64_t n = T0 + sidx;
+        if (n >= a.win_start && n < a.win_end) {
+          if (a.base) xs[u] += a.base[n - a.win_start];
+          float q = rintf(xs[u] * a.scale);
+          q = fminf(fmaxf(q, -32767.f), 32767.f);
+          if (a.out_q) a.out_q[(n - a.win_start) * (a.q_stride ? a.q_stride : 1)] = (int16_t)q;
+          if (a.out_f) a.out_f[n - a.win_start] = xs[u];
+        }
       }
     }
-  }
-  if (a.exit_ctr) {   // this CTA's samples are stored and visible
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) atomicAdd(a.exit_ctr, 1ull);
+    if (a.exit_ctr) {   // this CTA's samples are stored and visible
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) atomicAdd(a.exit_ctr, 1ull);
+    }
   }
 }
 
