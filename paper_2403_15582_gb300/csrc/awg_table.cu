@@ -229,6 +229,32 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
   }
 }
 
+// Table mode with the lane's tone words already loaded (phi, F, A; zero amplitude past K): the
+// same rows as gen_a_tile<T, false>.
+template <typename T>
+__device__ __forceinline__ void gen_a_rows(const TableGemmArgs& a, uint64_t phi, uint64_t F, float A, uint32_t row0,
+                                           int g, int lane, uint32_t tile_hi, uint32_t tile_lo) {
+  const uint64_t f8 = F << a.nb_log2;
+  uint64_t w = phi + (uint64_t)(a.row_base + (int64_t)row0 + g) * f8;
+  const uint64_t step = f8 << 2;
+  const uint32_t col = (uint32_t)(lane & 3) * 4u;
+  const uint32_t chunk = (uint32_t)(lane >> 2);
+#pragma unroll 8
+  for (int i = 0; i < TM / 4; ++i) {
+    const uint32_t r = (uint32_t)(g + 4 * i);
+    float sn, cs;
+    __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
+    const float sv = A * sn, cv = A * cs;
+    const uint32_t hv = pack2<T>(sv, cv);
+    const float2 h = unpack2<T>(hv);
+    const uint32_t lv = pack2<T>(sv - h.x, cv - h.y);
+    const uint32_t off = r * 128u + ((chunk ^ (r & 7u)) << 4) + col;
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(tile_hi + off), "r"(hv) : "memory");
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(tile_lo + off), "r"(lv) : "memory");
+    w += step;
+  }
+}
+
 template <typename T, bool WINDOW>
 __global__ void __launch_bounds__(192, 1)
     table_gemm_kernel(const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
@@ -321,13 +347,26 @@ __global__ void __launch_bounds__(192, 1)
       const int g = warp - 2;   // rows g, g + 4, ...
       for (int kb = 0; kb < n_kb; ++kb) {
         const int s = kb % NSTAGE;
+        // table mode: this k-block's tone words are loaded before the wait for the stage, so
+        // their latency hides under it
+        uint64_t phi = 0, F = 0;
+        float A = 0.f;
+        if (!WINDOW) {
+          const int k = (kb0 + kb) * (TK / 2) + lane;
+          if (k < a.K) {
+            phi = __ldg(&a.tones[k].phi_ref);
+            F = __ldg(&a.tones[k].F);
+            A = __ldg(&a.tones[k].A);
+          }
+        }
         if (kb >= NSTAGE && !mbar_wait(empty0 + 8 * s, (uint32_t)(((kb / NSTAGE) - 1) & 1))) {
           s_fail = 1;
           break;
         }
         if (s_fail) break;
         const uint32_t st = base + (uint32_t)s * STAGE_BYTES;
-        gen_a_tile<T, WINDOW>(a, (kb0 + kb) * (TK / 2), (uint32_t)row0, g, lane, st, st + A_TILE);
+        if (WINDOW) gen_a_tile<T, true>(a, (kb0 + kb) * (TK / 2), (uint32_t)row0, g, lane, st, st + A_TILE);
+        else gen_a_rows<T>(a, phi, F, A, (uint32_t)row0, g, lane, st, st + A_TILE);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full0 + 8 * s) : "memory");
