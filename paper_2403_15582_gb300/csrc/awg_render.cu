@@ -455,7 +455,7 @@ __device__ bool wait_counter(const unsigned long long* ctr, unsigned long long t
   return true;
 }
 
-__global__ void __launch_bounds__(128) prep_kernel(const __grid_constant__ PrepArgs a) {
+__global__ void __launch_bounds__(128, 5) prep_kernel(const __grid_constant__ PrepArgs a) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)a.n_active * a.n_tiles;
   if (idx >= total) return;
