@@ -577,7 +577,7 @@ class HostPool {
 
  private:
   HostPool() {
-    const size_t n = std::min<size_t>(7, std::max(1u, std::thread::hardware_concurrency()) - 1);
+    const size_t n = std::min<size_t>(15, std::max(1u, std::thread::hardware_concurrency()) - 1);
     for (size_t i = 0; i < n; ++i) workers_.emplace_back([this] { run(); });
   }
   void run() {
@@ -1420,6 +1420,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     W192 d[7];
     uint64_t end_offset;
     bool exact, flat3;
+    float rot_c, rot_s;   // rotator constants of F_end
   };
   std::vector<Coeffs> co(pend.size());
   auto work = [&](size_t lo, size_t hi) {
@@ -1430,9 +1431,10 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
                                                                : chirp_offset_word(co[i].d, p.L);
       co[i].exact = needs_exact(p.F0, p.F1, p.L, p.profile);
       co[i].flat3 = flat_third_difference(p.F0, p.F1, p.L, p.profile);
+      rotation_of(p.F1, &co[i].rot_c, &co[i].rot_s);
     }
   };
-  HostPool::get().parallel_for(pend.size(), pend.size() / 64 + 1, work);
+  HostPool::get().parallel_for(pend.size(), pend.size() / 32 + 1, work);
   std::vector<int32_t> changed_tones, changed_slots;
   for (size_t pi = 0; pi < pend.size(); ++pi) {
     const Pending& p = pend[pi];
@@ -1472,7 +1474,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     t.n_s = p.ns;
     t.n_e = p.ns + p.L;
     t.F_end = p.F1;
-    rotation_of(p.F1, &t.rot_c_end, &t.rot_s_end);
+    t.rot_c_end = co[pi].rot_c;
+    t.rot_s_end = co[pi].rot_s;
     t.phi_post_ref = phi_end - (uint64_t)t.n_e * p.F1;
     t.flags = (t.flags & (awgk::TONE_AMP_RAMP | awgk::TONE_AMP_MINJERK)) | c.flags;
   }
