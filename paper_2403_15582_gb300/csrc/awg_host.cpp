@@ -1004,6 +1004,7 @@ int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
     t.win_start = c;
     t.win_end = c + m;
     t.window_mode = two_segments ? 1 : 0;
+    t.invariant = 1;
     t.precision = h->static_engine == AWG_STATIC_GEMM_FP16 ? AWG_PREC_FP16 : AWG_PREC_BF16;
     t.b_hi = h->d_gemm;
     t.b_lo = h->d_gemm + b_elems;

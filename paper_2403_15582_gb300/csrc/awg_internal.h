@@ -233,6 +233,8 @@ struct TableArgs2 {
   int32_t window_mode;    // 1: static engine: per tone two segments (4 columns), each taken only
                           //    in the 4096-sample tiles where it is static (tile_segment_static)
   int32_t precision;      // 0 BF16, 1 FP16 hi+lo operands
+  int32_t invariant;      // 1: the summation of a sample may not depend on M (static engine: the
+                          //    same samples however the stream is cut)
   void* b_hi;             // 256 x Kp (the A operand is generated inside the GEMM kernel)
   void* b_lo;
   int16_t* out_q;

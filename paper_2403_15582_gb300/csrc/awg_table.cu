@@ -563,7 +563,7 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
                             : (bf16 ? table_gemm_kernel<__nv_bfloat16, false> : table_gemm_kernel<__half, false>);
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  // K split over a cluster of 1, 2 or 4 CTAs per 128-row tile, whichever finishes first by a
+  // K split over a cluster of 1, 2 or 4 CTAs per 128-row tile (periodic tables), whichever finishes first by a
   // simple model: waves of co-resident clusters (a cluster of 4 leaves SMs of some GPCs idle: 36
   // clusters = 144 CTAs at once on 152 SMs, against 76 clusters of 2) times the K blocks per CTA
   // plus an epilogue worth about 8 K blocks
@@ -573,6 +573,9 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   double best = 1e300;
   for (unsigned c = 1; c <= 4; c *= 2) {
     if ((int)c > ga.n_kb) break;
+    // the static engine sums each sample over a K split that must not depend on the window's
+    // length (chunk invariance): always the largest split there
+    if (t.invariant && c < 4 && 4 <= ga.n_kb) continue;
     if (!active[c]) {
       cudaLaunchConfig_t q = {};
       q.gridDim = dim3(c, 1, 1);
@@ -593,9 +596,9 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
       active[c] = n;
     }
     const double waves = (double)((tiles + active[c] - 1) / active[c]);
-    const double t = waves * ((double)ga.n_kb / c + 8.0);
-    if (t < best) {
-      best = t;
+    const double cost = waves * ((double)ga.n_kb / c + 8.0);
+    if (cost < best) {
+      best = cost;
       split = c;
     }
   }

@@ -210,3 +210,39 @@ def test_engine_validation(awg):
     with pytest.raises(awg.AwgError):
         s.set_static_engine(3)
     assert s.static_engine == awg.STATIC_DIRECT
+
+
+@pytest.mark.parametrize("with_ramps", [False, True])
+def test_same_samples_for_long_and_short_calls(awg, with_ramps):
+    """The engine's GEMM sums a sample the same way whatever the length of the call that renders
+    it: one call of 2^21 samples and calls of 2^14 (and a ragged tail) give the same bits, for a
+    static comb (two columns per tone) and with ramps (four)."""
+    rng = np.random.default_rng(17)
+    K = 3000
+    f = rng.uniform(1e6, 139e6, K)
+    a = rng.uniform(0.2, 1.0, K) / K
+    th = rng.uniform(0, 2 * np.pi, K)
+    ramps = [dict(tone=int(t), amp_end=float(rng.uniform(0, 2.0 / K)), duration=float(rng.integers(5000, 100000)) / FS,
+                  profile=int(t % 2), start_sample=int(rng.integers(0, 1_500_000))) for t in rng.choice(K, 40, replace=False)]
+
+    def make():
+        s = awg.Synth(FS)
+        s.set_tones(f, a, th)
+        if with_ramps:
+            s.set_ramp_list(ramps)
+            s.set_full_scale(2.0 * float(np.sum(a)))
+        s.set_static_engine(awg.STATIC_GEMM_FP16)
+        return s
+
+    n = 1 << 21
+    one = torch.empty(n, dtype=torch.int16, device="cuda")
+    make().render(n, one)
+    s = make()
+    cut = torch.empty(n, dtype=torch.int16, device="cuda")
+    c = 0
+    while c < n:
+        m = min(1 << 14, n - c) if c < n - 3000 else n - c
+        s.render(m, cut[c:])
+        c += m
+    torch.cuda.synchronize()
+    assert np.array_equal(one.cpu().numpy(), cut.cpu().numpy())
