@@ -260,8 +260,8 @@ int awg_phase_words(awg_t* h, int64_t sample, uint64_t* out_host, int32_t n);
  * checking the in-tile phase approximation against exact words.  Synchronous. */
 int awg_render_phases(awg_t* h, int32_t tone, int64_t n0, int32_t count, uint32_t* out_host);
 
-/* Tile split used for this handle's tone count: tones are summed in this many partial sums per
- * tile (thread-block cluster size).  For information. */
+/* Tile split used for this handle's tone count: the tones of a tile are summed by this many CTAs,
+ * whose partial sums are added in rank order.  For information. */
 int32_t awg_tone_split(const awg_t* h);
 
 /* Sum of the device time (ms) of the last render's kernels, recorded with CUDA events; it is
