@@ -118,3 +118,14 @@ def test_bad_arguments_rejected_without_gpu(awglib):
         awglib.phase_word(float("nan"))
     with pytest.raises(awglib.AwgError):
         awglib.grid_word(1e6, 280e6, 0)
+
+
+def test_null_handles_rejected_without_gpu(awglib):
+    """Entry points given no handle fail with AWG_EINVAL (or -1 for counters) instead of touching
+    the device."""
+    L = awglib.lib()
+    assert L.awg_render_stream(None, 100, 10, None, None) == awglib.AWG_EINVAL
+    assert L.awg_render_chunks(None, 10, 2, None, None) == awglib.AWG_EINVAL
+    assert L.awg_render(None, 100, None, None) == awglib.AWG_EINVAL
+    assert L.awg_launch_count(None) == -1
+    assert L.awg_set_static_engine(None, 1) == awglib.AWG_EINVAL
