@@ -367,6 +367,36 @@ bool flat_third_difference(uint64_t F0, uint64_t F1, int64_t L, int profile) {
   return bound < 1073741824.0;   // 2^30
 }
 
+// Whether a TONE_FLAT3 chirp may also drop the stride-32 differences B_6, E_5 and G_2..G_4 of its
+// run set-up (TONE_LOW6): each is bounded through the mean value theorem by 32^q max |P^(k)| (B_q:
+// k = q, E_q: k = q + 1, G_q: k = q + 2), with max |P^(k)| = 60, 360, 720 |D| / L^(k-1) for
+// k = 4, 5, 6 on the minimum-jerk profile and F_max |alpha|^(k-1) on the exponential one.  Their
+// largest effect on a run's phase, through C(127, q) and the 31 / 465 steps the run takes f and g
+// through, must stay below 64 units of 2^-32 turn (the cascade's own bound is 2500).
+bool low_order_negligible(uint64_t F0, uint64_t F1, int64_t L, int profile) {
+  const double l = (double)L;
+  double d4, d5, d6;
+  if (profile == AWG_PROFILE_MINJERK) {
+    const double D = std::fabs((double)F1 - (double)F0);
+    d4 = 60.0 * D / (l * l * l);
+    d5 = 360.0 * D / (l * l * l * l);
+    d6 = 720.0 * D / (l * l * l * l * l);
+  } else if (profile == AWG_PROFILE_EXPONENTIAL && F0 != F1) {
+    const double a = std::fabs(exp_params(F0, F1, L).alpha) * 1.01;
+    const double Fm = (double)std::max(F0, F1) * 1.01;
+    d4 = Fm * a * a * a;
+    d5 = d4 * a;
+    d6 = d5 * a;
+  } else {
+    return false;
+  }
+  const double s32 = 32.0, c2 = 8001.0, c3 = 333375.0, c4 = 10334625.0, c5 = 254231775.0, c6 = 5169379425.0;
+  const double B6 = std::pow(s32, 6) * d6, E5 = std::pow(s32, 5) * d6;
+  const double G2 = s32 * s32 * d4, G3 = std::pow(s32, 3) * d5, G4 = std::pow(s32, 4) * d6;
+  const double words = B6 * c6 + 31.0 * E5 * c5 + 465.0 * (G2 * c2 + G3 * c3 + G4 * c4);
+  return words < 64.0 * 4294967296.0;
+}
+
 // Phase offset at the end of an exponential chirp, R(L), the same FP64 formula as the render's.
 uint64_t exp_end_offset(uint64_t F0, uint64_t F1, int64_t L) {
   const ExpParams e = exp_params(F0, F1, L);
@@ -1420,7 +1450,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   struct Coeffs {
     W192 d[7];
     uint64_t end_offset;
-    bool exact, flat3;
+    bool exact, flat3, low6;
     float rot_c, rot_s;   // rotator constants of F_end
   };
   std::vector<Coeffs> co(pend.size());
@@ -1432,6 +1462,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
                                                                : chirp_offset_word(co[i].d, p.L);
       co[i].exact = needs_exact(p.F0, p.F1, p.L, p.profile);
       co[i].flat3 = flat_third_difference(p.F0, p.F1, p.L, p.profile);
+      co[i].low6 = co[i].flat3 && low_order_negligible(p.F0, p.F1, p.L, p.profile);
       rotation_of(p.F1, &co[i].rot_c, &co[i].rot_s);
     }
   };
@@ -1469,7 +1500,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     c.L = p.L;
     c.tone = p.tone;
     c.flags = (co[pi].exact ? awgk::TONE_EXACT : 0) | (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0) |
-              (p.profile == AWG_PROFILE_EXPONENTIAL ? awgk::TONE_EXP : 0) | (co[pi].flat3 ? awgk::TONE_FLAT3 : 0);
+              (p.profile == AWG_PROFILE_EXPONENTIAL ? awgk::TONE_EXP : 0) | (co[pi].flat3 ? awgk::TONE_FLAT3 : 0) |
+              (co[pi].low6 ? awgk::TONE_LOW6 : 0);
     const uint64_t phi_end = c.phi_start + co[pi].end_offset;
     t.slot = slot;
     t.n_s = p.ns;

@@ -48,6 +48,8 @@ constexpr int32_t TONE_AMP_RAMP = 4;      // the amplitude ramps (see ToneRec::a
 constexpr int32_t TONE_AMP_MINJERK = 8;   // ... along the minimum-jerk profile (else linear)
 constexpr int32_t TONE_FLAT3 = 32;        // the chirp's third unit difference stays below 2^30 words:
                                           // the run cascade's h rounds to 0 in every run
+constexpr int32_t TONE_LOW6 = 64;         // FLAT3, and B_6, E_5, G_2..G_4 move a run's phase by
+                                          // < 64 units of 2^-32 turn: left out of the run set-up
 constexpr int32_t TONE_EXP = 16;          // exponential chirp: ChirpRec::d[0..4] hold F_start, F_end
                                           // and the doubles alpha, C, e^alpha - 1 (bit patterns)
 

@@ -217,6 +217,18 @@ __device__ __forceinline__ RunPoly poly_state_flat3(const TileRec& rc, const Run
   return pack_run(p, f, g, 0);
 }
 
+// poly_state for a TONE_LOW6 chirp: FLAT3, and the set-up bounds B_6, E_5 and G_2..G_4 below 64
+// units of 2^-32 turn of phase over a run, so they are left out.
+__device__ __forceinline__ RunPoly poly_state_low6(const TileRec& rc, const RunBin& b) {
+  uint64_t p = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.B[0], rc.B[1], b.c1), rc.B[2], b.c2), rc.B[3], b.c3), rc.B[4], b.c4),
+                       rc.B[5], b.c5);
+  asm volatile("" ::: "memory");
+  uint64_t f = mac_u32(mac_u32(mac_u32(mac_u32(rc.E[0], rc.E[1], b.c1), rc.E[2], b.c2), rc.E[3], b.c3), rc.E[4], b.c4);
+  asm volatile("" ::: "memory");
+  uint64_t g = mac_u32(rc.G[0], rc.G[1], b.c1);
+  return pack_run(p, f, g, 0);
+}
+
 __device__ __forceinline__ RunPoly pack_run(uint64_t p, uint64_t f, uint64_t g, uint64_t h) {
   RunPoly r;
   r.p = (uint32_t)((p + P_OFFSET) >> 32);
@@ -607,7 +619,8 @@ struct alignas(16) Desc {
   float c, s;     // DESC_STATIC_ROT: cos and sin of the per-sample phase step
 };
 enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_STATIC_ROT = 4, DESC_SKIP = 5,
-       DESC_FLAT3 = 6 };   // FLAT3: a degree-6 chirp whose h is 0 in every run (TONE_FLAT3)
+       DESC_FLAT3 = 6,     // FLAT3: a degree-6 chirp whose h is 0 in every run (TONE_FLAT3)
+       DESC_LOW6 = 7 };    // LOW6: FLAT3 without the negligible high orders (TONE_LOW6)
 
 
 // Scale, round half to even, clamp and store sample T0 + sidx of a tile (inside the window),
@@ -769,7 +782,10 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
         d.p0 = 0;
         const bool inside = T0 >= tr.n_s && T0 + TILE - 1 <= tr.n_e;
         d.kind = (inside && !exact)
-                     ? ((tr.flags & TONE_LINEAR) ? DESC_LINEAR : (tr.flags & TONE_FLAT3) ? DESC_FLAT3 : DESC_MINJERK)
+                     ? ((tr.flags & TONE_LINEAR)  ? DESC_LINEAR
+                        : (tr.flags & TONE_LOW6)  ? DESC_LOW6
+                        : (tr.flags & TONE_FLAT3) ? DESC_FLAT3
+                                                  : DESC_MINJERK)
                      : DESC_MIXED;
         if (!exact) {
           need = true;
@@ -854,9 +870,9 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
             p += f;
             f += g;
           }
-        } else if (kind == DESC_FLAT3) {
+        } else if (kind == DESC_FLAT3 || kind == DESC_LOW6) {
           // the third difference rounds to 0 everywhere (set-up bound): g is constant over the run
-          const RunPoly q = poly_state_flat3(s_rec[b][i], rb);
+          const RunPoly q = kind == DESC_LOW6 ? poly_state_low6(s_rec[b][i], rb) : poly_state_flat3(s_rec[b][i], rb);
           uint32_t p = q.p + HALF_TURN, f = q.f;
           const uint32_t g = q.g;
 #pragma unroll
