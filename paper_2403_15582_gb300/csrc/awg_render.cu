@@ -5,13 +5,14 @@
 // Phase words.  Static tones: Phi(n) = phi_ref + n F.  Chirps (Eq. freqchirp, linear or
 // minimum-jerk): Phi(n_s + m) = Phi(n_s) + top64(sum_k d_k C(m,k)) with the 192-bit forward
 // differences d_k set up on the host; evaluated here exactly by the closed form
-// (exact_chirp_word), which is what a sequential 192-bit cascade would produce.
+// (exact_chirp_word), which is what a sequential 192-bit cascade would produce.  Exponential
+// chirps: Phi(n_s) + C (e^(alpha m) - 1) in FP64.
 //
 // Work decomposition (see awg_internal.h): a CTA renders one tile of TILE = 4096 absolute-aligned
 // samples; thread j owns the run of RUN = 32 samples starting at T0 + 32 j and keeps its 32 partial
-// sums in registers; the tones are split over the CTAs of a thread-block cluster and the partial
-// sums are added through distributed shared memory in a fixed order, then scaled, rounded and
-// stored by the same kernel.
+// sums in registers; the tones are split over `split` CTAs, whose partial tiles are added in rank
+// order (through L2 scratch by the last CTA of the tile to finish, or through distributed shared
+// memory in a thread-block cluster), then scaled, rounded and stored by the same kernel.
 //
 // Per (tone, run) the phase is set up once and then stepped per sample in 32-bit fixed point
 // (units of 2^-32 turn):
