@@ -83,10 +83,6 @@ W192 w_mul(W192 a, W192 b) {
   return r;
 }
 W192 w_from_u64(uint64_t v) { return W192{{v, 0, 0}}; }
-W192 w_from_s64(int64_t v) {
-  uint64_t s = (uint64_t)(v >> 63);
-  return W192{{(uint64_t)v, s, s}};
-}
 
 // Unsigned little-endian multi-limb integer (up to 8 limbs).
 struct Big {
@@ -159,12 +155,6 @@ Big big_add(const Big& a, const Big& b) {
   }
   return r;
 }
-int big_cmp(const Big& a, const Big& b) {
-  for (int i = 7; i >= 0; --i) {
-    if (a.l[i] != b.l[i]) return a.l[i] < b.l[i] ? -1 : 1;
-  }
-  return 0;
-}
 
 // Delta^k [m^p] at m = 0 = sum_j (-1)^(k-j) C(k,j) j^p  (k! S(p,k), Stirling numbers of the 2nd kind)
 s128 power_difference_sum(int p, int k) {
@@ -191,36 +181,43 @@ s128 power_difference(int p, int k) {
   return table.v[p][k];
 }
 
-// round_half_even( sign * mag * 2^127 / L^pw ), returned mod 2^192
+Big big_shr1(const Big& a) {
+  Big r;
+  for (int i = 0; i < 8; ++i) r.l[i] = (a.l[i] >> 1) | (i < 7 ? a.l[i + 1] << 63 : 0);
+  return r;
+}
+
+// round_half_even( sign * mag * 2^127 / L^pw ), returned mod 2^192.  Successive divisions by L
+// give q2 = floor(mag 2^128 / L^pw) (floor(floor(x / a) / b) = floor(x / (a b))); the quotient
+// rounds up when q2 is odd (fraction >= 1/2), except on an exact tie (every remainder 0) with
+// floor(q2 / 2) even.
 W192 rounded_quotient(bool negative, const Big& mag, uint64_t L, int pw) {
-  Big num = big_shl(mag, 127);
-  // num = q L^pw + R with R = r1 + r2 L + ... (remainders of the successive divisions)
-  Big q = num;
-  uint64_t rem[5] = {0, 0, 0, 0, 0};
-  for (int i = 0; i < pw; ++i) rem[i] = big_divmod_u64(q, L);
-  Big R;
-  Big Lpow = big_from_u128(1);
-  for (int i = 0; i < pw; ++i) {
-    R = big_add(R, big_mul_u128(Lpow, rem[i]));
-    Lpow = big_mul_u128(Lpow, L);
-  }
-  Big twoR = big_shl(R, 1);
-  int c = big_cmp(twoR, Lpow);
-  if (c > 0 || (c == 0 && (q.l[0] & 1))) q = big_add(q, big_from_u128(1));
+  Big q2 = big_shl(mag, 128);
+  bool exact = true;
+  for (int i = 0; i < pw; ++i) exact &= big_divmod_u64(q2, L) == 0;
+  Big q = big_shr1(q2);
+  if ((q2.l[0] & 1) && (!exact || (q.l[0] & 1))) q = big_add(q, big_from_u128(1));
   W192 r = {{q.l[0], q.l[1], q.l[2]}};
   return negative ? w_neg(r) : r;
 }
 
-// C(m, k) for 0 <= m < 2^28 as an exact 192-bit value (the product of k factors < 2^168)
-W192 binom_w(int64_t m, int k) {
-  if (k == 0) return w_from_u64(1);
-  if (m < k) return w_from_u64(0);
-  Big p = big_from_u128(1);
-  for (int i = 0; i < k; ++i) p = big_mul_u128(p, (u128)(m - i));
-  uint64_t fact = 1;
-  for (int i = 2; i <= k; ++i) fact *= (uint64_t)i;
-  big_divmod_u64(p, fact);
-  return W192{{p.l[0], p.l[1], p.l[2]}};
+// C(m, k), k = 0..6, for 0 <= m < 2^28 as exact 192-bit values: C(m, k) = C(m, k-1) (m - k + 1) / k,
+// every product below 6 C(m, 6) < 2^168 and every quotient exact.
+void binomials_w(int64_t m, W192 c[7]) {
+  c[0] = w_from_u64(1);
+  for (int k = 1; k <= 6; ++k) {
+    if (m < k) {
+      c[k] = w_from_u64(0);
+      continue;
+    }
+    const W192 p = w_mul(c[k - 1], w_from_u64((uint64_t)(m - k + 1)));
+    u128 rem = 0;
+    for (int i = 2; i >= 0; --i) {
+      const u128 cur = (rem << 64) | p.w[i];
+      c[k].w[i] = (uint64_t)(cur / (uint64_t)k);
+      rem = cur % (uint64_t)k;
+    }
+  }
 }
 
 W192 w_inverse_odd(uint64_t o) {   // o^-1 mod 2^192 by Newton's iteration
@@ -341,8 +338,11 @@ int chirp_coeffs_impl(uint64_t F0, uint64_t F1, int64_t L, int profile, W192 d[7
 
 // top64 of sum_k d_k C(m, k): the chirp phase in words at offset m (d_0 holds the rounding offset)
 uint64_t chirp_offset_word(const W192 d[7], int64_t m) {
+  W192 c[7];
+  binomials_w(m, c);
   W192 s = {{0, 0, 0}};
-  for (int k = 0; k < 7; ++k) s = w_add(s, w_mul(d[k], binom_w(m, k)));
+  for (int k = 0; k < 7; ++k)
+    if (d[k].w[0] | d[k].w[1] | d[k].w[2]) s = w_add(s, w_mul(d[k], c[k]));
   return s.w[2];
 }
 
