@@ -539,6 +539,62 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
     else if (n0 >= tr.n_s && last <= tr.n_e && !(tr.flags & TONE_EXACT)) mode = 2;
     else mode = 3;
   }
+  if (!ramp && !(tr.flags & TONE_EXACT)) {
+    // no ramp and no table (tile TILE_CHIRP, record present): one loop per warp.  The same
+    // integers as the per-thread paths below, without running three of them one after another
+    // in the warp that holds a chirp boundary.
+    if (__all_sync(0xffffffffu, mode <= 1)) {
+      const uint64_t phi = mode == 0 ? tr.phi_ref : tr.phi_post_ref;
+      const uint64_t F = mode == 0 ? tr.F : tr.F_end;
+      uint32_t p = static_p0(phi, F, n0) + HALF_TURN;
+      const uint32_t f = static_f(F);
+#pragma unroll
+      for (int r = 0; r < RUN; ++r) {
+        acc[r] = fmaf(A, sin_centred(p), acc[r]);
+        p += f;
+      }
+      return;
+    }
+    const RunPoly st = poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0);
+    uint32_t pp = st.p + HALF_TURN, ff = st.f, gg = st.g;
+    const uint32_t hh = st.h;
+    if (__all_sync(0xffffffffu, mode == 2)) {
+      if (__all_sync(0xffffffffu, hh == 0)) {
+#pragma unroll
+        for (int r = 0; r < RUN; ++r) {
+          acc[r] = fmaf(A, sin_centred(pp), acc[r]);
+          pp += ff;
+          ff += gg;
+        }
+      } else {
+#pragma unroll
+        for (int r = 0; r < RUN; ++r) {
+          acc[r] = fmaf(A, sin_centred(pp), acc[r]);
+          pp += ff;
+          ff += gg;
+          gg += hh;
+        }
+      }
+      return;
+    }
+    // a boundary in the warp: sample r takes the static phase before the chirp (r < i1), the
+    // one after it (r > i2), else the chirp cascade; i1, i2 clamped to [-1, RUN]
+    const int i1 = (int)max((int64_t)-1, min((int64_t)RUN, tr.n_s - n0));
+    const int i2 = (int)max((int64_t)-1, min((int64_t)RUN, tr.n_e - n0));
+    uint32_t qa = static_p0(tr.phi_ref, tr.F, n0) + HALF_TURN, qb = static_p0(tr.phi_post_ref, tr.F_end, n0) + HALF_TURN;
+    const uint32_t fa = static_f(tr.F), fb = static_f(tr.F_end);
+#pragma unroll
+    for (int r = 0; r < RUN; ++r) {
+      const uint32_t ph = r < i1 ? qa : (r > i2 ? qb : pp);
+      acc[r] = fmaf(A, sin_centred(ph), acc[r]);
+      qa += fa;
+      qb += fb;
+      pp += ff;
+      ff += gg;
+      gg += hh;
+    }
+    return;
+  }
   if (ramp_run && mode <= 1) {
     // a ramp on a static segment: stepped phase, the amplitude of ramp_amp per sample
     const uint64_t phi = mode == 0 ? tr.phi_ref : tr.phi_post_ref;
