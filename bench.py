@@ -42,7 +42,7 @@ N_SM = 152
 SM_MAX_MHZ = 2070.0
 # DRAM traffic (read + write) of one render launch (2^18-sample chunk, 1000 chirping tones) from
 # the ncu capture summarised in profiles/render_split_kernel_chirp1000_chunk2e18.md (cold cache).
-RENDER_TRAFFIC_BYTES = 11.585536e6   # ncu dram__bytes_read+write of one 2^18-sample render launch
+RENDER_TRAFFIC_BYTES = 11.580928e6   # ncu dram__bytes_read+write of one 2^18-sample render launch
 
 CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
                 "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
