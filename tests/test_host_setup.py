@@ -76,6 +76,29 @@ def test_chirp_coefficients_match_oracle_bitwise(awglib, oracle, profile):
         assert awglib.chirp_coeffs(F0, F1, L, profile) == oracle.chirp_coefficients(F0, F1, L, profile), (F0, F1, L)
 
 
+
+def test_chirp_coefficients_round_exact_ties_to_even(awglib, oracle):
+    """Power-of-two lengths make some minimum-jerk c_k 2^128 land exactly on a half (L^5 = 2^130
+    for L = 2^26): the library's quotient rounding must send those to even, as the oracle's exact
+    fractions do.  The cases are checked to contain such ties.  (Linear coefficients never tie:
+    their denominator 2L holds at most 2^29.)"""
+    profile = 1
+    import math
+    from fractions import Fraction
+    rng = np.random.default_rng(5)
+    M = 1 << 64
+    ties = 0
+    for L in (1 << 26, 1 << 27, 1 << 25, 1 << 24, 3 << 24):
+        for _ in range(10):
+            F0, F1 = int(rng.integers(0, M, dtype=np.uint64)), int(rng.integers(0, M, dtype=np.uint64))
+            P = oracle.chirp_phase_poly(F0, F1, L, profile)
+            vals = [P(m) for m in range(7)]
+            for k in range(1, 7):
+                ck = sum(((-1) ** (k - j)) * math.comb(k, j) * vals[j] for j in range(k + 1))
+                ties += (Fraction(ck) * (1 << 128)).denominator == 2
+            assert awglib.chirp_coeffs(F0, F1, L, profile) == oracle.chirp_coefficients(F0, F1, L, profile), (F0, F1, L)
+    assert ties >= 2, ties
+
 def test_chirp_coefficient_errors(awglib):
     with pytest.raises(awglib.AwgError):
         awglib.chirp_coeffs(1, 2, 0, 0)

@@ -460,3 +460,42 @@ def test_split_sums_across_launches(awg, oracle):
     assert np.max(np.abs(x.cpu().numpy()[idx].astype(np.float64) - x_ref)) <= fp32_bound(a, 16)
     q_ref = oracle.quantize(x_ref, w.full_scale())
     assert np.max(np.abs(q1[idx].astype(np.int32) - q_ref)) <= 1
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_chirp_boundaries_in_every_lane(awg, oracle, mode):
+    """Chirp starts and ends at every run position of a tile (every lane of the four warps), at
+    the first, second and last sample of a run, with both ends in one run (lengths 1..31), in
+    adjacent runs, warps and tiles; linear, minimum-jerk and exponential profiles; a few tones
+    ramping through the same tiles.  Every sample against the oracle, both sine variants, with a
+    tone split of 3."""
+    fs = 280e6
+    K = 200
+    rng = np.random.default_rng(11)
+    f = rng.uniform(5e6, 135e6, K)
+    a = rng.uniform(0.2, 1.0, K)
+    th = rng.uniform(0, 2 * np.pi, K)
+    lengths = (1, 2, 5, 31, 32, 33, 64, 95, 4095, 4096, 4097, 20000)
+    offsets = (0, 1, 31)
+    chirps = []
+    for k in range(160):
+        lane = (k * 37) % 128
+        n_s = 4096 * (1 + k % 40) + 32 * lane + offsets[k % 3]
+        L = lengths[k % len(lengths)]
+        prof = k % 3
+        chirps.append(dict(tone=k, f_start=float(f[k]), f_end=float(rng.uniform(1e6, 139e6)),
+                           duration=L / fs, profile=prof, start_sample=int(n_s)))
+    ramps = [dict(tone=int(t), amp_end=0.3 * float(a[t]), duration=5000 / fs, profile=int(t % 2),
+                  start_sample=int(4096 * (3 + t % 30) + 17 * t)) for t in range(150, 200, 2)]
+    s = awg.Synth(fs)
+    s.set_tones(f, a, th)
+    s.set_chirp_list(chirps)
+    s.set_amp_ramps([r["tone"] for r in ramps], [r["amp_end"] for r in ramps], [r["duration"] for r in ramps],
+                    [r["profile"] for r in ramps], [r["start_sample"] for r in ramps])
+    s.set_sine_mode(mode)
+    assert s.tone_split == 3
+    w = oracle.add_ramps(oracle.make_waveform(fs, f, a, th, chirps), ramps)
+    n = 4096 * 43
+    q, x = render(s, n)
+    assert s.device_status() == 0
+    check(q, x, w, oracle, oracle.render(w, 0, n, nthreads=NTHREADS), s.tone_split)
