@@ -118,8 +118,12 @@ class ClockSampler:
                 "power_w_max": max(pw) if pw else None}
 
 
-def oracle_window_rate(wk, seconds: float, n0: int | None = None):
-    """Time the CPU oracle (all host cores) on a window of the workload sized for ~`seconds`."""
+def oracle_window_rate(wk, seconds: float, n0: int | None = None, record=None, parity=None):
+    """Time the CPU oracle (all host cores) on a window of the workload sized for ~`seconds`.
+    With `record` (the int16 samples the GPU rendered for the whole workload), the timed window is
+    also compared with them: `parity` receives the largest |difference| in LSB and the share of
+    samples equal to the oracle's FP64 sum quantised in FP64."""
+    import numpy as np
     import oracle
     oracle.build()
     w = oracle.make_waveform(wk.fs, wk.freq_hz, wk.amp, wk.phase_rad, wk.chirps, grid_log2=wk.grid_log2)
@@ -131,9 +135,13 @@ def oracle_window_rate(wk, seconds: float, n0: int | None = None):
     dt = max(time.perf_counter() - t0, 1e-6)
     n = int(min(max(probe, probe * seconds / dt), wk.n_samples - start))
     t0 = time.perf_counter()
-    oracle.render(w, start, n, nthreads=nthreads)
+    x_ref = oracle.render(w, start, n, nthreads=nthreads)
     dt = time.perf_counter() - t0
     used = oracle.render.last_threads
+    if record is not None and parity is not None:
+        dq = np.abs(record[start:start + n].astype(np.int32) - oracle.quantize(x_ref, w.full_scale()).astype(np.int32))
+        parity.update({"samples": int(n), "from_sample": int(start), "max_lsb": int(dq.max(initial=0)),
+                       "exact_fraction": float(np.mean(dq == 0)), "reference": "oracle FP64 sum, quantised in FP64"})
     # the same oracle on one thread, on a window sized to ~a quarter of the time budget
     n1 = max(probe, min(n, int(n / max(used, 1) * 0.25)))
     t0 = time.perf_counter()
@@ -547,6 +555,8 @@ def main():
         if i >= args.warmup:
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
     e2e_total = max_over_ranks(sum(e2e_ms), dist, "cuda")
+    record = out.cpu().numpy()   # the whole record (timed steps; the chunk-by-chunk pass wrote the same samples)
+    e2e_same = bool(np.array_equal(record, out_host.numpy()))
     e2e_value = world * work_per_step * args.steps / (e2e_total * 1e-3)
     h2d = K * (2 * 96 + 208)     # 96-B tone records twice (set_tones, set_chirps) + 208-B chirp records
 
@@ -603,7 +613,9 @@ def main():
         line["stream"] = {f"{int(fs_/1e6)}MSps": stream_leg(awg, fs_, stream) for fs_ in (280e6, 50e6)}
         line["stream"]["280MSps_gemm"] = stream_leg(awg, 280e6, stream, engine=awg.STATIC_GEMM_FP16)
     if not args.no_cpu_baseline and world == 1:
-        line["cpu_baseline"] = oracle_window_rate(wk, args.cpu_seconds)
+        parity = {"e2e_output_equals_device_output": e2e_same}
+        line["cpu_baseline"] = oracle_window_rate(wk, args.cpu_seconds, record=record, parity=parity)
+        line["parity"] = parity
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

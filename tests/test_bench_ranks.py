@@ -38,3 +38,20 @@ def test_step_time_is_max_over_two_ranks():
 def test_single_process_is_identity():
     import bench
     assert bench.max_over_ranks(7.0, None, "cpu") == 7.0
+
+
+def test_parity_report_of_the_oracle_window(oracle):
+    """bench.py's parity line: the oracle window against a record, exact and with one sample off."""
+    import bench
+    from paper_2403_15582_gb300 import workloads as wl
+    wk = wl.static_100(seed=0, n_samples=1 << 14)
+    w = oracle.make_waveform(wk.fs, wk.freq_hz, wk.amp, wk.phase_rad, wk.chirps, grid_log2=wk.grid_log2)
+    rec = oracle.quantize(oracle.render(w, 0, wk.n_samples), w.full_scale())
+    par = {}
+    bench.oracle_window_rate(wk, 0.05, record=rec, parity=par)
+    assert par["samples"] > 0 and par["from_sample"] == wk.n_samples // 2
+    assert par["max_lsb"] == 0 and par["exact_fraction"] == 1.0
+    rec[par["from_sample"] + 3] += 2
+    par2 = {}
+    bench.oracle_window_rate(wk, 0.05, record=rec, parity=par2)
+    assert par2["max_lsb"] == 2 and par2["exact_fraction"] == 1.0 - 1.0 / par2["samples"]
