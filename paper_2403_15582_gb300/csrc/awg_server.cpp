@@ -342,23 +342,23 @@ void admit(awg_server_t* s) {
   for (auto it = s->pending.begin(); it != s->pending.end();) {
     Request* r = *it;
     const size_t mem = footprint(r);
-    int verdict = 0;   // 0 wait, 1 admit, -1 reject (deadline), -2 reject (memory)
+    int decision = 0;   // 0 wait, 1 admit, -1 reject (deadline), -2 reject (memory)
     if (!fits_alone(s, r)) {
-      verdict = -1;
+      decision = -1;
     } else if ((int64_t)mem > s->budget) {
-      verdict = -2;
+      decision = -2;
     } else {
       const bool mem_ok = s->used + (int64_t)mem <= s->budget && (int32_t)s->active.size() < s->max_active;
       const bool rt_ok = fits_deadline(s, r);
-      if (mem_ok && rt_ok) verdict = 1;
-      else if (now - r->t_arrival > s->max_queue_s) verdict = rt_ok ? -2 : -1;
+      if (mem_ok && rt_ok) decision = 1;
+      else if (now - r->t_arrival > s->max_queue_s) decision = rt_ok ? -2 : -1;
     }
-    if (verdict == 0) {
+    if (decision == 0) {
       ++it;
       continue;
     }
     changed = true;
-    if (verdict == 1) {
+    if (decision == 1) {
       r->mem = mem;
       s->used += (int64_t)mem;
       r->state = AWG_REQ_ACTIVE;
@@ -367,7 +367,7 @@ void admit(awg_server_t* s) {
       s->to_setup.push_back(r);
     } else {
       r->state = AWG_REQ_REJECTED;
-      ++(verdict == -1 ? s->rej_deadline : s->rej_memory);
+      ++(decision == -1 ? s->rej_deadline : s->rej_memory);
     }
     it = s->pending.erase(it);
   }
