@@ -36,13 +36,15 @@ UNIT = "tone-samples/s"
 # 610 ms, i.e. 9.8e9 / 0.61 tone-samples/s.  Context, another machine.
 PAPER_TONE_SAMPLES_PER_S = 9.8e9 / 0.610
 # SFU peak used as the roofline denominator of the render kernel: 16 sine results per clock per SM
-# x 152 SMs x 2070 MHz maximum SM clock.
+# x the device's SMs (queried) x its maximum SM clock (nvidia-smi clocks.max.sm during the timed
+# region; 2070 MHz on GB300 if unsampled).
 SFU_SIN_PER_CLK_SM = 16
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-# DRAM traffic (read + write) of one render launch (2^18-sample chunk, 1000 chirping tones) from
-# the ncu capture summarised in profiles/render_split_kernel_chirp1000_chunk2e18.md (cold cache).
-RENDER_TRAFFIC_BYTES = 11.580928e6   # ncu dram__bytes_read+write of one 2^18-sample render launch
+SM_MAX_MHZ_DEFAULT = 2070.0
+# DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one render launch of the timed
+# step (a 2^18-sample chunk of the 1000-chirp record), from one ncu capture of the render kernel as
+# it stands in this file's revision; None when the kernel has changed since that capture.
+RENDER_TRAFFIC_BYTES = None
+RENDER_TRAFFIC_SOURCE = "ncu --set full capture of one render_split_kernel launch (2^18 samples, 1000 chirps)"
 
 CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
                 "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
@@ -204,6 +206,56 @@ def stream_leg(awg, fs: float, stream, seconds: float = 1.0, n_slots: int = 4, p
             "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"]},
             "min_lead_ms": st["lead_min_ms"], "playback_ms": st["chunk_playback_ms"], "slots": n_slots,
             "required_tone_samples_per_s": wk.K * fs, "static_engine": ["direct", "gemm_fp16", "gemm_bf16"][engine]}
+
+
+def chirping_leg(awg, stream, K: int, fs: float = 280e6, chunk: int = 1 << 20, segments: int = 7,
+                 n_slots: int = 6, prefill: int = 3):
+    """K tones that all chirp all the time (back-to-back 33.7 ms linear / minimum-jerk chirps between
+    seeded 80-180 MHz frequencies), streamed in real time through the pinned ring with a host sink
+    playing one chunk per chunk / fs: underruns and chunk latency (GPU completion minus push)
+    against the playback time of a chunk.  Beside it, the device rate of one segment rendered
+    through the pipelined chunk loop with the tone state resident."""
+    import torch
+    from paper_2403_15582_gb300 import workloads as wl
+    from paper_2403_15582_gb300.stream import run_stream
+    wk = wl.chirping_stream(seed=0, K=K, fs=fs, segments=segments)
+    S = wk.n_samples // segments
+    synth = awg.Synth(fs)
+    synth.set_tones(wk.freq_hz, wk.amp, wk.phase_rad)
+    ring = awg.Ring(synth, chunk, n_slots)
+    n_chunks = wk.n_samples // chunk
+    t0 = time.perf_counter()
+    st = run_stream(synth, ring, wk.chirps, n_chunks, stream, prefill=prefill)
+    wall = time.perf_counter() - t0
+    status = synth.device_status()
+    ring.close()
+    synth.close()
+    # device rate: the first segment through the pipelined chunk loop, best of 3
+    synth = awg.Synth(fs)
+    synth.set_tones(wk.freq_hz, wk.amp, wk.phase_rad)
+    synth.set_chirp_list([c for c in wk.chirps if c["start_sample"] == 0])
+    out = torch.empty(S, dtype=torch.int16, device="cuda")
+    ts = []
+    for r in range(4):
+        synth.seek(0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        synth.render_stream(S, chunk, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r:
+            ts.append(e0.elapsed_time(e1))
+    synth.close()
+    ms = min(ts)
+    playback = 1e3 * chunk / fs
+    return {"tones": K, "chirping": K, "fs_hz": fs, "chunk": chunk, "chunks": int(st["played"]),
+            "underruns": int(st["underruns"]), "playback_ms": playback,
+            "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"]},
+            "p99_within_playback": bool(st["latency_p99_ms"] < playback), "min_lead_ms": st["lead_min_ms"],
+            "required_tone_samples_per_s": K * fs, "stream_wall_s": wall, "device_status": status,
+            "device_segment_ms": ms, "device_tone_samples_per_s": K * S / (ms * 1e-3),
+            "device_realtime_factor": (S / fs * 1e3) / ms,
+            "slots": n_slots, "prefill": prefill, "segment_samples": S}
 
 
 def measured_peaks():
@@ -466,6 +518,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
+    ap.add_argument("--no-chirping", action="store_true")
     ap.add_argument("--no-table", action="store_true")
     ap.add_argument("--no-served", action="store_true")
     ap.add_argument("--no-static", action="store_true")
@@ -591,9 +644,11 @@ def main():
     chunk_sizes = [min(chunk, N - c0) for c0 in range(0, N, chunk)] * args.steps
     render_total_s = float(np.sum(render_ms)) * 1e-3
     achieved_isolated = K * float(np.sum(chunk_sizes)) / render_total_s / 1e12
-    peak = SFU_SIN_PER_CLK_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12
-    chunk_lat = np.asarray(prep_ms) + np.asarray(render_ms)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     clocks = sampler.summary()
+    sm_max = clocks.get("sm_max_mhz") or SM_MAX_MHZ_DEFAULT
+    peak = SFU_SIN_PER_CLK_SM * n_sm * sm_max * 1e6 / 1e12
+    chunk_lat = np.asarray(prep_ms) + np.asarray(render_ms)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -604,8 +659,9 @@ def main():
         "chunk_latency_ms": {"p50": float(np.percentile(chunk_lat, 50)), "p99": float(np.percentile(chunk_lat, 99)),
                              "playback_ms": 1e3 * chunk / wk.fs},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tsin/s",
-                     "frac": achieved / peak, "traffic": RENDER_TRAFFIC_BYTES,
-                     "kernel": "render_split_kernel", "peak_source": "16 SFU sin/clk/SM x 152 SMs x 2070 MHz",
+                     "frac": achieved / peak, "traffic": RENDER_TRAFFIC_BYTES, "traffic_source": RENDER_TRAFFIC_SOURCE,
+                     "kernel": "render_split_kernel",
+                     "peak_source": f"16 SFU sin/clk/SM x {n_sm} SMs x {sm_max:g} MHz (nominal SFU rate, measured clock)",
                      "basis": "timed steps: sines / step time (pipelined chunk renders, set-up included)",
                      "isolated_launch": {"achieved": achieved_isolated, "frac": achieved_isolated / peak,
                                          "basis": "chunk-by-chunk pass: sines / render kernel event time"}},
@@ -630,6 +686,11 @@ def main():
     if not args.no_stream:
         line["stream"] = {f"{int(fs_/1e6)}MSps": stream_leg(awg, fs_, stream) for fs_ in (280e6, 50e6)}
         line["stream"]["280MSps_gemm"] = stream_leg(awg, 280e6, stream, engine=awg.STATIC_GEMM_FP16)
+    if not args.no_chirping:
+        # the real-time target: 10,000 (and 11,000) tones all chirping at once at 280 MS/s
+        line["chirping_10000_280MSps"] = {f"chunk_2^{c.bit_length() - 1}": chirping_leg(awg, stream, 10000, chunk=c)
+                                         for c in (1 << 20, 1 << 18)}
+        line["chirping_11000_280MSps"] = {"chunk_2^20": chirping_leg(awg, stream, 11000, chunk=1 << 20)}
     if not args.no_cpu_baseline and world == 1:
         parity = {"e2e_output_equals_device_output": e2e_same}
         line["cpu_baseline"] = oracle_window_rate(wk, args.cpu_seconds, record=record, parity=parity)

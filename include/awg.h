@@ -290,8 +290,9 @@ int awg_profile_end(awg_t* h, float* prep_ms, float* render_ms, int32_t cap, int
  * up front.  Such a caller creates the handle and sets its tones and chirps beforehand, then
  * calls this for every chunk.  The chirp tile records and their slot map go to a fixed 12 MiB
  * scratch array compiled into the library, which every GPU that loads the library holds until
- * the process exits.  The first call on a device looks up that array's device address, so make
- * it before any stream capture.  AWG_ENOMEM (with a message) when the window needs more than
+ * the process exits.  awg_create looks up that array's device address on its device (loading
+ * the code that holds it), so no call of this function does; it renders on the handle's device
+ * only (AWG_EINVAL on another current device).  AWG_ENOMEM (with a message) when the window needs more than
  * AWG_NOALLOC_MAX_RECORDS records or a chirp slot index reaches AWG_NOALLOC_MAX_SLOTS.  All calls
  * in the process share the scratch: each call writes every record it reads, so nothing needs to
  * start at zero, but calls whose kernels overlap on the GPU (other streams, other handles) race
@@ -302,6 +303,15 @@ int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream);
  * AWG_ETIMEOUT when a bounded wait on an mbarrier gave up).  Reading it synchronises.  Clears
  * the word. */
 int awg_device_status(awg_t* h);
+
+/* Test hook for the bounded waits on the device: launches on `stream` the join kernel that ends
+ * the pipelined chunk sequences (awg_render_chunks), with a target one above the handle's count of
+ * finished render CTAs -- a count no kernel will reach -- and a wait limit of limit_us
+ * microseconds (1 .. 10^7).  The wait gives up after the limit, sets the device status word to
+ * AWG_ETIMEOUT (read it with awg_device_status) and the kernel returns: nothing hangs, and the
+ * handle and the CUDA context stay usable.  Asynchronous.  AWG_EINVAL for a limit out of range.
+ * (The paper has no counterpart: this checks the library's own failure path.) */
+int awg_test_wait_timeout(awg_t* h, int64_t limit_us, void* stream);
 
 /* ------------------------------------------------------------------------------------------
  * Periodic table on tensor cores.

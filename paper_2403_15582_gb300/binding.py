@@ -15,6 +15,7 @@ SINE_SFU, SINE_ROTATOR = 0, 1
 PERIODIC_DIRECT, PERIODIC_GEMM_BF16, PERIODIC_GEMM_FP16 = 0, 1, 2
 STATIC_DIRECT, STATIC_GEMM_FP16, STATIC_GEMM_BF16 = 0, 1, 2
 PROFILE_LINEAR, PROFILE_MINJERK, PROFILE_EXPONENTIAL = 0, 1, 2
+NOALLOC_MAX_RECORDS, NOALLOC_MAX_SLOTS = 71493, 16384   # AWG_NOALLOC_MAX_RECORDS / _SLOTS of awg.h
 
 # (name, restype, argtypes) of every symbol declared in include/awg.h
 P, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
@@ -75,6 +76,7 @@ SIGNATURES = [
     ("awg_profile_begin", ctypes.c_int, [P]),
     ("awg_profile_end", ctypes.c_int, [P, P, P, i32, P]),
     ("awg_device_status", ctypes.c_int, [P]),
+    ("awg_test_wait_timeout", ctypes.c_int, [P, i64, P]),
 ]
 
 _lib = None
@@ -332,6 +334,9 @@ class Synth:
     def device_status(self) -> int:
         v = lib().awg_device_status(self._h)
         return int(v)
+
+    def test_wait_timeout(self, limit_us: int, stream=None):
+        _check(lib().awg_test_wait_timeout(self._h, int(limit_us), _stream_ptr(stream)))
 
 
 class RingStats(ctypes.Structure):

@@ -20,6 +20,10 @@ using awgk::ChirpRec;
 using awgk::TileRec;
 using awgk::ToneRec;
 
+// The public limits of awg_render_noalloc are the sizes of its fixed scratch.
+static_assert(awgk::NOALLOC_MAX_RECORDS == AWG_NOALLOC_MAX_RECORDS, "awg.h: AWG_NOALLOC_MAX_RECORDS");
+static_assert(awgk::NOALLOC_MAX_SLOTS == AWG_NOALLOC_MAX_SLOTS, "awg.h: AWG_NOALLOC_MAX_SLOTS");
+
 namespace {
 
 thread_local std::string g_err;
@@ -500,6 +504,12 @@ struct awg {
   int64_t periodic_start = -1;
   cudaStream_t priv = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_done = nullptr;
+  // stream-ordered uploads of changed records (awg_set_chirps): pinned staging, copied on the
+  // private stream after the last render issued (ev_done); later launches wait for ev_upload
+  unsigned char* stage = nullptr;
+  size_t cap_stage = 0;
+  cudaEvent_t ev_upload = nullptr;
+  bool upload_pending = false;
   bool timed = false, have_done = false;
   bool profiling = false;
   std::vector<cudaEvent_t> prof_ev;   // 4 per recorded render call
@@ -545,7 +555,24 @@ int wait_idle(awg_t* h) {
     cudaError_t e = cudaEventSynchronize(h->ev_done);
     if (e != cudaSuccess) return cuda_fail(e, "waiting for the last render");
   }
+  if (h->upload_pending) {
+    cudaError_t e = cudaEventSynchronize(h->ev_upload);
+    if (e != cudaSuccess) return cuda_fail(e, "waiting for the last upload");
+    h->upload_pending = false;
+  }
   return AWG_OK;
+}
+
+// Device work on stream s that reads the handle's tone, chirp or table records is issued after
+// the copies of the last stream-ordered upload.
+cudaError_t order_after_uploads(awg_t* h, cudaStream_t s) {
+  if (!h->upload_pending) return cudaSuccess;
+  if (cudaEventQuery(h->ev_upload) == cudaSuccess) {
+    h->upload_pending = false;
+    return cudaSuccess;
+  }
+  cudaGetLastError();   // cudaErrorNotReady is not an error here
+  return cudaStreamWaitEvent(s, h->ev_upload, 0);
 }
 
 template <class T>
@@ -779,7 +806,7 @@ int set_tones_common(awg_t* h, const double* f, const double* amp, const double*
 // Per-sample exact 32-bit phases for every live TONE_EXACT chirp (very short, fast chirps),
 // packed one after another; the tone records get their offsets.  Chirp records must already be
 // on the device.
-int build_exact_tables(awg_t* h) {
+int build_exact_tables(awg_t* h, bool sync = true) {
   size_t total = 0;
   for (const ChirpRec& c : h->chirps)
     if (c.tone >= 0 && (c.flags & awgk::TONE_EXACT)) total += (size_t)c.L + 1;
@@ -800,8 +827,59 @@ int build_exact_tables(awg_t* h) {
     h->tones[(size_t)c.tone].tab_off = (int32_t)off;
     off += (size_t)c.L + 1;
   }
+  if (!sync) return AWG_OK;
   cudaError_t e = cudaStreamSynchronize(h->priv);
   if (e != cudaSuccess) return cuda_fail(e, "exact tables");
+  return AWG_OK;
+}
+
+// Stream-ordered upload through the pinned staging buffer: stage_begin makes room for `bytes`
+// (after the previous upload's copies have read the buffer) and orders the private stream after
+// the last render issued; stage_runs queues the copies of the records at the given sorted unique
+// indices; stage_end marks the upload's completion (ev_upload) for later launches to wait on.
+int stage_begin(awg_t* h, size_t bytes) {
+  cudaError_t e;
+  if (h->upload_pending) {
+    if ((e = cudaEventSynchronize(h->ev_upload)) != cudaSuccess) return cuda_fail(e, "waiting for the last upload");
+    h->upload_pending = false;
+  }
+  if (bytes > h->cap_stage) {
+    const size_t ncap = std::max(bytes, 2 * h->cap_stage);
+    unsigned char* p = nullptr;
+    if (cudaHostAlloc((void**)&p, ncap, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AWG_ENOMEM, "cudaHostAlloc upload staging");
+    }
+    if (h->stage) cudaFreeHost(h->stage);
+    h->stage = p;
+    h->cap_stage = ncap;
+  }
+  if (h->have_done && (e = cudaStreamWaitEvent(h->priv, h->ev_done, 0)) != cudaSuccess)
+    return cuda_fail(e, "upload ordering");
+  return AWG_OK;
+}
+
+template <class T>
+int stage_runs(awg_t* h, T* dev, const std::vector<T>& host, const std::vector<int32_t>& idx, size_t* off) {
+  size_t i = 0;
+  while (i < idx.size()) {
+    size_t j = i + 1;
+    while (j < idx.size() && idx[j] == idx[j - 1] + 1) ++j;
+    const size_t first = (size_t)idx[i], count = (size_t)(idx[j - 1] - idx[i] + 1);
+    const size_t bytes = count * sizeof(T);
+    std::memcpy(h->stage + *off, host.data() + first, bytes);
+    cudaError_t e = cudaMemcpyAsync(dev + first, h->stage + *off, bytes, cudaMemcpyHostToDevice, h->priv);
+    if (e != cudaSuccess) return cuda_fail(e, "staged upload");
+    *off += bytes;
+    i = j;
+  }
+  return AWG_OK;
+}
+
+int stage_end(awg_t* h) {
+  cudaError_t e = cudaEventRecord(h->ev_upload, h->priv);
+  if (e != cudaSuccess) return cuda_fail(e, "upload event");
+  h->upload_pending = true;
   return AWG_OK;
 }
 
@@ -884,6 +962,7 @@ int render_direct(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
     for (int i = 0; i < 4; ++i) pe[i] = h->prof_ev[4 * h->prof_calls + (size_t)i];
   }
   int64_t launches = 0;
+  if ((e = order_after_uploads(h, s)) != cudaSuccess) return cuda_fail(e, "upload ordering");
   if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
   if (pe[0] && (e = cudaEventRecord(pe[0], s)) != cudaSuccess) return cuda_fail(e, "event");
   for (size_t b = 0; b < active.size(); b += awgk::MAX_ACTIVE_PER_LAUNCH) {
@@ -1043,6 +1122,7 @@ int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
     t.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
     t.status = h->d_status;
     cudaError_t e;
+    if ((e = order_after_uploads(h, s)) != cudaSuccess) return cuda_fail(e, "upload ordering");
     if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
     if ((e = counted(h, awgk::launch_table_prep(t, s))) != cudaSuccess) return cuda_fail(e, "static operand launch");
     if ((e = counted(h, awgk::launch_table_gemm(t, s))) != cudaSuccess) return cuda_fail(e, "static GEMM launch");
@@ -1108,6 +1188,10 @@ int awgk::prepare_render(awg_t* h, int64_t n, int16_t* out_q, float* out_f, cuda
     if (st) return st;
     recs = h->d_recs;
     act = h->d_act;
+  }
+  {
+    const cudaError_t e = order_after_uploads(h, s);
+    if (e != cudaSuccess) return cuda_fail(e, "upload ordering");
   }
   for (size_t b = 0; b < active.size(); b += awgk::MAX_ACTIVE_PER_LAUNCH) {
     awgk::PrepArgs pa;
@@ -1175,6 +1259,17 @@ std::vector<int32_t> active_slots(const awg_t* h, int64_t c, int64_t n, int64_t*
 // chunk complete.
 constexpr size_t SEQ_RECORD_BUDGET = (size_t)1 << 22;   // 4M records (704 MiB) per group
 
+// The device counter of render CTAs that stored their samples (pipelined sequences), zero at
+// allocation; every sequence's join waits for its own running total.
+int ensure_seq_counter(awg_t* h) {
+  if (h->d_seq_exit) return AWG_OK;
+  if (cudaMalloc((void**)&h->d_seq_exit, sizeof(unsigned long long)) != cudaSuccess)
+    return fail(AWG_ENOMEM, "cudaMalloc sequence counter");
+  cudaError_t e = cudaMemset(h->d_seq_exit, 0, sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_fail(e, "sequence counter");
+  return AWG_OK;
+}
+
 int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, cudaStream_t s, int64_t tail = 0) {
   // chunks 0 .. n_chunks - 1 of `chunk` samples, then (tail > 0) one of `tail` samples
   const int64_t n_total = (int64_t)n_chunks * chunk + tail;
@@ -1183,12 +1278,8 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
     return std::min((int64_t)b * chunk, n_total) - (int64_t)a * chunk;
   };
   cudaError_t e;
-  if (!h->d_seq_exit) {
-    if (cudaMalloc((void**)&h->d_seq_exit, sizeof(unsigned long long)) != cudaSuccess)
-      return fail(AWG_ENOMEM, "cudaMalloc sequence counter");
-    if ((e = cudaMemset(h->d_seq_exit, 0, sizeof(unsigned long long))) != cudaSuccess)
-      return cuda_fail(e, "sequence counter");
-  }
+  int st0 = ensure_seq_counter(h);
+  if (st0) return st0;
   const int64_t c0 = h->cursor;
   struct Group {
     int32_t g0, g1;
@@ -1223,6 +1314,7 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
   if (h->split > 1 && (st = ensure_split_scratch(h, (int32_t)(chunk / awgk::TILE + 2), h->split))) return st;
   st = ensure(&h->d_seq_act, &h->cap_seq_act, std::max<size_t>(1, h->chirps.size()), h, "slot map");
   if (st) return st;
+  if ((e = order_after_uploads(h, s)) != cudaSuccess) return cuda_fail(e, "upload ordering");
   if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
   for (const Group& grp : groups) {
     const int32_t g0 = grp.g0, g1 = grp.g1;
@@ -1276,7 +1368,8 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
       if ((e = counted(h, awgk::launch_render(ra, s))) != cudaSuccess) return cuda_fail(e, "render launch");
       h->seq_exit_target += (unsigned long long)ra.n_tiles * (unsigned long long)h->split;
     }
-    if ((e = counted(h, awgk::launch_join(h->d_seq_exit, h->seq_exit_target, h->d_status, s))) != cudaSuccess)
+    if ((e = counted(h, awgk::launch_join(h->d_seq_exit, h->seq_exit_target, h->d_status, awgk::JOIN_LIMIT_NS, s))) !=
+        cudaSuccess)
       return cuda_fail(e, "join launch");
   }
   if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
@@ -1345,12 +1438,20 @@ awg_t* awg_create(double sample_rate_hz) {
   fill_constants(h);
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = awgk::render_setup_attributes();
+  if (e == cudaSuccess) {
+    // the allocation-free render's fixed scratch: its device address is looked up (and its module
+    // loaded) here, at set-up, so that no awg_render_noalloc call pays for it
+    awgk::TileRec* recs = nullptr;
+    int32_t* act = nullptr;
+    e = awgk::noalloc_scratch(h->device, &recs, &act);
+  }
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->d_status, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->priv, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&h->ev1);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_upload, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     cuda_fail(e, "awg_create");
     awg_destroy(h);
@@ -1388,7 +1489,9 @@ void awg_destroy(awg_t* h) {
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ev_done) cudaEventDestroy(h->ev_done);
+  if (h->ev_upload) cudaEventDestroy(h->ev_upload);
   if (h->priv) cudaStreamDestroy(h->priv);
+  if (h->stage) cudaFreeHost(h->stage);
   delete h;
 }
 
@@ -1441,8 +1544,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     const ToneRec& t = h->tones[(size_t)p.tone];
     if (t.slot >= 0 && t.n_e >= h->cursor) return fail(AWG_EINVAL, "tone already has a chirp that has not finished rendering");
   }
-  int st = wait_idle(h);
-  if (st) return st;
+  int st;
   h->periodic_start = -1;
   const size_t slots_before = h->chirps.size();
   // the coefficient words, end offsets and exact-table flags of every chirp: pure functions of
@@ -1516,18 +1618,33 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   std::sort(changed_tones.begin(), changed_tones.end());
   std::sort(changed_slots.begin(), changed_slots.end());
   changed_slots.erase(std::unique(changed_slots.begin(), changed_slots.end()), changed_slots.end());
-  if (h->chirps.size() > h->cap_chirps || slots_before == 0) {
-    st = upload_chirps(h);
-  } else {
-    st = upload_runs(h->d_chirps, h->chirps, changed_slots, "upload chirps");
-  }
-  if (st) return st;
-  st = build_exact_tables(h);
-  if (st) return st;
   bool any_exact = false;
   for (const ChirpRec& c : h->chirps) any_exact |= (c.tone >= 0 && (c.flags & awgk::TONE_EXACT));
-  if (any_exact) return upload_tones(h);   // table offsets may have moved for any exact tone
-  return upload_runs(h->d_tones, h->tones, changed_tones, "upload tones");
+  if (h->chirps.size() > h->cap_chirps || slots_before == 0) {
+    // first chirps or a larger slot pool: synchronous (reallocation waits for the device anyway)
+    if ((st = wait_idle(h))) return st;
+    if ((st = upload_chirps(h))) return st;
+    if ((st = build_exact_tables(h))) return st;
+    if (any_exact) return upload_tones(h);   // table offsets may have moved for any exact tone
+    return upload_runs(h->d_tones, h->tones, changed_tones, "upload tones");
+  }
+  // steady state: the copies (and the exact tables' kernels) run on the private stream after the
+  // renders issued so far, and later renders wait for them, so this call does not wait for the
+  // device.  Staged: chirp records, then the tone records (all of them when an exact table's
+  // offset may have moved).
+  const size_t tone_bytes = (any_exact ? h->tones.size() : changed_tones.size()) * sizeof(ToneRec);
+  if ((st = stage_begin(h, changed_slots.size() * sizeof(ChirpRec) + tone_bytes))) return st;
+  size_t off = 0;
+  if ((st = stage_runs(h, h->d_chirps, h->chirps, changed_slots, &off))) return st;
+  if ((st = build_exact_tables(h, false))) return st;
+  if (any_exact) {
+    std::vector<int32_t> all(h->tones.size());
+    for (size_t k = 0; k < all.size(); ++k) all[k] = (int32_t)k;
+    if ((st = stage_runs(h, h->d_tones, h->tones, all, &off))) return st;
+  } else if ((st = stage_runs(h, h->d_tones, h->tones, changed_tones, &off))) {
+    return st;
+  }
+  return stage_end(h);
 }
 
 int awg_set_amp_ramps(awg_t* h, const int32_t* tone, const double* amp_end, const double* duration_s,
@@ -1891,6 +2008,7 @@ int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q
     }
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) pe[i] = h->prof_ev[4 * h->prof_calls + (size_t)i];
   }
+  if (e == cudaSuccess) e = order_after_uploads(h, s);
   if (e == cudaSuccess) e = cudaEventRecord(h->ev0, s);
   if (e == cudaSuccess && pe[0]) e = cudaEventRecord(pe[0], s);
   if (e == cudaSuccess) e = counted(h, awgk::launch_table_prep(t, s));
@@ -1928,6 +2046,7 @@ int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream) {
   const int64_t tile0 = c / awgk::TILE;
   const int64_t tile_last = (c + n - 1) / awgk::TILE;
   const int64_t n_tiles = tile_last - tile0 + 1;
+  if (n_tiles > (int64_t)(INT32_MAX / awgk::MAX_SPLIT)) return fail(AWG_EINVAL, "render window too long");
   const int64_t span0 = tile0 * awgk::TILE, span1 = (tile_last + 1) * awgk::TILE - 1;
   auto is_active = [&](const ChirpRec& cr) {
     return cr.tone >= 0 && !(cr.flags & awgk::TONE_EXACT) && cr.n_s <= span1 && cr.n_s + cr.L >= span0;
@@ -1943,6 +2062,7 @@ int awg_render_noalloc(awg_t* h, int64_t n, int16_t* out, void* stream) {
     return fail(AWG_ENOMEM, "window needs " + std::to_string(n_active * n_tiles) +
                                 " chirp tile records; the fixed scratch holds " +
                                 std::to_string(awgk::NOALLOC_MAX_RECORDS) + " (AWG_NOALLOC_MAX_RECORDS)");
+  if ((e = order_after_uploads(h, s)) != cudaSuccess) return cuda_fail(e, "upload ordering");
   if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
   awgk::PrepArgs pa;
   std::memset(&pa, 0, sizeof(pa));
@@ -2021,6 +2141,19 @@ int awg_profile_end(awg_t* h, float* prep_ms, float* render_ms, int32_t cap, int
     if (render_ms) render_ms[i] = b;
   }
   return (int)std::min<size_t>(n, (size_t)INT32_MAX);
+}
+
+int awg_test_wait_timeout(awg_t* h, int64_t limit_us, void* stream) {
+  if (!h) return fail(AWG_EINVAL, "null handle");
+  if (limit_us < 1 || limit_us > 10000000) return fail(AWG_EINVAL, "limit_us must be in 1 .. 10^7");
+  int st = ensure_seq_counter(h);
+  if (st) return st;
+  // one above the running total of every sequence issued so far: no render CTA brings the counter
+  // there, so the wait runs out
+  cudaError_t e = counted(h, awgk::launch_join(h->d_seq_exit, h->seq_exit_target + 1, h->d_status,
+                                               (uint64_t)limit_us * 1000ull, (cudaStream_t)stream));
+  if (e != cudaSuccess) return cuda_fail(e, "join launch");
+  return AWG_OK;
 }
 
 int awg_device_status(awg_t* h) {

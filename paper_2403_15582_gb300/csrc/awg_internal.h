@@ -205,8 +205,11 @@ cudaError_t launch_exact_table(const TableArgs& a, int64_t L, cudaStream_t s);
 cudaError_t launch_render(const RenderArgs& a, cudaStream_t s);
 cudaError_t launch_replay(const int16_t* tab, int32_t log2_len, int64_t c, int64_t n, int16_t* out, int32_t stride,
                           cudaStream_t s);
+// A bounded wait on the device (join of a pipelined sequence): at most limit_ns of wall time, then
+// the status word becomes AWG_ETIMEOUT and the kernel returns.
+constexpr uint64_t JOIN_LIMIT_NS = 2000000000ull;
 cudaError_t launch_join(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status,
-                        cudaStream_t s);
+                        uint64_t limit_ns, cudaStream_t s);
 // items[i] = (request index into reqs, window tile); every request has split == `split`.
 // Several renders in one launch (tiles items[i] = (request, tile) of the requests reqs[]; all of
 // tone split `split`); every request carries split scratch (part, tile_ctr with n_tiles zeroed
@@ -216,6 +219,9 @@ cudaError_t launch_render_batch_split(const RenderArgs* reqs, const int2* items,
 cudaError_t launch_phase_words(const PhaseArgs& a, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, cudaStream_t s);
 cudaError_t render_setup_attributes();
+// Number of SMs of the current device (queried once per device, then cached); grid sizes of the
+// grid-stride kernels are multiples of it.
+int device_sm_count();
 
 // Fixed scratch of the allocation-free render (awg_noalloc.cu): 12 MiB of tile records and a map
 // for 16384 chirp slots.  Looks up the arrays' device addresses on first use for `device`, which

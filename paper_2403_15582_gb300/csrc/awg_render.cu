@@ -24,6 +24,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 
 #include "awg_internal.h"
@@ -456,13 +457,13 @@ __device__ __forceinline__ void prep_exp(const ChirpRec& c, int64_t m, const Pre
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
-// Bounded wait (~2 s) until a device counter reaches target; false on timeout.
-__device__ bool wait_counter(const unsigned long long* ctr, unsigned long long target) {
+// Bounded wait (limit_ns of wall time) until a device counter reaches target; false on timeout.
+__device__ bool wait_counter(const unsigned long long* ctr, unsigned long long target, uint64_t limit_ns) {
   const volatile unsigned long long* v = ctr;
   if (*v >= target) return true;
   const uint64_t t0 = global_ns();
   while (*v < target) {
-    if (global_ns() - t0 > 2000000000ull) return false;
+    if (global_ns() - t0 > limit_ns) return false;
     __nanosleep(256);
   }
   return true;
@@ -1083,6 +1084,18 @@ __global__ void trace_kernel(const __grid_constant__ TraceArgs a) {
 
 }  // namespace
 
+int device_sm_count() {
+  constexpr int MAX_DEV = 64;
+  static std::atomic<int> cache[MAX_DEV];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEV) return 1;
+  int n = cache[dev].load(std::memory_order_relaxed);
+  if (n > 0) return n;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+  cache[dev].store(n, std::memory_order_relaxed);
+  return n;
+}
+
 cudaError_t render_setup_attributes() {
   cudaError_t e = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   return e;
@@ -1138,21 +1151,23 @@ cudaError_t launch_replay(const int16_t* tab, int32_t log2_len, int64_t c, int64
   const uint64_t mask = ((uint64_t)1 << log2_len) - 1;
   const int vec = stride == 1 && (c & 7) == 0 && ((uintptr_t)out & 15) == 0 && log2_len >= 3;
   const int64_t work = vec ? n / 8 + 1 : n;
-  const int64_t blocks = std::min<int64_t>((work + 255) / 256, 152 * 16);
+  const int64_t blocks = std::min<int64_t>((work + 255) / 256, (int64_t)device_sm_count() * 16);
   replay_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(tab, mask, c, n, out, stride, vec);
   return cudaGetLastError();
 }
 
 // End of a pipelined sequence: returns once every render CTA of the sequence has stored its
-// samples (*exit_ctr >= target), so that later work in the stream sees all of them.
-__global__ void join_kernel(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status) {
-  if (!wait_counter(exit_ctr, target)) atomicExch(status, STATUS_TIMEOUT);
+// samples (*exit_ctr >= target), so that later work in the stream sees all of them.  Gives up after
+// limit_ns, sets the status word to AWG_ETIMEOUT and returns.
+__global__ void join_kernel(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status,
+                            uint64_t limit_ns) {
+  if (!wait_counter(exit_ctr, target, limit_ns)) atomicExch(status, STATUS_TIMEOUT);
   __threadfence();
 }
 
 cudaError_t launch_join(const unsigned long long* exit_ctr, unsigned long long target, int32_t* status,
-                        cudaStream_t s) {
-  join_kernel<<<1, 1, 0, s>>>(exit_ctr, target, status);
+                        uint64_t limit_ns, cudaStream_t s) {
+  join_kernel<<<1, 1, 0, s>>>(exit_ctr, target, status, limit_ns);
   return cudaGetLastError();
 }
 

@@ -512,7 +512,7 @@ size_t table_kp_window(int K) { return (((size_t)4 * K + TK - 1) / TK) * TK; }
 cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s) {
   const int64_t Kp = (int64_t)(t.window_mode ? table_kp_window(t.K) : table_kp(t.K));
   const int threads = 256;
-  const int blocks = 152 * 4;
+  const int blocks = device_sm_count() * 4;
   if (t.precision == 0)
     prep_b_kernel<__nv_bfloat16><<<blocks, threads, 0, s>>>(t.tones, t.K, Kp, (__nv_bfloat16*)t.b_hi,
                                                            (__nv_bfloat16*)t.b_lo, t.window_mode);

@@ -125,6 +125,30 @@ def stream_rotating(seed: int = 0, fs: float = 280e6, K: int = 10000, group: int
     return Workload(f"stream-{K}tone-{fs/1e6:g}MSps", fs, f, A, th, chirps, n, chunk)
 
 
+def chirping_stream(seed: int = 0, K: int = 10000, fs: float = 280e6, segments: int = 7,
+                    segment_samples: int = 9 << 20) -> Workload:
+    """K tones that all chirp all the time: in segment s (samples s S .. (s+1) S - 1, S = 9 x 2^20,
+    33.7 ms at 280 MS/s) every tone ramps from its current frequency to a new seeded target in
+    80-180 MHz over L = S - 1 samples, so the next chirp starts at the next segment's first sample
+    (a chirp spans m = 0..L).  Even tones linear, odd tones minimum-jerk; amplitudes U[0.5, 1]/K,
+    uniform phases: the 1000-tone 35 ms chirp shape at K tones, continued indefinitely."""
+    rng = np.random.default_rng(seed)
+    cur = rng.uniform(80e6, 180e6, K)
+    f0 = cur.copy()
+    A = rng.uniform(0.5, 1.0, K) / K
+    th = rng.uniform(0.0, 2.0 * math.pi, K)
+    L = segment_samples - 1
+    chirps = []
+    for seg in range(segments):
+        tgt = rng.uniform(80e6, 180e6, K)
+        for k in range(K):
+            chirps.append(dict(tone=k, f_start=float(cur[k]), f_end=float(tgt[k]), duration=L / fs,
+                               profile=(LINEAR if k % 2 == 0 else MINJERK), start_sample=seg * segment_samples))
+        cur = tgt
+    n = segments * segment_samples
+    return Workload(f"chirping-{K}tone-{fs/1e6:g}MSps", fs, f0, A, th, chirps, n, 1 << 20)
+
+
 @dataclass
 class Request:
     """One tweezer-rearrangement request (Sec. V-B): a static comb with some tones chirped."""

@@ -29,6 +29,18 @@ def test_library_exports_every_declared_symbol(awglib):
     assert bound == declared
 
 
+def test_header_limits_match_the_binding(awglib):
+    """The noalloc limits the binding exposes are the #defines of include/awg.h (the library itself
+    ties those to its fixed scratch with static_asserts)."""
+    import os
+    import re
+    from paper_2403_15582_gb300 import binding
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "awg.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in re.finditer(r"#define\s+(AWG_\w+)\s+(\d+)", hdr)}
+    assert defs["AWG_NOALLOC_MAX_RECORDS"] == binding.NOALLOC_MAX_RECORDS
+    assert defs["AWG_NOALLOC_MAX_SLOTS"] == binding.NOALLOC_MAX_SLOTS
+
+
 def test_version_and_error_string(awglib):
     assert awglib.lib().awg_version() >= 10000
     with pytest.raises(awglib.AwgError) as e:

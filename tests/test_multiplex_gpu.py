@@ -1,10 +1,15 @@
-"""Channel multiplexing fused into the render's store (the WM step): interleaved groups of one
-sample per channel, each channel bit-identical to its own render."""
+"""Channel multiplexing fused into the render's store (the WM step of Sec. IV-C): interleaved
+groups of one sample per channel.  Each de-interleaved channel is compared element by element with
+the CPU oracle (int16 within 1 LSB) and with its own render (bit for bit)."""
+import os
+
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+NTHREADS = os.cpu_count() or 1
 
 
 @pytest.fixture(scope="module")
@@ -14,7 +19,7 @@ def awg(awglib):
     return awglib
 
 
-def _channel(awg, seed, K, fs=280e6, chirps=0):
+def _channel(awg, seed, K, fs=280e6, chirps=0, oracle=None):
     rng = np.random.default_rng(seed)
     f = rng.uniform(80e6, 180e6, K)
     a = rng.uniform(0.5, 1.0, K) / K
@@ -29,12 +34,18 @@ def _channel(awg, seed, K, fs=280e6, chirps=0):
         if ch:
             s.set_chirp_list(ch)
         return s
+
+    def reference(n):
+        """The oracle's int16 codes of samples 0 .. n-1 (full scale sum |A|)."""
+        w = oracle.make_waveform(fs, f, a, th, ch)
+        return oracle.quantize(oracle.render(w, 0, n, nthreads=NTHREADS), w.full_scale())
+    make.reference = reference
     return make
 
 
 @pytest.mark.parametrize("n_ch", [1, 2, 4])
-def test_interleaved_channels_equal_their_own_renders(awg, n_ch):
-    makers = [_channel(awg, 10 + c, K, chirps=nc) for c, (K, nc) in
+def test_interleaved_channels_equal_their_own_renders(awg, oracle, n_ch):
+    makers = [_channel(awg, 10 + c, K, chirps=nc, oracle=oracle) for c, (K, nc) in
               enumerate([(100, 0), (700, 40), (37, 37), (2000, 10)][:n_ch])]
     n1, n2 = 70001, 50000
     chans = [m() for m in makers]
@@ -50,6 +61,8 @@ def test_interleaved_channels_equal_their_own_renders(awg, n_ch):
         torch.cuda.synchronize()
         assert np.array_equal(got[:, c], ref.cpu().numpy()), c
         assert chans[c].cursor == n1 + n2
+        dq = np.abs(got[:, c].astype(np.int32) - m.reference(n1 + n2).astype(np.int32))
+        assert dq.max() <= 1, (c, int(dq.max()))
 
 
 def test_multiplex_argument_errors(awg):

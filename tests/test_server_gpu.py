@@ -1,5 +1,8 @@
 """Served request stream: continuous batching, admission by deadline and memory, and results that
-do not depend on the co-runners (each request equals its standalone render bit for bit)."""
+do not depend on the co-runners.  Every served request is compared element by element with the
+CPU oracle (FP64 sum of Eq. dynamicandstatic, quantised in FP64: int16 within 1 LSB) and with its
+standalone render (bit for bit: alone and in the mix give the same samples)."""
+import os
 import time
 
 import numpy as np
@@ -7,6 +10,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+NTHREADS = os.cpu_count() or 1
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +46,23 @@ def _standalone(awg, fs, req):
     return out.cpu().numpy()
 
 
-def test_results_same_alone_and_in_the_mix(awg):
+def _oracle_codes(oracle, fs, req):
+    """The oracle's int16 codes for the whole request (its chunks back to back from sample 0; chirp
+    start samples are relative to the request's first sample; full scale sum |A|)."""
+    f, a, th, chirps, chunk, n_chunks = req
+    w = oracle.make_waveform(fs, f, a, th, chirps)
+    return oracle.quantize(oracle.render(w, 0, chunk * n_chunks, nthreads=NTHREADS), w.full_scale())
+
+
+def _check_against_oracle(oracle, fs, req, got):
+    q_ref = _oracle_codes(oracle, fs, req)
+    dq = np.abs(got.astype(np.int32) - q_ref.astype(np.int32))
+    assert got.shape == q_ref.shape
+    assert dq.max() <= 1, (int(dq.max()), int(np.argmax(dq)))
+    return float(np.mean(dq == 0))
+
+
+def test_results_same_alone_and_in_the_mix(awg, oracle):
     fs = 20e6     # long playback periods: every request is admitted
     reqs = [_request(i, fs, K, chunk, 4, nc) for i, (K, chunk, nc) in
             enumerate([(50, 1 << 16, 10), (700, 1 << 17, 40), (3000, 1 << 16, 100), (129, 70000, 5),
@@ -61,6 +82,32 @@ def test_results_same_alone_and_in_the_mix(awg):
         assert state == awg.binding.REQ_DONE and done == r[5]
         got = srv.read(rid, r[4] * r[5])
         assert np.array_equal(got, _standalone(awg, fs, r)), rid
+        _check_against_oracle(oracle, fs, r, got)
+        srv.release(rid)
+    srv.close()
+
+
+def test_two_split_sizes_in_one_round_match_the_oracle(awg, oracle):
+    """A 10,000-tone request (tone split 16) and a 16-tone request (split 1) run side by side.  The
+    short request's 0.8 ms chunks keep rounds short, so the long request's 2^19-sample chunks are
+    cut into tile pieces that share rounds with the short one's chunks: such a round launches the
+    batched render once per split size.  Both requests' samples equal the oracle's within 1 LSB
+    and their standalone renders bit for bit."""
+    fs = 20e6
+    reqs = [_request(21, fs, 10000, 1 << 19, 2, 100), _request(22, fs, 16, 1 << 14, 48, 16)]
+    srv = awg.Server(fs, 8 << 30, 64)
+    ids = []
+    for r in reqs:
+        ids.append(srv.submit(r[0], r[1], r[2], r[4], r[5], r[3]))
+        time.sleep(0.002)
+    srv.drain(60000)
+    st = srv.stats()
+    assert st["admitted"] == 2 and st["completed"] == 2, st
+    assert st["max_batch"] >= 2, st          # a round held pieces of both requests
+    for rid, r in zip(ids, reqs):
+        got = srv.read(rid, r[4] * r[5])
+        assert np.array_equal(got, _standalone(awg, fs, r)), rid
+        _check_against_oracle(oracle, fs, r, got)
         srv.release(rid)
     srv.close()
 
@@ -91,7 +138,7 @@ def test_admission_by_memory(awg):
     srv.close()
 
 
-def test_chunks_cut_into_tile_pieces_match_standalone(awg):
+def test_chunks_cut_into_tile_pieces_match_standalone(awg, oracle):
     """At 280 MS/s a 2^16-sample chunk plays for 234 us, so rounds stay short and the 2^20-sample
     chunks of a 1500-tone request are rendered in many tile-aligned pieces; the samples still equal
     a standalone render of each request."""
@@ -108,5 +155,6 @@ def test_chunks_cut_into_tile_pieces_match_standalone(awg):
     for rid, r in zip(ids, reqs):
         got = srv.read(rid, r[4] * r[5])
         assert np.array_equal(got, _standalone(awg, fs, r)), rid
+        _check_against_oracle(oracle, fs, r, got)
         srv.release(rid)
     srv.close()
