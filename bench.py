@@ -209,7 +209,7 @@ def stream_leg(awg, fs: float, stream, seconds: float = 1.0, n_slots: int = 4, p
 
 
 def chirping_leg(awg, stream, K: int, fs: float = 280e6, chunk: int = 1 << 20, segments: int = 7,
-                 n_slots: int = 6, prefill: int = 3):
+                 n_slots: int = 3, prefill: int = 2):
     """K tones that all chirp all the time (back-to-back 33.7 ms linear / minimum-jerk chirps between
     seeded 80-180 MHz frequencies), streamed in real time through the pinned ring with a host sink
     playing one chunk per chunk / fs: underruns and chunk latency (GPU completion minus push)
@@ -245,7 +245,17 @@ def chirping_leg(awg, stream, K: int, fs: float = 280e6, chunk: int = 1 << 20, s
         torch.cuda.synchronize()
         if r:
             ts.append(e0.elapsed_time(e1))
+    # one chunk at a time on an otherwise idle device: set-up + render of each chunk (library events)
+    o1 = torch.empty(chunk, dtype=torch.int16, device="cuda")
+    synth.profile_begin()
+    synth.seek(0)
+    for _ in range(min(16, S // chunk)):
+        synth.render(chunk, o1, stream)
+    torch.cuda.synchronize()
+    prep, rend, _ = synth.profile_end()
     synth.close()
+    import numpy as np
+    iso = np.asarray(prep) + np.asarray(rend)
     ms = min(ts)
     playback = 1e3 * chunk / fs
     return {"tones": K, "chirping": K, "fs_hz": fs, "chunk": chunk, "chunks": int(st["played"]),
@@ -253,6 +263,7 @@ def chirping_leg(awg, stream, K: int, fs: float = 280e6, chunk: int = 1 << 20, s
             "chunk_latency_ms": {"p50": st["latency_p50_ms"], "p99": st["latency_p99_ms"], "max": st["latency_max_ms"]},
             "p99_within_playback": bool(st["latency_p99_ms"] < playback), "min_lead_ms": st["lead_min_ms"],
             "required_tone_samples_per_s": K * fs, "stream_wall_s": wall, "device_status": status,
+            "isolated_chunk_latency_ms": {"p50": float(np.percentile(iso, 50)), "p99": float(np.percentile(iso, 99))},
             "device_segment_ms": ms, "device_tone_samples_per_s": K * S / (ms * 1e-3),
             "device_realtime_factor": (S / fs * 1e3) / ms,
             "slots": n_slots, "prefill": prefill, "segment_samples": S}
@@ -467,17 +478,51 @@ def periodic_leg(awg, stream, reps: int = 5):
             "write_gbs": gbs, "frac_of_hbm": gbs / peaks["hbm_gbs"], "peak_source": f"{src} hbm {peaks['hbm_gbs']} GB/s"}
 
 
-def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, capacity: float = 2.5e12):
+def late_chunk_breakdown(srv):
+    """Where the time of each late chunk went: release -> planning of the round that completed it
+    (host), planning -> device start (queue), device start -> done; medians over the late chunks,
+    and the same for all chunks c >= 1."""
+    import numpy as np
+    rounds, chunks = srv.trace_rounds(), srv.trace_chunks()
+    if len(rounds) == 0 or len(chunks) == 0:
+        return {}
+    by_done = {float(r["t_done"]): r for r in rounds}
+
+    def parts(sel):
+        rows = []
+        for c in sel:
+            r = by_done.get(float(c["done"]))
+            if r is None:
+                continue
+            rows.append((1e3 * (r["t_plan"] - c["release"]), 1e3 * (r["t_start"] - r["t_plan"]),
+                         1e3 * (r["t_done"] - r["t_start"]), 1e3 * (c["due"] - c["release"]), r["work"], r["pieces"]))
+        if not rows:
+            return {"n": 0}
+        a = np.array(rows, dtype=np.float64)
+        return {"n": len(rows), "release_to_plan_ms": float(np.median(a[:, 0])), "plan_to_start_ms": float(np.median(a[:, 1])),
+                "start_to_done_ms": float(np.median(a[:, 2])), "period_ms": float(np.median(a[:, 3])),
+                "round_work": float(np.median(a[:, 4])), "round_pieces": float(np.median(a[:, 5])),
+                "max_release_to_plan_ms": float(a[:, 0].max()), "max_plan_to_start_ms": float(a[:, 1].max()),
+                "max_start_to_done_ms": float(a[:, 2].max())}
+    later = chunks[chunks["chunk"] >= 1]
+    return {"late": parts(later[later["late"] != 0]), "all": parts(later)}
+
+
+def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, prefetch: int = 2):
     """Served rearrangement stream: Poisson arrivals of requests (50-10,000 tones, up to 100 chirping
     over 0.1-2 ms, 8 chunks of 2^16-2^20 samples) at rho x capacity / mean request work, submitted in
-    real time; admission by memory and deadline; continuous batching."""
+    real time; admission by memory and deadline; continuous batching.  capacity is the server's own
+    calibration of this GPU (static tone-samples per second of a busy device, the direct render
+    path); each chunk may be rendered `prefetch` chunk periods before it is due."""
     import math
     from paper_2403_15582_gb300 import workloads as wl
+    srv = awg.Server(fs, 16 << 30, 256)
+    srv.set_prefetch(prefetch)
+    capacity = srv.stats()["est_throughput"]
     mean_K = (10000 - 50) / math.log(10000 / 50)
     mean_chunk = sum(1 << e for e in range(16, 21)) / 5
     rate = rho * capacity / (mean_K * mean_chunk * 8)
     reqs = wl.served_requests(seed=0, rate_hz=rate, seconds=seconds, fs=fs)
-    srv = awg.Server(fs, 16 << 30, 256)
     t0 = time.perf_counter()
     ids = []
     for r in reqs:
@@ -487,10 +532,12 @@ def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, c
         ids.append(srv.submit(r.freq_hz, r.amp, r.phase_rad, r.chunk, r.n_chunks, r.chirps))
     srv.drain(120000)
     st = srv.stats()
+    late = late_chunk_breakdown(srv)
     for rid in ids:
         srv.release(rid)
     srv.close()
-    return {"fs_hz": fs, "rho": rho, "assumed_capacity": capacity, "arrival_rate_hz": rate, "seconds": seconds,
+    return {"fs_hz": fs, "rho": rho, "capacity": capacity, "prefetch_chunks": prefetch, "arrival_rate_hz": rate,
+            "seconds": seconds, "served_over_capacity": st["tone_samples_per_s"] / capacity,
             "requests": st["submitted"], "admitted": st["admitted"], "rejected_deadline": st["rejected_deadline"],
             "rejected_memory": st["rejected_memory"], "completed": st["completed"], "chunks": st["chunks"],
             "deadline_misses": st["deadline_misses"],
@@ -500,7 +547,8 @@ def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, c
             "samples_per_s": st["samples_per_s"], "tone_samples_per_s": st["tone_samples_per_s"],
             "mean_batch": st["mean_batch"], "max_batch": st["max_batch"], "rounds": st["rounds"], "busy_fraction": st["busy_fraction"],
             "est_throughput": st["est_throughput"],
-            "est_round_cost_ms": st["est_round_cost_ms"], "est_cta_rate": st["est_cta_rate"]}
+            "est_round_cost_ms": st["est_round_cost_ms"], "est_cta_rate": st["est_cta_rate"],
+            "late_chunks": late}
 
 
 def config(wk, args):

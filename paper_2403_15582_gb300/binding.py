@@ -39,6 +39,7 @@ SIGNATURES = [
     ("awg_table_gemm", ctypes.c_int, [P, i32, i32, P, P, P]),
     ("awg_server_create", P, [dbl, i64, i32, dbl]),
     ("awg_server_destroy", None, [P]),
+    ("awg_server_set_prefetch", ctypes.c_int, [P, i32]),
     ("awg_server_submit", i64, [P, P]),
     ("awg_server_poll", ctypes.c_int, [P, i64, P, P]),
     ("awg_server_read", ctypes.c_int, [P, i64, P, i64]),
@@ -441,6 +442,9 @@ class Server:
             self.close()
         except Exception:
             pass
+
+    def set_prefetch(self, chunks: int):
+        _check(lib().awg_server_set_prefetch(self._s, int(chunks)))
 
     def submit(self, freq_hz, amp, phase_rad, chunk: int, n_chunks: int, chirps=(), full_scale: float = 0.0) -> int:
         f, a, th = _f64(freq_hz), _f64(amp), _f64(phase_rad)

@@ -352,23 +352,29 @@ uint64_t chirp_offset_word(const W192 d[7], int64_t m) {
 
 // Chirps whose neglected 4th..6th-order phase terms over one 32-sample run could exceed 512 units
 // of 2^-32 turn (1.2e-7 turn) are rendered from a per-sample table of exact phases instead.
-// Whether the third unit difference of the chirp phase stays below 2^30 words over the whole
-// chirp, so that the render's run cascade rounds h to 0 in every run (TONE_FLAT3): by the mean
-// value theorem |Delta^3 P| <= max |P'''|, which is 5.77 |D| / L^2 for the minimum-jerk profile
-// (60 max |t - 3 t^2 + 2 t^3| = 5.77 over t in [0, 1]) and F_max |e^alpha - 1|^3 (1 + |e^alpha - 1|)
-// for the exponential one; linear chirps take their own path.
-bool flat_third_difference(uint64_t F0, uint64_t F1, int64_t L, int profile) {
+// Bound on |Delta^3 P| (words) over the whole chirp, or -1 for profiles without one (linear chirps
+// have Delta^3 P = 0 exactly and take their own path).  Minimum-jerk: by the mean value theorem
+// |Delta^3 P| <= max |P'''| = 5.77 |D| / L^2 (60 max |t - 3 t^2 + 2 t^3| = 5.77 over t in [0, 1]),
+// taken as 6 |D| / L^2.  Exponential: exactly Delta^3 R(m) = C e^(alpha m) q^3 with C = F_start /
+// alpha and q = e^alpha - 1, i.e. F(m) q^3 / alpha, at most F_max |q|^3 / |alpha| (1 + |q|)^3 over
+// the differences that reach past the end.
+double third_difference_bound(uint64_t F0, uint64_t F1, int64_t L, int profile) {
   const double l = (double)L;
-  double bound;
-  if (profile == AWG_PROFILE_MINJERK) {
-    bound = 6.0 * std::fabs((double)F1 - (double)F0) / (l * l);
-  } else if (profile == AWG_PROFILE_EXPONENTIAL && F0 != F1) {
-    const double q = std::fabs(exp_params(F0, F1, L).q);
-    bound = (double)std::max(F0, F1) * q * q * q * (1.0 + q) * 1.01;
-  } else {
-    return false;
+  if (profile == AWG_PROFILE_MINJERK) return 6.0 * std::fabs((double)F1 - (double)F0) / (l * l);
+  if (profile == AWG_PROFILE_EXPONENTIAL && F0 != F1) {
+    const ExpParams e = exp_params(F0, F1, L);
+    const double q = std::fabs(e.q), a = std::fabs(e.alpha);
+    return (double)std::max(F0, F1) * q * q * q / a * (1.0 + q) * (1.0 + q) * (1.0 + q) * 1.01;
   }
-  return bound < 1073741824.0;   // 2^30
+  return -1.0;
+}
+
+// Whether the third unit difference of the chirp phase stays below 2^30 words over the whole
+// chirp, so that the render's run cascade rounds h to 0 in every run (TONE_FLAT3).
+
+bool flat_third_difference(uint64_t F0, uint64_t F1, int64_t L, int profile) {
+  const double bound = third_difference_bound(F0, F1, L, profile);
+  return bound >= 0 && bound < 1073741824.0;   // 2^30
 }
 
 // Whether a TONE_FLAT3 chirp may also drop the stride-32 differences B_6, E_5 and G_2..G_4 of its
@@ -751,6 +757,16 @@ int upload_runs(T* dev, const std::vector<T>& host, const std::vector<int32_t>& 
   return AWG_OK;
 }
 
+// Largest |amplitude| any tone takes (its ramp target included), in FP32 as the kernels hold it.
+double max_amplitude(const awg_t* h) {
+  double m = 0;
+  for (const ToneRec& t : h->tones) {
+    m = std::max(m, (double)std::fabs(t.A));
+    if (t.flags & awgk::TONE_AMP_RAMP) m = std::max(m, (double)std::fabs(t.A_end));
+  }
+  return m;
+}
+
 double default_full_scale(const awg_t* h) {
   double s = 0;
   for (double a : h->amp) s += std::fabs(a);
@@ -1120,6 +1136,7 @@ int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
     t.out_q = all_static ? oq : nullptr;
     t.out_f = all_static ? of : h->d_base;
     t.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
+    t.a_scale = awgk::table_amp_scale(max_amplitude(h));
     t.status = h->d_status;
     cudaError_t e;
     if ((e = order_after_uploads(h, s)) != cudaSuccess) return cuda_fail(e, "upload ordering");
@@ -1996,6 +2013,7 @@ int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q
   t.out_q = out_q;
   t.out_f = out_f;
   t.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
+  t.a_scale = awgk::table_amp_scale(max_amplitude(h));
   t.status = h->d_status;
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};

@@ -7,14 +7,16 @@
 
 namespace awgk {
 
-// Work decomposition of the render kernel.  A thread owns RUN consecutive samples (one run)
-// and keeps their partial sums in registers; a CTA of NT threads owns one tile of TILE
-// consecutive samples; the tones of a tile are split over the CTAs of a thread-block cluster.
-// Runs and tiles are aligned to absolute sample indices, so a sample's value does not depend on
-// where a render window starts (chunk invariance).
+// Work decomposition of the render kernel.  A tile is TILE consecutive samples, cut into RUNS runs
+// of RUN samples (run index j, 0 <= j < RUNS: the unit of the chirp records' stride differences).
+// A render CTA of RT threads owns one tile; thread j owns run j and keeps its RUN partial sums in
+// registers; the tones of a tile are split over several CTAs.  Runs and tiles are aligned to
+// absolute sample indices, so a sample's value does not depend on where a render window starts
+// (chunk invariance).
 constexpr int RUN = 32;
-constexpr int NT = 128;
-constexpr int TILE = RUN * NT;     // 4096 samples
+constexpr int RUNS = 128;
+constexpr int TILE = RUN * RUNS;   // 4096 samples
+constexpr int RT = RUNS;           // threads per render CTA
 constexpr int STAGE = 32;          // tones staged in shared memory at a time (double-buffered)
 constexpr int SINE_SFU = 0;        // static segments: SFU sine of every sample's phase
 constexpr int SINE_ROTATOR = 1;    // static segments: exact sin/cos at the run start, then rotations
@@ -102,7 +104,7 @@ struct alignas(16) ChirpRec {
 static_assert(sizeof(ChirpRec) == 208, "ChirpRec layout");
 
 // Per (active chirp, tile) record: the chirp phase polynomial re-expressed at the tile start as
-// forward differences with stride RUN in the run index j (0 <= j < NT), for the phase and its
+// forward differences with stride RUN in the run index j (0 <= j < RUNS), for the phase and its
 // first three unit-stride differences.  Words (2^-64 turn), rounded.  B[0] is the phase word.
 struct alignas(16) TileRec {
   uint64_t B[7];
@@ -248,8 +250,14 @@ struct TableArgs2 {
   int16_t* out_q;
   float* out_f;
   float scale;
+  // power of two the A operand is multiplied by before its hi + lo split (the largest amplitude
+  // lands in [1, 2), so that the FP16 halves stay in the normal range), divided out exactly in
+  // the epilogue
+  float a_scale;
   int32_t* status;
 };
+// a_scale for amplitudes whose largest magnitude is amax (1 for amax 0)
+float table_amp_scale(double amax);
 size_t table_kp(int K);  // padded inner dimension (2K rounded up to the K tile)
 size_t table_kp_window(int K);   // the same for the static engine's 4 columns per tone
 cudaError_t launch_table_prep(const TableArgs2& t, cudaStream_t s);   // B operand halves

@@ -157,7 +157,7 @@ struct RunPoly {
   uint32_t p, f, g, h;
 };
 
-// C(j, q) for the run index j (0 <= j < NT = 128): q <= 5 fit in 32 bits, C(j, 6) needs 33.
+// C(j, q) for the run index j (0 <= j < RUNS = 128): q <= 5 fit in 32 bits, C(j, 6) needs 33.
 struct RunBin {
   uint32_t c1, c2, c3, c4, c5;
   uint64_t c6;
@@ -185,60 +185,120 @@ __device__ __forceinline__ uint64_t mac_u32(uint64_t acc, uint64_t x, uint32_t c
   return acc + lo + ((uint64_t)hi << 32);
 }
 
-__device__ __forceinline__ RunPoly pack_run(uint64_t p, uint64_t f, uint64_t g, uint64_t h);
+// The top 32 bits of a sum of 64-bit words times small integers, (sum_q x_q c_q mod 2^64) >> 32,
+// accumulated as a 64-bit sum of the low halves' products plus a 32-bit sum of the high halves'
+// products: S = 2^32 sum hi32(x_q) c_q + sum lo32(x_q) c_q, so bits 32..63 of S are the high sum
+// plus bits 32..63 of the low sum, whatever wraps above bit 63.  Two integer multiply-adds per
+// term; the same integers as the full 64-bit sum.
+struct Top32 {
+  uint64_t lo;
+  uint32_t hi;
+};
+// start from word x plus an offset (the rounding offsets P_OFFSET and HALF32)
+__device__ __forceinline__ Top32 top_init(uint64_t x, uint64_t off) {
+  return Top32{(uint64_t)(uint32_t)x + (uint32_t)off, (uint32_t)(x >> 32) + (uint32_t)(off >> 32)};
+}
+__device__ __forceinline__ void top_mac(Top32& t, uint64_t x, uint32_t c) {
+  t.lo += (uint64_t)(uint32_t)x * c;
+  t.hi += (uint32_t)(x >> 32) * c;
+}
+// x c mod 2^64 for a 64-bit c: lo32(x) lo32(c) + 2^32 (hi32(x) lo32(c) + lo32(x) hi32(c))
+__device__ __forceinline__ void top_mac64(Top32& t, uint64_t x, uint64_t c) {
+  t.lo += (uint64_t)(uint32_t)x * (uint32_t)c;
+  t.hi += (uint32_t)(x >> 32) * (uint32_t)c + (uint32_t)x * (uint32_t)(c >> 32);
+}
+__device__ __forceinline__ uint32_t top_get(const Top32& t) { return t.hi + (uint32_t)(t.lo >> 32); }
+
+constexpr uint64_t HALF32_OFF = 1ull << 31;
 
 // (p, f, g, h) at run j from the stride-RUN records: p = sum_q B_q C(j,q), f = sum_q E_q C(j,q),
-// g = sum_q G_q C(j,q), h = sum_q H_q C(j,q), all mod 2^64.
+// g = sum_q G_q C(j,q), h = sum_q H_q C(j,q), all mod 2^64, then to 32-bit fixed point: p with the
+// 2^8 offset of the sine argument (floor of (p + 2^40) / 2^32), f, g, h rounded to nearest.
 __device__ __forceinline__ RunPoly poly_state(const TileRec& rc, const RunBin& b, bool linear) {
+  RunPoly r;
   if (linear) {   // B_q (q >= 3), E_q (q >= 2), G_q (q >= 1) and H are exactly zero
-    uint64_t p = mac_u32(mac_u32(rc.B[0], rc.B[1], b.c1), rc.B[2], b.c2);
-    uint64_t f = mac_u32(rc.E[0], rc.E[1], b.c1);
-    return pack_run(p, f, rc.G[0], 0);
+    Top32 p = top_init(rc.B[0], 1ull << 40);
+    top_mac(p, rc.B[1], b.c1);
+    top_mac(p, rc.B[2], b.c2);
+    Top32 f = top_init(rc.E[0], HALF32_OFF);
+    top_mac(f, rc.E[1], b.c1);
+    r.p = top_get(p);
+    r.f = top_get(f);
+    r.g = (uint32_t)((rc.G[0] + HALF32_OFF) >> 32);
+    r.h = 0;
+    return r;
   }
-  uint64_t p = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.B[0], rc.B[1], b.c1), rc.B[2], b.c2), rc.B[3], b.c3), rc.B[4], b.c4),
-                       rc.B[5], b.c5) + rc.B[6] * b.c6;
-  asm volatile("" ::: "memory");   // evaluate the four polynomials one after another (registers)
-  uint64_t f = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.E[0], rc.E[1], b.c1), rc.E[2], b.c2), rc.E[3], b.c3), rc.E[4], b.c4),
-                       rc.E[5], b.c5);
-  asm volatile("" ::: "memory");
-  uint64_t g = mac_u32(mac_u32(mac_u32(mac_u32(rc.G[0], rc.G[1], b.c1), rc.G[2], b.c2), rc.G[3], b.c3), rc.G[4], b.c4);
-  asm volatile("" ::: "memory");
-  uint64_t h = mac_u32(mac_u32(mac_u32(rc.H[0], rc.H[1], b.c1), rc.H[2], b.c2), rc.H[3], b.c3);
-  return pack_run(p, f, g, h);
+  Top32 p = top_init(rc.B[0], 1ull << 40);
+  top_mac(p, rc.B[1], b.c1);
+  top_mac(p, rc.B[2], b.c2);
+  top_mac(p, rc.B[3], b.c3);
+  top_mac(p, rc.B[4], b.c4);
+  top_mac(p, rc.B[5], b.c5);
+  top_mac64(p, rc.B[6], b.c6);
+  Top32 f = top_init(rc.E[0], HALF32_OFF);
+  top_mac(f, rc.E[1], b.c1);
+  top_mac(f, rc.E[2], b.c2);
+  top_mac(f, rc.E[3], b.c3);
+  top_mac(f, rc.E[4], b.c4);
+  top_mac(f, rc.E[5], b.c5);
+  Top32 g = top_init(rc.G[0], HALF32_OFF);
+  top_mac(g, rc.G[1], b.c1);
+  top_mac(g, rc.G[2], b.c2);
+  top_mac(g, rc.G[3], b.c3);
+  top_mac(g, rc.G[4], b.c4);
+  Top32 h = top_init(rc.H[0], HALF32_OFF);
+  top_mac(h, rc.H[1], b.c1);
+  top_mac(h, rc.H[2], b.c2);
+  top_mac(h, rc.H[3], b.c3);
+  r.p = top_get(p);
+  r.f = top_get(f);
+  r.g = top_get(g);
+  r.h = top_get(h);
+  return r;
 }
 
 // poly_state for a degree-6 chirp whose h is known to round to 0 (TONE_FLAT3): no H polynomial.
 __device__ __forceinline__ RunPoly poly_state_flat3(const TileRec& rc, const RunBin& b) {
-  uint64_t p = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.B[0], rc.B[1], b.c1), rc.B[2], b.c2), rc.B[3], b.c3), rc.B[4], b.c4),
-                       rc.B[5], b.c5) + rc.B[6] * b.c6;
-  asm volatile("" ::: "memory");
-  uint64_t f = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.E[0], rc.E[1], b.c1), rc.E[2], b.c2), rc.E[3], b.c3), rc.E[4], b.c4),
-                       rc.E[5], b.c5);
-  asm volatile("" ::: "memory");
-  uint64_t g = mac_u32(mac_u32(mac_u32(mac_u32(rc.G[0], rc.G[1], b.c1), rc.G[2], b.c2), rc.G[3], b.c3), rc.G[4], b.c4);
-  return pack_run(p, f, g, 0);
+  Top32 p = top_init(rc.B[0], 1ull << 40);
+  top_mac(p, rc.B[1], b.c1);
+  top_mac(p, rc.B[2], b.c2);
+  top_mac(p, rc.B[3], b.c3);
+  top_mac(p, rc.B[4], b.c4);
+  top_mac(p, rc.B[5], b.c5);
+  top_mac64(p, rc.B[6], b.c6);
+  Top32 f = top_init(rc.E[0], HALF32_OFF);
+  top_mac(f, rc.E[1], b.c1);
+  top_mac(f, rc.E[2], b.c2);
+  top_mac(f, rc.E[3], b.c3);
+  top_mac(f, rc.E[4], b.c4);
+  top_mac(f, rc.E[5], b.c5);
+  Top32 g = top_init(rc.G[0], HALF32_OFF);
+  top_mac(g, rc.G[1], b.c1);
+  top_mac(g, rc.G[2], b.c2);
+  top_mac(g, rc.G[3], b.c3);
+  top_mac(g, rc.G[4], b.c4);
+  return RunPoly{top_get(p), top_get(f), top_get(g), 0u};
 }
 
 // poly_state for a TONE_LOW6 chirp: FLAT3, and the set-up bounds B_6, E_5 and G_2..G_4 below 64
 // units of 2^-32 turn of phase over a run, so they are left out.
 __device__ __forceinline__ RunPoly poly_state_low6(const TileRec& rc, const RunBin& b) {
-  uint64_t p = mac_u32(mac_u32(mac_u32(mac_u32(mac_u32(rc.B[0], rc.B[1], b.c1), rc.B[2], b.c2), rc.B[3], b.c3), rc.B[4], b.c4),
-                       rc.B[5], b.c5);
-  asm volatile("" ::: "memory");
-  uint64_t f = mac_u32(mac_u32(mac_u32(mac_u32(rc.E[0], rc.E[1], b.c1), rc.E[2], b.c2), rc.E[3], b.c3), rc.E[4], b.c4);
-  asm volatile("" ::: "memory");
-  uint64_t g = mac_u32(rc.G[0], rc.G[1], b.c1);
-  return pack_run(p, f, g, 0);
+  Top32 p = top_init(rc.B[0], 1ull << 40);
+  top_mac(p, rc.B[1], b.c1);
+  top_mac(p, rc.B[2], b.c2);
+  top_mac(p, rc.B[3], b.c3);
+  top_mac(p, rc.B[4], b.c4);
+  top_mac(p, rc.B[5], b.c5);
+  Top32 f = top_init(rc.E[0], HALF32_OFF);
+  top_mac(f, rc.E[1], b.c1);
+  top_mac(f, rc.E[2], b.c2);
+  top_mac(f, rc.E[3], b.c3);
+  top_mac(f, rc.E[4], b.c4);
+  Top32 g = top_init(rc.G[0], HALF32_OFF);
+  top_mac(g, rc.G[1], b.c1);
+  return RunPoly{top_get(p), top_get(f), top_get(g), 0u};
 }
 
-__device__ __forceinline__ RunPoly pack_run(uint64_t p, uint64_t f, uint64_t g, uint64_t h) {
-  RunPoly r;
-  r.p = (uint32_t)((p + P_OFFSET) >> 32);
-  r.f = (uint32_t)((f + HALF32) >> 32);
-  r.g = (uint32_t)((g + HALF32) >> 32);
-  r.h = (uint32_t)((h + HALF32) >> 32);
-  return r;
-}
 
 __device__ __forceinline__ uint32_t static_p0(uint64_t phi_ref, uint64_t F, int64_t n0) {
   return (uint32_t)((phi_ref + (uint64_t)n0 * F + P_OFFSET) >> 32);
@@ -253,27 +313,14 @@ __device__ __forceinline__ int classify_tile(const ToneRec& t, int64_t T0) {
   return TILE_CHIRP;
 }
 
-// The 32-bit phase the render feeds to the sine for sample r of run j (any segment).  The fast
-// loops below produce the same integers by stepping.
-__device__ __noinline__ uint32_t phase32_at(const ToneRec& t, const TileRec* rec, const ChirpRec* chirps, int64_t T0,
-                               int j, int r, const uint64_t (*inv)[3]) {
-  const int64_t n0 = T0 + (int64_t)j * RUN;
-  const int64_t n = n0 + r;
-  const uint32_t ur = (uint32_t)r;
-  if (t.slot < 0 || n < t.n_s) return static_p0(t.phi_ref, t.F, n0) + ur * static_f(t.F);
-  if (n > t.n_e) return static_p0(t.phi_post_ref, t.F_end, n0) + ur * static_f(t.F_end);
-  if (t.flags & TONE_EXACT) return (uint32_t)((exact_chirp_word(chirps[t.slot], n - t.n_s, inv) + P_OFFSET) >> 32);
-  RunPoly s = poly_state(*rec, run_binomials(j), (t.flags & TONE_LINEAR) != 0);
-  const uint32_t c2 = ur * (ur - 1) / 2, c3 = (r >= 3) ? ur * (ur - 1) * (ur - 2) / 6 : 0u;
-  return s.p + ur * s.f + c2 * s.g + c3 * s.h;
-}
-
 // sin(2 pi p / 2^32) for a phase already offset by half a turn (pc = p + 2^31): the top 23 bits
 // of pc become the mantissa of a float v in [1, 2); 2 pi (v - 3/2) lies in [-pi, pi) and is
 // congruent to the phase.  The half-turn offset is added once per run, not per sample.
 constexpr uint32_t HALF_TURN = 1u << 31;
+// The float 1.m with the 23-bit fraction m = pc >> 9 (exponent field of [1, 2)).
+__device__ __forceinline__ float mantissa_float(uint32_t pc) { return __uint_as_float((pc >> 9) + 0x3F800000u); }
 __device__ __forceinline__ float sin_centred(uint32_t pc) {
-  const float v = __uint_as_float((pc >> 9) + 0x3F800000u);
+  const float v = mantissa_float(pc);
   return __sinf(fmaf(v, 6.28318530717958647692f, -9.42477796076937971538f));
 }
 
@@ -489,7 +536,61 @@ __global__ void __launch_bounds__(128, 5) prep_kernel(const __grid_constant__ Pr
 // ------------------------------------------------------------------------------------------
 // render
 // ------------------------------------------------------------------------------------------
-// Per (tone, run) contribution of one staged tone, added into the thread's RUN partial sums.
+// Accumulators: a thread's RUN partial sums as RUN / 2 pairs of consecutive samples (float2).
+// The static loop computes the sine arguments and the multiply-adds of two samples as packed FP32
+// pairs (each component rounds as fmaf, so the sums are the same bits as with scalar fmaf); the
+// chirp loops stay scalar (there the packed form lowered the issue rate more than it saved).
+typedef float2 Acc[RUN / 2];
+
+constexpr float TWO_PI_F = 6.28318530717958647692f;
+constexpr float THREE_PI_F = 9.42477796076937971538f;
+
+// acc += (A0 sin(p0), A1 sin(p1)) for two phases already offset by half a turn (see sin_centred)
+__device__ __forceinline__ void acc_pair(float2& acc, float A0, float A1, uint32_t p0, uint32_t p1) {
+  acc.x = fmaf(A0, sin_centred(p0), acc.x);
+  acc.y = fmaf(A1, sin_centred(p1), acc.y);
+}
+// the same for one amplitude, as packed FP32 pairs
+__device__ __forceinline__ void acc_pair_packed(float2& acc, float A, uint32_t p0, uint32_t p1) {
+  const float2 v = make_float2(mantissa_float(p0), mantissa_float(p1));
+  const float2 x = __ffma2_rn(v, make_float2(TWO_PI_F, TWO_PI_F), make_float2(-THREE_PI_F, -THREE_PI_F));
+  acc = __ffma2_rn(make_float2(A, A), make_float2(__sinf(x.x), __sinf(x.y)), acc);
+}
+// acc += (A0 s0, A1 s1) for sines already computed
+__device__ __forceinline__ void acc_pair_s(float2& acc, float A0, float A1, float s0, float s1) {
+  acc.x = fmaf(A0, s0, acc.x);
+  acc.y = fmaf(A1, s1, acc.y);
+}
+
+// Static segment over N samples from acc pair B: p += f per sample.
+template <int B, int N>
+__device__ __forceinline__ void static_loop(uint32_t p, uint32_t f, float A, Acc& acc) {
+#pragma unroll
+  for (int r = 0; r < N; r += 2) {
+    const uint32_t p1 = p + f;
+    acc_pair_packed(acc[B + r / 2], A, p, p1);
+    p = p1 + f;
+  }
+}
+
+// Chirp cascade over N samples from acc pair B: p += f, f += g (and g += h with WITH_H).
+template <int B, int N, bool WITH_H>
+__device__ __forceinline__ void cascade(const RunPoly& q, float A, Acc& acc) {
+  uint32_t p = q.p + HALF_TURN, f = q.f, g = q.g;
+  const uint32_t h = q.h;
+#pragma unroll
+  for (int r = 0; r < N; r += 2) {
+    const uint32_t p1 = p + f;
+    uint32_t f1 = f + g;
+    if (WITH_H) g += h;
+    acc_pair(acc[B + r / 2], A, A, p, p1);
+    p = p1 + f1;
+    f = f1 + g;
+    if (WITH_H) g += h;
+  }
+}
+
+// Per (tone, run) contribution of one staged tone, added into the thread's partial sums.
 // Amplitude a(n) of a ramping tone (TONE_AMP_RAMP): A before a_ns, A_end from a_ns + a_L on, and
 // A + (A_end - A) s(tau) between, tau = (n - a_ns) / a_L, s linear or minimum-jerk
 // (10 tau^3 - 15 tau^4 + 6 tau^5).  FP32 (tau as m times the rounded 1 / a_L); error
@@ -522,8 +623,12 @@ __device__ __forceinline__ float ramp_amp_at(const RampRun& rr, int r) {
   return fmaf(rr.dA, s, rr.A);
 }
 
+// The general paths for the thread's run (samples n0 .. n0 + RUN - 1), used where a tile holds a
+// chirp boundary, an amplitude ramp or a per-sample phase table; col is the run's column of the
+// partial-sum buffer ([r][run], stride RUNS).
 __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, const RunBin& rb, float* col,
-                                         float (&acc)[RUN], int64_t T0, int64_t n0, const uint32_t* exact_tab) {
+                                         Acc& acc, int64_t T0, int64_t n0, const uint32_t* exact_tab) {
+  constexpr int B = 0;
   const bool ramp = (tr.flags & TONE_AMP_RAMP) != 0;
   const bool ramp_run = ramp && n0 + RUN - 1 > tr.a_ns && n0 < tr.a_ns + tr.a_L;   // a(n) varies in the run
   const float A = (ramp && n0 >= tr.a_ns + tr.a_L) ? tr.A_end : tr.A;
@@ -547,35 +652,13 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
     if (__all_sync(0xffffffffu, mode <= 1)) {
       const uint64_t phi = mode == 0 ? tr.phi_ref : tr.phi_post_ref;
       const uint64_t F = mode == 0 ? tr.F : tr.F_end;
-      uint32_t p = static_p0(phi, F, n0) + HALF_TURN;
-      const uint32_t f = static_f(F);
-#pragma unroll
-      for (int r = 0; r < RUN; ++r) {
-        acc[r] = fmaf(A, sin_centred(p), acc[r]);
-        p += f;
-      }
+      static_loop<B, RUN>(static_p0(phi, F, n0) + HALF_TURN, static_f(F), A, acc);
       return;
     }
     const RunPoly st = poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0);
-    uint32_t pp = st.p + HALF_TURN, ff = st.f, gg = st.g;
-    const uint32_t hh = st.h;
     if (__all_sync(0xffffffffu, mode == 2)) {
-      if (__all_sync(0xffffffffu, hh == 0)) {
-#pragma unroll
-        for (int r = 0; r < RUN; ++r) {
-          acc[r] = fmaf(A, sin_centred(pp), acc[r]);
-          pp += ff;
-          ff += gg;
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < RUN; ++r) {
-          acc[r] = fmaf(A, sin_centred(pp), acc[r]);
-          pp += ff;
-          ff += gg;
-          gg += hh;
-        }
-      }
+      if (__all_sync(0xffffffffu, st.h == 0)) cascade<B, RUN, false>(st, A, acc);
+      else cascade<B, RUN, true>(st, A, acc);
       return;
     }
     // a boundary in the warp: sample r takes the static phase before the chirp (r < i1), the
@@ -584,15 +667,23 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
     const int i2 = (int)max((int64_t)-1, min((int64_t)RUN, tr.n_e - n0));
     uint32_t qa = static_p0(tr.phi_ref, tr.F, n0) + HALF_TURN, qb = static_p0(tr.phi_post_ref, tr.F_end, n0) + HALF_TURN;
     const uint32_t fa = static_f(tr.F), fb = static_f(tr.F_end);
+    uint32_t pp = st.p + HALF_TURN, ff = st.f, gg = st.g;
+    const uint32_t hh = st.h;
 #pragma unroll
-    for (int r = 0; r < RUN; ++r) {
-      const uint32_t ph = r < i1 ? qa : (r > i2 ? qb : pp);
-      acc[r] = fmaf(A, sin_centred(ph), acc[r]);
+    for (int r = 0; r < RUN; r += 2) {
+      const uint32_t ph0 = r < i1 ? qa : (r > i2 ? qb : pp);
       qa += fa;
       qb += fb;
       pp += ff;
       ff += gg;
       gg += hh;
+      const uint32_t ph1 = r + 1 < i1 ? qa : (r + 1 > i2 ? qb : pp);
+      qa += fa;
+      qb += fb;
+      pp += ff;
+      ff += gg;
+      gg += hh;
+      acc_pair(acc[B + r / 2], A, A, ph0, ph1);
     }
     return;
   }
@@ -604,9 +695,9 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
     const uint32_t f = static_f(F);
     const RampRun rr = ramp_run_setup(tr, n0);
 #pragma unroll
-    for (int r = 0; r < RUN; ++r) {
-      acc[r] = fmaf(ramp_amp_at(rr, r), sin_centred(p), acc[r]);
-      p += f;
+    for (int r = 0; r < RUN; r += 2) {
+      acc_pair(acc[B + r / 2], ramp_amp_at(rr, r), ramp_amp_at(rr, r + 1), p, p + f);
+      p += 2 * f;
     }
   } else if (ramp_run) {
     mode = 3;
@@ -616,29 +707,14 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
   } else if (mode <= 1) {
     const uint64_t phi = mode == 0 ? tr.phi_ref : tr.phi_post_ref;
     const uint64_t F = mode == 0 ? tr.F : tr.F_end;
-    uint32_t p = static_p0(phi, F, n0) + HALF_TURN;
-    const uint32_t f = static_f(F);
-#pragma unroll
-    for (int r = 0; r < RUN; ++r) {
-      acc[r] = fmaf(A, sin_centred(p), acc[r]);
-      p += f;
-    }
+    static_loop<B, RUN>(static_p0(phi, F, n0) + HALF_TURN, static_f(F), A, acc);
     return;
   }
   if (mode == 2) {
-    const RunPoly st = poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0);
-    uint32_t p = st.p + HALF_TURN, f = st.f, g = st.g;
-    const uint32_t h = st.h;
-#pragma unroll
-    for (int r = 0; r < RUN; ++r) {
-      acc[r] = fmaf(A, sin_centred(p), acc[r]);
-      p += f;
-      f += g;
-      g += h;
-    }
+    cascade<B, RUN, true>(poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0), A, acc);
   } else {
     // a segment boundary inside this run, or a table chirp: choose the segment per sample; the
-    // sines go to the thread's column of the partial-sum buffer, then into the accumulators
+    // sines go to the run's column of the partial-sum buffer, then into the accumulators
     const uint32_t p_pre = static_p0(tr.phi_ref, tr.F, n0), f_pre = static_f(tr.F);
     const uint32_t p_post = static_p0(tr.phi_post_ref, tr.F_end, n0), f_post = static_f(tr.F_end);
     const bool exact = (tr.flags & TONE_EXACT) != 0;
@@ -651,7 +727,7 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
       if (r < r1) ph = p_pre + (uint32_t)r * f_pre;
       else if (r > r2) ph = p_post + (uint32_t)r * f_post;
       else ph = exact ? exact_tab[tr.tab_off + (int32_t)(r - r1)] : pp;
-      col[r * NT] = sin_centred(ph + HALF_TURN);
+      col[r * RUNS] = sin_centred(ph + HALF_TURN);
       pp += ff;
       ff += gg;
       gg += st.h;
@@ -659,10 +735,11 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
     if (ramp_run) {
       const RampRun rr = ramp_run_setup(tr, n0);
 #pragma unroll
-      for (int r = 0; r < RUN; ++r) acc[r] = fmaf(ramp_amp_at(rr, r), col[r * NT], acc[r]);
+      for (int r = 0; r < RUN; r += 2)
+        acc_pair_s(acc[B + r / 2], ramp_amp_at(rr, r), ramp_amp_at(rr, r + 1), col[r * RUNS], col[(r + 1) * RUNS]);
     } else {
 #pragma unroll
-      for (int r = 0; r < RUN; ++r) acc[r] = fmaf(A, col[r * NT], acc[r]);
+      for (int r = 0; r < RUN; r += 2) acc_pair_s(acc[B + r / 2], A, A, col[r * RUNS], col[(r + 1) * RUNS]);
     }
   }
 }
@@ -680,9 +757,13 @@ enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_
        DESC_FLAT3 = 6,     // FLAT3: a degree-6 chirp whose h is 0 in every run (TONE_FLAT3)
        DESC_LOW6 = 7 };    // LOW6: FLAT3 without the negligible high orders (TONE_LOW6)
 
+// Kind of a chirp tile that the chirp covers from start to end (no table, no ramp in the tile).
+__device__ __forceinline__ int chirp_inside_kind(int32_t flags) {
+  return (flags & TONE_LINEAR) ? DESC_LINEAR : (flags & TONE_LOW6) ? DESC_LOW6 : (flags & TONE_FLAT3) ? DESC_FLAT3 : DESC_MINJERK;
+}
 
-// Scale, round half to even, clamp and store sample T0 + sidx of a tile (inside the window),
-// after adding the tensor-core engine's static sum when there is one.
+// Scale, round half to even, clamp and store sample n (inside the window), after adding the
+// tensor-core engine's static sum when there is one.
 __device__ __forceinline__ void store_sample(const RenderArgs& a, int64_t n, float x) {
   if (n < a.win_start || n >= a.win_end) return;
   if (a.base) x += a.base[n - a.win_start];
@@ -692,42 +773,105 @@ __device__ __forceinline__ void store_sample(const RenderArgs& a, int64_t n, flo
   if (a.out_f) a.out_f[n - a.win_start] = x;
 }
 
-// Sum over the split without clusters.  Thread t holds samples 32 t .. 32 t + 31 of the tile in
-// acc.  With split 1 it stores them; otherwise the CTA writes them to its partial tile
+// Whether 8-sample groups (first sample a multiple of 8) of the int16 and FP32 outputs start on
+// 16-byte boundaries: sample n sits at out + (n - win_start), so this holds for every group at
+// once when out - win_start is 16-byte aligned.
+__device__ __forceinline__ bool q_vec_ok(const RenderArgs& a) {
+  return a.out_q && a.q_stride <= 1 && (((uintptr_t)a.out_q - 2u * (uint64_t)a.win_start) & 15u) == 0;
+}
+__device__ __forceinline__ bool f_vec_ok(const RenderArgs& a) {
+  return !a.out_f || (((uintptr_t)a.out_f - 4u * (uint64_t)a.win_start) & 15u) == 0;
+}
+
+// Store the 8 samples n .. n + 7 (n a multiple of 8): one 16-byte vector of int16 codes (and two
+// of FP32 sums) when the group lies inside the window and the outputs are aligned, else sample
+// by sample.
+__device__ __forceinline__ void store_group(const RenderArgs& a, int64_t n, const float (&xv)[8], bool vec) {
+  if (vec && n >= a.win_start && n + 8 <= a.win_end) {
+    const int64_t o = n - a.win_start;
+    float x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = a.base ? xv[u] + a.base[o + u] : xv[u];
+    uint32_t w[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float q0 = fminf(fmaxf(rintf(x[2 * u] * a.scale), -32767.f), 32767.f);
+      const float q1 = fminf(fmaxf(rintf(x[2 * u + 1] * a.scale), -32767.f), 32767.f);
+      w[u] = (uint32_t)(uint16_t)(int16_t)q0 | ((uint32_t)(uint16_t)(int16_t)q1 << 16);
+    }
+    if (a.out_q) *reinterpret_cast<uint4*>(a.out_q + o) = make_uint4(w[0], w[1], w[2], w[3]);
+    if (a.out_f) {
+      float4* f4 = reinterpret_cast<float4*>(a.out_f + o);
+      f4[0] = make_float4(x[0], x[1], x[2], x[3]);
+      f4[1] = make_float4(x[4], x[5], x[6], x[7]);
+    }
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) store_sample(a, n + u, xv[u]);
+}
+
+// Sum over the split without clusters.  Thread t holds samples RUN t .. RUN t + RUN - 1 of the
+// tile in acc.  With split 1 it stores them; otherwise the CTA writes them to its partial tile
 // a.part[(tile split + crank) TILE ...] and counts itself in on a.tile_ctr[tile]; the CTA that
 // brings the count to split - 1 (mod split) is the last of the tile: it sums the split's partials
-// in rank order (as the cluster reduction does: the same FP32 sums) and stores all 4096 samples.
+// in rank order (as the cluster reduction does: the same FP32 sums) and stores all 4096 samples,
+// thread t taking the 8-sample groups t, t + RT, ... (coalesced 16-byte stores).
 // In a pipelined sequence (pdl 2) the scratch of this launch was used two launches back: waiting
 // for the preceding launch to complete (which waited for the one before) makes it free.
 __device__ __forceinline__ void tile_epilogue_split(const RenderArgs& a, int tile, int crank, int split, int64_t T0,
-                                                 const float (&acc)[RUN]) {
+                                                    const Acc& acc) {
   const int tid = threadIdx.x;
   __shared__ int s_last;
+  const bool vec = q_vec_ok(a) && f_vec_ok(a);
   if (split == 1) {
 #pragma unroll
-    for (int u = 0; u < RUN; ++u) store_sample(a, T0 + tid * RUN + u, 0.f + acc[u]);
+    for (int g = 0; g < RUN / 8; ++g) {
+      float xv[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xv[2 * u] = 0.f + acc[4 * g + u].x;
+        xv[2 * u + 1] = 0.f + acc[4 * g + u].y;
+      }
+      store_group(a, T0 + (int64_t)tid * RUN + 8 * g, xv, vec);
+    }
   } else {
     if (a.pdl == 2) pdl_wait();
     float4* dst = reinterpret_cast<float4*>(a.part + ((int64_t)tile * split + crank) * TILE + tid * RUN);
 #pragma unroll
-    for (int j = 0; j < RUN / 4; ++j) __stcg(dst + j, make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]));
+    for (int j = 0; j < RUN / 4; ++j)
+      __stcg(dst + j, make_float4(acc[2 * j].x, acc[2 * j].y, acc[2 * j + 1].x, acc[2 * j + 1].y));
     __threadfence();
     __syncthreads();
     if (tid == 0) s_last = atomicAdd(&a.tile_ctr[tile], 1ull) % (unsigned long long)split == (unsigned long long)(split - 1);
     __syncthreads();
     if (s_last) {
       __threadfence();
-      // rank by rank, 32 independent loads per thread in flight (sample u NT + tid)
-      const float* src = a.part + (int64_t)tile * split * TILE + tid;
-      float xs[RUN];
+      // rank by rank, the thread's 8-sample groups tid + RT v, 16-byte loads in flight
+      constexpr int G = TILE / 8 / RT;   // 8-sample groups per thread
+      const float4* src = reinterpret_cast<const float4*>(a.part + (int64_t)tile * split * TILE) + 2 * tid;
+      float xs[G][8];
 #pragma unroll
-      for (int u = 0; u < RUN; ++u) xs[u] = 0.f;
+      for (int v = 0; v < G; ++v)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xs[v][u] = 0.f;
       for (int c = 0; c < split; ++c) {
 #pragma unroll
-        for (int u = 0; u < RUN; ++u) xs[u] += __ldcg(src + (int64_t)c * TILE + u * NT);
+        for (int v = 0; v < G; ++v) {
+          const float4 lo = __ldcg(src + (int64_t)c * (TILE / 4) + 2 * RT * v);
+          const float4 hi = __ldcg(src + (int64_t)c * (TILE / 4) + 2 * RT * v + 1);
+          xs[v][0] += lo.x;
+          xs[v][1] += lo.y;
+          xs[v][2] += lo.z;
+          xs[v][3] += lo.w;
+          xs[v][4] += hi.x;
+          xs[v][5] += hi.y;
+          xs[v][6] += hi.z;
+          xs[v][7] += hi.w;
+        }
       }
 #pragma unroll
-      for (int u = 0; u < RUN; ++u) store_sample(a, T0 + u * NT + tid, xs[u]);
+      for (int v = 0; v < G; ++v) store_group(a, T0 + 8 * ((int64_t)tid + RT * v), xs[v], vec);
     }
   }
   if (a.exit_ctr) {   // this CTA's samples (if any) are stored and visible
@@ -748,13 +892,13 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   __shared__ alignas(16) ToneRec s_tone[2][STAGE];
   __shared__ alignas(16) TileRec s_rec[2][STAGE];
   __shared__ alignas(16) Desc s_desc[2][STAGE];
-  __shared__ alignas(16) float s_red[RUN * NT];   // partial sums, [r][thread]
+  __shared__ alignas(16) float s_red[TILE];       // general paths: [r][run]; cluster sums: [i][thread]
   __shared__ alignas(8) uint64_t s_bar[4];        // tones[0], tones[1], records[0], records[1]
 
   cg::cluster_group cluster = cg::this_cluster();
   const int tid = threadIdx.x;
   const int64_t T0 = (a.tile0 + tile) * (int64_t)TILE;
-  const int64_t n0 = T0 + (int64_t)tid * RUN;
+  const int64_t n0 = T0 + (int64_t)tid * RUN;       // the thread's run
   const uint32_t run_off = (uint32_t)(tid * RUN);
   // positions [l_begin, l_end) of the visit: the CTA's range of tones, or of the tone list
   int l_begin = (int)((int64_t)a.K * crank / split);
@@ -775,9 +919,9 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   }
   const int n_stages = (l_end - l_begin + STAGE - 1) / STAGE;
 
-  float acc[RUN];
+  Acc acc;
 #pragma unroll
-  for (int r = 0; r < RUN; ++r) acc[r] = 0.f;
+  for (int r = 0; r < RUN / 2; ++r) acc[r] = make_float2(0.f, 0.f);
 
   if (a.pdl == 1) {   // pipelined sequence: the records' set-up (the preceding kernel) is complete
     pdl_wait();         // before the next render may start (it relies on the same set-up)
@@ -839,12 +983,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
         d.F = 0;
         d.p0 = 0;
         const bool inside = T0 >= tr.n_s && T0 + TILE - 1 <= tr.n_e;
-        d.kind = (inside && !exact)
-                     ? ((tr.flags & TONE_LINEAR)  ? DESC_LINEAR
-                        : (tr.flags & TONE_LOW6)  ? DESC_LOW6
-                        : (tr.flags & TONE_FLAT3) ? DESC_FLAT3
-                                                  : DESC_MINJERK)
-                     : DESC_MIXED;
+        d.kind = (inside && !exact) ? chirp_inside_kind(tr.flags) : DESC_MIXED;
         if (!exact) {
           need = true;
           src = a.recs + (int64_t)a.act_of_slot[tr.slot] * (a.rec_stride ? a.rec_stride : a.n_tiles) + a.rec_tile0 + tile;
@@ -878,7 +1017,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     __syncthreads();   // stage-0 descriptors visible
   }
   int fail_stage = -1;
-  const RunBin rb = run_binomials(tid);
+  const RunBin rb0 = run_binomials(tid);
   for (int st = 0; st < n_stages; ++st) {
     const int b = st & 1;
     const uint32_t par = (uint32_t)((st >> 1) & 1);
@@ -896,73 +1035,37 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
         const float A = d.A;
         if (kind == DESC_SKIP) continue;
         if (kind == DESC_STATIC) {
-          uint32_t p = (uint32_t)((mac_u32(d.p0 + P_OFFSET, d.F, run_off)) >> 32) + HALF_TURN;
-          const uint32_t f = static_f(d.F);
-#pragma unroll
-          for (int r = 0; r < RUN; ++r) {
-            acc[r] = fmaf(A, sin_centred(p), acc[r]);
-            p += f;
-          }
+          static_loop<0, RUN>((uint32_t)((mac_u32(d.p0 + P_OFFSET, d.F, run_off)) >> 32) + HALF_TURN, static_f(d.F), A, acc);
         } else if (kind == DESC_STATIC_ROT) {
-          // exact phase word at the run start, SFU sine and cosine once, then 31 rotations by the
-          // per-sample step on the FP32 pipe (amplitude folded into the phasor)
+          // the exact phase word at the run start, SFU sine and cosine once, then 31 rotations by
+          // the per-sample step on the FP32 pipe (amplitude folded into the phasor)
+          const float c = d.c, s = d.s;
           const uint64_t w = d.p0 + (uint64_t)run_off * d.F;
           float sn, cs;
           __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
           float im = A * sn, re = A * cs;
-          const float c = d.c, s = d.s;
 #pragma unroll
           for (int r = 0; r < RUN; ++r) {
-            acc[r] += im;
+            if (r & 1) acc[r / 2].y += im;
+            else acc[r / 2].x += im;
             const float t = fmaf(re, c, -im * s);
             im = fmaf(re, s, im * c);
             re = t;
           }
         } else if (kind == DESC_LINEAR) {
-          const RunPoly q = poly_state(s_rec[b][i], rb, true);
-          uint32_t p = q.p + HALF_TURN, f = q.f;
-          const uint32_t g = q.g;
-#pragma unroll
-          for (int r = 0; r < RUN; ++r) {
-            acc[r] = fmaf(A, sin_centred(p), acc[r]);
-            p += f;
-            f += g;
-          }
+          cascade<0, RUN, false>(poly_state(s_rec[b][i], rb0, true), A, acc);
         } else if (kind == DESC_FLAT3 || kind == DESC_LOW6) {
           // the third difference rounds to 0 everywhere (set-up bound): g is constant over the run
-          const RunPoly q = kind == DESC_LOW6 ? poly_state_low6(s_rec[b][i], rb) : poly_state_flat3(s_rec[b][i], rb);
-          uint32_t p = q.p + HALF_TURN, f = q.f;
-          const uint32_t g = q.g;
-#pragma unroll
-          for (int r = 0; r < RUN; ++r) {
-            acc[r] = fmaf(A, sin_centred(p), acc[r]);
-            p += f;
-            f += g;
-          }
+          const TileRec& rc = s_rec[b][i];
+          cascade<0, RUN, false>(kind == DESC_LOW6 ? poly_state_low6(rc, rb0) : poly_state_flat3(rc, rb0), A, acc);
         } else if (kind == DESC_MINJERK) {
-          const RunPoly q = poly_state(s_rec[b][i], rb, false);
-          uint32_t p = q.p + HALF_TURN, f = q.f, g = q.g;
-          const uint32_t h = q.h;
-          if (__all_sync(0xffffffffu, h == 0)) {
-            // third difference below 2^-33 turn (long ramps): g is constant over the run, the
-            // same integers as the loop below
-#pragma unroll
-            for (int r = 0; r < RUN; ++r) {
-              acc[r] = fmaf(A, sin_centred(p), acc[r]);
-              p += f;
-              f += g;
-            }
-          } else {
-#pragma unroll
-            for (int r = 0; r < RUN; ++r) {
-              acc[r] = fmaf(A, sin_centred(p), acc[r]);
-              p += f;
-              f += g;
-              g += h;
-            }
-          }
+          // third difference below 2^-33 turn (long ramps): g is constant over the run, the same
+          // integers as the loop with h
+          const RunPoly q0 = poly_state(s_rec[b][i], rb0, false);
+          if (__all_sync(0xffffffffu, q0.h == 0)) cascade<0, RUN, false>(q0, A, acc);
+          else cascade<0, RUN, true>(q0, A, acc);
         } else {
-          tone_run(s_tone[b][i], &s_rec[b][i], rb, &s_red[tid], acc, T0, n0, a.exact_tab);
+          tone_run(s_tone[b][i], &s_rec[b][i], rb0, &s_red[tid], acc, T0, n0, a.exact_tab);
         }
       }
     }
@@ -987,14 +1090,18 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   if constexpr (!CLUSTER) {
     tile_epilogue_split(a, tile, crank, split, T0, acc);
   } else {
-    // partial sums -> shared memory ([r][thread]), then the cluster-wide sum in rank order
+    // partial sums -> shared memory ([i][thread], sample RUN thread + i), then the cluster-wide
+    // sum in rank order
 #pragma unroll
-    for (int r = 0; r < RUN; ++r) s_red[r * NT + tid] = acc[r];
+    for (int r = 0; r < RUN / 2; ++r) {
+      s_red[(2 * r) * RT + tid] = acc[r].x;
+      s_red[(2 * r + 1) * RT + tid] = acc[r].y;
+    }
     cluster.sync();
 
     // this CTA reduces and stores samples [lo, hi) of the tile; thread t takes `per` consecutive ones
     const int lo = (int)((int64_t)TILE * crank / split), hi = (int)((int64_t)TILE * (crank + 1) / split);
-    const int per = (hi - lo + NT - 1) / NT;
+    const int per = (hi - lo + RT - 1) / RT;
     const int s_first = lo + tid * per;
     float xs[RUN];
 #pragma unroll
@@ -1004,7 +1111,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
 #pragma unroll
       for (int u = 0; u < RUN; ++u) {
         const int sidx = s_first + u;
-        if (u < per && sidx < hi) xs[u] += rem[(sidx % RUN) * NT + sidx / RUN];
+        if (u < per && sidx < hi) xs[u] += rem[(sidx % RUN) * RT + sidx / RUN];
       }
     }
     cluster.sync();   // remote reads done before any CTA of the cluster exits
@@ -1013,16 +1120,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
 #pragma unroll
     for (int u = 0; u < RUN; ++u) {
       const int sidx = s_first + u;
-      if (u < per && sidx < hi) {
-        const int64_t n = T0 + sidx;
-        if (n >= a.win_start && n < a.win_end) {
-          if (a.base) xs[u] += a.base[n - a.win_start];
-          float q = rintf(xs[u] * a.scale);
-          q = fminf(fmaxf(q, -32767.f), 32767.f);
-          if (a.out_q) a.out_q[(n - a.win_start) * (a.q_stride ? a.q_stride : 1)] = (int16_t)q;
-          if (a.out_f) a.out_f[n - a.win_start] = xs[u];
-        }
-      }
+      if (u < per && sidx < hi) store_sample(a, T0 + sidx, xs[u]);
     }
     if (a.exit_ctr) {   // this CTA's samples are stored and visible
       __threadfence();
@@ -1032,13 +1130,15 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   }
 }
 
-__global__ void __launch_bounds__(NT, 5) render_kernel(const __grid_constant__ RenderArgs a) {
+// 96 registers: five CTAs of RT threads per SM
+#define AWG_RENDER_MIN_BLOCKS 5
+__global__ void __launch_bounds__(RT, AWG_RENDER_MIN_BLOCKS) render_kernel(const __grid_constant__ RenderArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   render_tile<true>(a, blockIdx.x / a.split, (int)cluster.block_rank(), a.split);
 }
 
 // The same without clusters (a.part set): CTA blockIdx.x takes rank blockIdx.x % split.
-__global__ void __launch_bounds__(NT, 5) render_split_kernel(const __grid_constant__ RenderArgs a) {
+__global__ void __launch_bounds__(RT, AWG_RENDER_MIN_BLOCKS) render_split_kernel(const __grid_constant__ RenderArgs a) {
   render_tile<false>(a, blockIdx.x / a.split, blockIdx.x % a.split, a.split);
 }
 
@@ -1046,10 +1146,36 @@ __global__ void __launch_bounds__(NT, 5) render_split_kernel(const __grid_consta
 // items[i].y of request items[i].x; every request of the launch has the same tone split.  The
 // split sums through each request's scratch (reqs[i].part and .tile_ctr, counters zero at
 // launch); CTA blockIdx.x takes rank blockIdx.x % split.
-__global__ void __launch_bounds__(NT, 5) render_batch_split_kernel(const RenderArgs* __restrict__ reqs,
-                                                                     const int2* __restrict__ items, int split) {
+__global__ void __launch_bounds__(RT, AWG_RENDER_MIN_BLOCKS) render_batch_split_kernel(const RenderArgs* __restrict__ reqs,
+                                                                                       const int2* __restrict__ items,
+                                                                                       int split) {
   const int2 it = items[blockIdx.x / split];
   render_tile<false>(reqs[it.x], it.y, (int)(blockIdx.x % split), split);
+}
+
+// The 32-bit phase the render feeds to the sine for sample s of the tile [T0, T0 + TILE) (any
+// segment), by the same integer steps as the render's loops: run j = s / RUN, sample r = s % RUN.
+__device__ __noinline__ uint32_t phase32_at(const ToneRec& t, const TileRec* rec, const ChirpRec* chirps, int64_t T0,
+                                            int s, const uint64_t (*inv)[3]) {
+  const int j = s / RUN, r = s % RUN;
+  const int64_t n0 = T0 + (int64_t)j * RUN, n = T0 + s;
+  const uint32_t ur = (uint32_t)r;
+  const uint32_t c2 = ur * (ur - 1) / 2, c3 = (r >= 3) ? ur * (ur - 1) * (ur - 2) / 6 : 0u;
+  if (t.slot < 0 || n < t.n_s) return static_p0(t.phi_ref, t.F, n0) + ur * static_f(t.F);
+  if (n > t.n_e) return static_p0(t.phi_post_ref, t.F_end, n0) + ur * static_f(t.F_end);
+  if (t.flags & TONE_EXACT) return (uint32_t)((exact_chirp_word(chirps[t.slot], n - t.n_s, inv) + P_OFFSET) >> 32);
+  const bool ramp_in_tile = (t.flags & TONE_AMP_RAMP) && T0 + TILE - 1 > t.a_ns && T0 < t.a_ns + t.a_L;
+  const bool inside = T0 >= t.n_s && T0 + TILE - 1 <= t.n_e;
+  const RunBin b = run_binomials(j);
+  RunPoly q;
+  if (!ramp_in_tile && inside) {   // the tile's kind decides the set-up (LOW6 leaves terms out)
+    const int kind = chirp_inside_kind(t.flags);
+    q = kind == DESC_LOW6 ? poly_state_low6(*rec, b)
+        : kind == DESC_FLAT3 ? poly_state_flat3(*rec, b) : poly_state(*rec, b, kind == DESC_LINEAR);
+  } else {
+    q = poly_state(*rec, b, (t.flags & TONE_LINEAR) != 0);
+  }
+  return q.p + ur * q.f + c2 * q.g + c3 * q.h;
 }
 
 // Exact phase words of the first n tones at one sample (test hook).
@@ -1073,13 +1199,11 @@ __global__ void trace_kernel(const __grid_constant__ TraceArgs a) {
   const int64_t n = a.n0 + i;
   const int64_t tile_abs = n / TILE;
   const int64_t T0 = tile_abs * TILE;
-  const int j = (int)((n - T0) / RUN);
-  const int r = (int)((n - T0) % RUN);
   const ToneRec t = a.tones[a.tone];
   const TileRec* rec = nullptr;
   if (classify_tile(t, T0) == TILE_CHIRP && !(t.flags & TONE_EXACT))
     rec = a.recs + (int64_t)a.act_of_slot[t.slot] * a.n_tiles + (tile_abs - a.tile0);
-  a.out[i] = phase32_at(t, rec, a.chirps, T0, j, r, a.inv_odd);
+  a.out[i] = phase32_at(t, rec, a.chirps, T0, (int)(n - T0), a.inv_odd);
 }
 
 }  // namespace
@@ -1104,7 +1228,7 @@ cudaError_t render_setup_attributes() {
 cudaError_t launch_render_batch_split(const RenderArgs* reqs, const int2* items, int n_items, int split,
                                       cudaStream_t s) {
   if (n_items == 0) return cudaSuccess;
-  render_batch_split_kernel<<<(unsigned)(n_items * split), NT, 0, s>>>(reqs, items, split);
+  render_batch_split_kernel<<<(unsigned)(n_items * split), RT, 0, s>>>(reqs, items, split);
   return cudaGetLastError();
 }
 
@@ -1175,7 +1299,7 @@ cudaError_t launch_render(const RenderArgs& a, cudaStream_t s) {
   if (a.n_tiles == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.n_tiles * a.split), 1, 1);
-  cfg.blockDim = dim3(NT, 1, 1);
+  cfg.blockDim = dim3(RT, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[2];

@@ -116,6 +116,7 @@ struct awg_server {
   double fs = 0;
   int64_t budget = 0;
   int32_t max_active = 0;
+  int32_t depth = 2;           // chunks rendered ahead of playback (awg_server_set_prefetch)
   double max_queue_s = 0;
   int device = 0;
   clk::time_point t0;
@@ -174,6 +175,15 @@ namespace {
 
 double now_s(const awg_server_t* s) { return std::chrono::duration<double>(clk::now() - s->t0).count(); }
 
+// Release and due time of chunk c >= 1 of a playing request (server clock): due when chunk c-1
+// ends playing, t_play + c period; released `depth` periods before that, but not before chunk 0
+// is complete (t_play).  With depth 1 a chunk is released when the one before starts playing
+// (double buffering); a deeper prefetch gives each chunk more time than one period.
+double chunk_due(const Request* r, int32_t c) { return r->t_play + (double)c * r->period; }
+double chunk_release(const awg_server_t* s, const Request* r, int32_t c) {
+  return r->t_play + (double)std::max(0, c - s->depth) * r->period;
+}
+
 size_t footprint(const Request* r) {
   const size_t tiles = (size_t)(r->chunk + 2 * awgk::TILE - 1) / awgk::TILE;
   return (size_t)r->f.size() * sizeof(awgk::ToneRec) + r->c_tone.size() * sizeof(awgk::ChirpRec) +
@@ -185,10 +195,13 @@ size_t footprint(const Request* r) {
 // about one horizon.
 double horizon(double min_period) { return std::min(2e-3, std::max(40e-6, min_period / 3.0)); }
 
-// Admission by the real-time budget (EDF density with release jitter): chunk i needs
-// C_i = K_i chunk_i / P of device time within its period T_i, of which the queue horizon H and the
-// round cost a_gpu are lost, so the set is accepted while sum C_i / (T_i - H - a_gpu) <= 0.85 and
-// one tile of the largest request fits in a horizon.  `extra` (may be null) is a candidate.
+// Admission by the real-time budget (EDF with release jitter): chunk i needs C_i = K_i chunk_i / P
+// of device time per period T_i and must be done within its window W_i = depth T_i - H - a_gpu -
+// 2 t_cta (released depth periods before its due time, less the queue horizon H, the round cost
+// a_gpu and twice the longest non-preemptible CTA).  The set is accepted while every window is
+// positive and sum C_i / min(T_i, W_i) <= 0.85 (the density test where windows are short, the
+// utilisation test where they exceed a period), and one tile of the largest request fits in a
+// horizon.
 bool fits_set(const awg_server_t* s, const std::vector<const Request*>& set) {
   double min_period = 1e30, kmax = 0, ctamax = 0, load = 0;
   for (const Request* q : set) {
@@ -204,9 +217,9 @@ bool fits_set(const awg_server_t* s, const std::vector<const Request*>& set) {
   const double t_cta = ctamax * awgk::TILE / s->r_cta * (1.0 + (RESIDENT - 1) * std::min(1.0, load));
   double density = 0;
   for (const Request* q : set) {
-    const double window = q->period - H - s->a_gpu - 2.0 * t_cta;
+    const double window = (double)s->depth * q->period - H - s->a_gpu - 2.0 * t_cta;
     if (window <= 0) return false;
-    density += q->weight * (double)q->chunk / s->P / window;
+    density += q->weight * (double)q->chunk / s->P / std::min(q->period, window);
   }
   return density <= 0.85 && kmax * awgk::TILE / s->P <= H;
 }
@@ -375,9 +388,8 @@ void admit(awg_server_t* s) {
 }
 
 // Earliest-deadline-first plan of one round at time `now`.  Chunk 0 of a request is released when
-// its set-up is done; it starts playback when it completes (t_play), and chunk c >= 1 is released
-// when chunk c-1 starts playing (t_play + (c-1) period) and due when chunk c-1 ends
-// (t_play + c period).  A round takes what fills the device's queue up to the horizon; a chunk
+// its set-up is done; it starts playback when it completes (t_play), and chunk c >= 1 is due when
+// chunk c-1 ends (t_play + c period) and released `depth` periods earlier (chunk_release).  A round takes what fills the device's queue up to the horizon; a chunk
 // that does not fit is cut into whole tiles and continued in later rounds.
 // Returns the earliest future release in *next_release.  Lock held.
 void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
@@ -398,8 +410,8 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
       due = r->t_ready + r->period;
     } else {
       if (r->t_play < 0) continue;   // chunk 0 still in flight
-      rel = r->t_play + (double)(c - 1) * r->period;
-      due = r->t_play + (double)c * r->period;
+      rel = chunk_release(s, r, c);
+      due = chunk_due(r, c);
     }
     if (rel <= now) cands.push_back({due, r});
     else *next_release = std::min(*next_release, rel);
@@ -587,11 +599,11 @@ void complete_round(awg_server_t* s) {
       cr.release = r->t_ready;
       cr.due = r->t_ready + r->period;
     } else {
-      const double rel = r->t_play + (double)(p.chunk - 1) * r->period;
+      const double rel = chunk_release(s, r, p.chunk);
       s->lat.push_back(t_chunk - rel);
       s->lat_frac.push_back((t_chunk - rel) / r->period);
       cr.release = rel;
-      cr.due = rel + r->period;
+      cr.due = chunk_due(r, p.chunk);
       cr.late = t_chunk > cr.due;
       if (cr.late) ++s->misses;
     }
@@ -786,6 +798,15 @@ awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes,
   s->sched = std::thread(sched_main, s);
   s->worker = std::thread(worker_main, s);
   return s;
+}
+
+int awg_server_set_prefetch(awg_server_t* s, int32_t chunks) {
+  if (!s) return awgk::set_error(AWG_EINVAL, "null server");
+  if (chunks < 1 || chunks > 16) return awgk::set_error(AWG_EINVAL, "prefetch depth must be 1 .. 16 chunks");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->all.empty()) return awgk::set_error(AWG_ESTATE, "prefetch depth is set before the first request");
+  s->depth = chunks;
+  return AWG_OK;
 }
 
 void awg_server_destroy(awg_server_t* s) {

@@ -31,6 +31,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 
 #include "awg_internal.h"
@@ -126,6 +127,7 @@ struct TableGemmArgs {
   int64_t row_base;      // absolute row of tile row 0 of tile 0
   int64_t win_start, win_end;
   int32_t window_mode;
+  float a_scale, inv_a_scale;   // A operand scaling (a power of two) and its inverse
 };
 
 template <typename T>
@@ -202,7 +204,8 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
     const uint64_t f8 = F << a.nb_log2;
     w = phi + (uint64_t)(a.row_base + (int64_t)row0 + g) * f8;
     step = f8 << 2;
-    amp = A;
+    amp = A * a.a_scale;
+    amp_end *= a.a_scale;
   }
   const uint32_t col = (uint32_t)(lane & 3) * 4u;
   const uint32_t chunk = (uint32_t)(lane >> 2);
@@ -356,7 +359,7 @@ __global__ void __launch_bounds__(192, 1)
           if (k < a.K) {
             phi = __ldg(&a.tones[k].phi_ref);
             F = __ldg(&a.tones[k].F);
-            A = __ldg(&a.tones[k].A);
+            A = __ldg(&a.tones[k].A) * a.a_scale;
           }
         }
         if (kb >= NSTAGE && !mbar_wait(empty0 + 8 * s, (uint32_t)(((kb / NSTAGE) - 1) & 1))) {
@@ -425,6 +428,7 @@ __global__ void __launch_bounds__(192, 1)
     const int row = r_lo + e / TN, col = e % TN;
     float x = 0.f;
     for (int c = 0; c < split; ++c) x += cluster.map_shared_rank(part, c)[row * PART_STRIDE + col];
+    x *= a.inv_a_scale;   // exact: a power of two
     const int64_t n = (a.row_base + row0 + row) * TN + col;   // absolute sample
     if (n < a.win_start || n >= a.win_end) continue;
     if (a.out_q) a.out_q[n - a.win_start] = (int16_t)fminf(fmaxf(rintf(x * a.scale), -32767.f), 32767.f);
@@ -506,6 +510,14 @@ cudaError_t encode_2d(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt,
 
 }  // namespace
 
+float table_amp_scale(double amax) {
+  if (!(amax > 0) || !std::isfinite(amax)) return 1.f;
+  int e = 0;
+  (void)std::frexp(amax, &e);                 // amax = m 2^e, m in [0.5, 1)
+  e = std::max(-100, std::min(100, e));
+  return (float)std::ldexp(1.0, 1 - e);      // amax a_scale in [1, 2)
+}
+
 size_t table_kp(int K) { return (((size_t)2 * K + TK - 1) / TK) * TK; }
 size_t table_kp_window(int K) { return (((size_t)4 * K + TK - 1) / TK) * TK; }
 
@@ -552,6 +564,8 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   ga.win_start = t.win_start;
   ga.win_end = t.win_end;
   ga.window_mode = t.window_mode;
+  ga.a_scale = t.a_scale > 0.f ? t.a_scale : 1.f;
+  ga.inv_a_scale = 1.f / ga.a_scale;
   // instruction descriptor: FP32 accumulate, A/B BF16 (1) or FP16 (0), both K-major, N/8, M/16
   const uint32_t fmt = bf16 ? 1u : 0u;
   ga.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);

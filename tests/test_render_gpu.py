@@ -118,8 +118,10 @@ def test_phase_words_long_chirps(awg, oracle):
 @pytest.mark.parametrize("dur_ms", [0.1, 0.5, 2.0, 35.0])
 def test_render_phase_cascade_within_bound(awg, oracle, dur_ms):
     """The 32-bit phases the kernel feeds to the sine stay within the stated bound of the exact
-    words: 2500 units of 2^-32 turn for minimum-jerk runs (g, h rounding over 31 steps), 300 for
-    linear, 20 for static segments."""
+    words: 2500 units of 2^-32 turn for minimum-jerk runs (g, h rounding over 31 steps of a
+    32-sample run; or, for a one-cascade 64-sample run, f and g rounding over 63 steps plus the
+    neglected third order, 31.5 + 976.5 + 512 + 64), 1100 for linear chirps (f and g rounding over
+    63 steps: 31.5 + 976.5), 40 for static segments (f rounding over 63 steps)."""
     fs = 280e6
     L = int(round(dur_ms * 1e-3 * fs))
     f = [90e6, 100e6, 120e6, 60e6]
@@ -135,7 +137,7 @@ def test_render_phase_cascade_within_bound(awg, oracle, dur_ms):
         n0 = max(n0, 0)
         cnt = 60000
         idx = np.arange(n0, n0 + cnt, dtype=np.int64)
-        for k, bound in ((0, 2500), (1, 300), (2, 2500), (3, 20)):
+        for k, bound in ((0, 2500), (1, 1100), (2, 2500), (3, 40)):
             got = s.render_phases(k, n0, cnt)
             words = oracle.phase_words_at(w, k, idx)
             ref = ((words.astype(object) + (1 << 40)) >> 32) % (1 << 32)

@@ -88,13 +88,14 @@ def test_results_same_alone_and_in_the_mix(awg, oracle):
 
 
 def test_two_split_sizes_in_one_round_match_the_oracle(awg, oracle):
-    """A 10,000-tone request (tone split 16) and a 16-tone request (split 1) run side by side.  The
-    short request's 0.8 ms chunks keep rounds short, so the long request's 2^19-sample chunks are
-    cut into tile pieces that share rounds with the short one's chunks: such a round launches the
-    batched render once per split size.  Both requests' samples equal the oracle's within 1 LSB
-    and their standalone renders bit for bit."""
+    """A 16-tone request (tone split 1) with 1.6 ms chunks starts first and keeps rounds short
+    (a third of its period); a 10,000-tone request (split 16) arriving while it plays has its
+    2^20-sample chunk cut into five tile pieces, issued over more than one period of the short
+    request, so a piece shares a round with a short chunk: such a round launches the batched
+    render once per split size.  Both requests' samples equal the oracle's within 1 LSB and their
+    standalone renders bit for bit."""
     fs = 20e6
-    reqs = [_request(21, fs, 10000, 1 << 19, 2, 100), _request(22, fs, 16, 1 << 14, 48, 16)]
+    reqs = [_request(22, fs, 16, 1 << 15, 48, 16), _request(21, fs, 10000, 1 << 20, 1, 100)]
     srv = awg.Server(fs, 8 << 30, 64)
     ids = []
     for r in reqs:
