@@ -43,7 +43,7 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one render launch of the timed
 # step (a 2^18-sample chunk of the 1000-chirp record), from one ncu capture of the render kernel as
 # it stands in this file's revision; None when the kernel has changed since that capture.
-RENDER_TRAFFIC_BYTES = None
+RENDER_TRAFFIC_BYTES = 11.58144e6
 RENDER_TRAFFIC_SOURCE = "ncu --set full capture of one render_split_kernel launch (2^18 samples, 1000 chirps)"
 
 CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
@@ -505,7 +505,10 @@ def late_chunk_breakdown(srv):
                 "max_release_to_plan_ms": float(a[:, 0].max()), "max_plan_to_start_ms": float(a[:, 1].max()),
                 "max_start_to_done_ms": float(a[:, 2].max())}
     later = chunks[chunks["chunk"] >= 1]
-    return {"late": parts(later[later["late"] != 0]), "all": parts(later)}
+    lead = 1e3 * (later["due"] - later["done"])   # time to spare at completion
+    return {"late": parts(later[later["late"] != 0]), "all": parts(later),
+            "lead_ms": {"min": float(lead.min()), "p01": float(np.percentile(lead, 1)), "p50": float(np.percentile(lead, 50))}
+            if len(lead) else {}}
 
 
 def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, prefetch: int = 2):

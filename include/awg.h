@@ -382,13 +382,14 @@ const int16_t* awg_ring_slot(const awg_ring_t* r, int32_t i);
  * Timing: chunk 0 is rendered as soon as the request is set up on the device; playback starts
  * when it is complete (t_play; its latency from submission is reported as the first-chunk time).
  * Chunk c >= 1 is due when chunk c-1 ends playing, t_play + c chunk/fs (a chunk completed after
- * that is a deadline miss: an underrun of the player), and is released for rendering `depth`
- * chunk periods before that, but not before t_play (awg_server_set_prefetch; default 2: a chunk
- * may be rendered while the two before it play, like a FIFO of two chunks ahead of the DAC).
+ * that is a deadline miss: an underrun of the player), and is released for rendering a look-ahead
+ * earlier -- `depth` chunk periods (awg_server_set_prefetch; default 2), and at least 1 ms -- but
+ * not before t_play: like a FIFO that holds the chunks ahead of the DAC.
  * Admission: a request is admitted while the device-memory budget and max_active allow and the
- * real-time budget holds with it: each chunk's window (depth periods less the queue horizon, the
- * round cost and twice the longest CTA that cannot be preempted) must be positive, and the set's
- * device time per period must stay below 85 % of the windows (a cost model fitted at creation).  A request that does not fit waits up to max_queue_ms (without blocking the requests
+ * real-time budget holds with it: each chunk's window (its look-ahead less the queue horizon, the
+ * round cost, twice the longest CTA that cannot be preempted and an allowance for the host's
+ * scheduling delay) must hold the chunk's own device time, and the set's device time per period
+ * must stay below 85 % of the windows (a cost model fitted at creation).  A request that does not fit waits up to max_queue_ms (without blocking the requests
  * behind it) and is then rejected; one that could never fit is rejected at once.
  * Rounds: the scheduler keeps two rounds in flight; each round takes the released chunks of all
  * active requests in earliest-deadline-first order, cuts the ones that do not fit the round's work
@@ -445,7 +446,8 @@ awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes,
                                 double max_queue_ms);
 
 /* Chunks rendered ahead of playback (1 .. 16, default 2): chunk c is released when chunk c - depth
- * starts playing.  Set before the first request; AWG_ESTATE after. */
+ * starts playing (or 1 ms before it is due, if that is earlier).  Set before the first request;
+ * AWG_ESTATE after. */
 int awg_server_set_prefetch(awg_server_t* s, int32_t chunks);
 
 /* Stop the scheduler, wait for in-flight work and free everything.  NULL is allowed. */

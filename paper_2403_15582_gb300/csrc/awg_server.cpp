@@ -72,6 +72,7 @@ struct Round {
   int set = 0;                 // staging buffers and events in use
   std::vector<Piece> pieces;
   double work = 0;             // tone-samples
+  double est_s = 0;            // estimated device time (round_time)
   double host_s = 0;           // host time to plan and issue
   awg_round_record_t rec{};
 };
@@ -151,7 +152,7 @@ struct awg_server {
   size_t cap_part[NSETS] = {}, cap_tctr[NSETS] = {};
   std::deque<Round> flight;
   int64_t round_seq = 0;
-  double queued_work = 0;      // tone-samples issued and not yet accounted complete
+  double queued_s = 0;         // estimated device time of the rounds issued and not yet complete
   double busy_end = -1;        // end of the device's current busy interval (server clock)
   // cost model (calibrated at creation): the device renders P static-tone samples/s when it is
   // kept busy (updated from busy rounds within [0.6, 1.2] of the calibration); a round costs a_gpu
@@ -176,12 +177,25 @@ namespace {
 double now_s(const awg_server_t* s) { return std::chrono::duration<double>(clk::now() - s->t0).count(); }
 
 // Release and due time of chunk c >= 1 of a playing request (server clock): due when chunk c-1
-// ends playing, t_play + c period; released `depth` periods before that, but not before chunk 0
-// is complete (t_play).  With depth 1 a chunk is released when the one before starts playing
-// (double buffering); a deeper prefetch gives each chunk more time than one period.
+// ends playing, t_play + c period; released a look-ahead earlier -- `depth` periods, and at least
+// MIN_LOOKAHEAD_S so that short chunks keep room for host and queue delays -- but not before
+// chunk 0 is complete (t_play).  With depth 1 and long chunks a chunk is released when the one
+// before starts playing (double buffering).
+constexpr double MIN_LOOKAHEAD_S = 1e-3;
+double lookahead(const awg_server_t* s, const Request* r) {
+  return std::max((double)s->depth * r->period, MIN_LOOKAHEAD_S);
+}
 double chunk_due(const Request* r, int32_t c) { return r->t_play + (double)c * r->period; }
 double chunk_release(const awg_server_t* s, const Request* r, int32_t c) {
-  return r->t_play + (double)std::max(0, c - s->depth) * r->period;
+  return std::max(r->t_play, chunk_due(r, c) - lookahead(s, r));
+}
+
+// Device time of one CTA of request r alone on an SM (its tones per CTA over the calibrated rate
+// of a lone CTA), and of a round: its fixed cost plus the larger of its work at the busy-device
+// rate and its longest CTA (a small round cannot spread over the device).
+double cta_time(const awg_server_t* s, const Request* r) { return r->cta_tones * awgk::TILE / s->r_cta; }
+double round_time(const awg_server_t* s, double work, double t_cta_max) {
+  return s->a_gpu + std::max(work / s->P, t_cta_max);
 }
 
 size_t footprint(const Request* r) {
@@ -196,12 +210,15 @@ size_t footprint(const Request* r) {
 double horizon(double min_period) { return std::min(2e-3, std::max(40e-6, min_period / 3.0)); }
 
 // Admission by the real-time budget (EDF with release jitter): chunk i needs C_i = K_i chunk_i / P
-// of device time per period T_i and must be done within its window W_i = depth T_i - H - a_gpu -
-// 2 t_cta (released depth periods before its due time, less the queue horizon H, the round cost
-// a_gpu and twice the longest non-preemptible CTA).  The set is accepted while every window is
-// positive and sum C_i / min(T_i, W_i) <= 0.85 (the density test where windows are short, the
+// of device time per period T_i and must be done within its window W_i = lookahead_i - H - a_gpu -
+// 2 t_cta - J (released a look-ahead before its due time, less the queue horizon H, the round
+// cost a_gpu, twice the longest non-preemptible CTA and the host's release jitter J), which must
+// also hold the chunk's own time alone (round_time).  The set is accepted while that holds for
+// every request and sum C_i / min(T_i, W_i) <= 0.85 (the density test where windows are short, the
 // utilisation test where they exceed a period), and one tile of the largest request fits in a
 // horizon.
+constexpr double HOST_JITTER_S = 150e-6;   // release-to-plan delay the host may add (scheduler wake-up)
+
 bool fits_set(const awg_server_t* s, const std::vector<const Request*>& set) {
   double min_period = 1e30, kmax = 0, ctamax = 0, load = 0;
   for (const Request* q : set) {
@@ -217,8 +234,8 @@ bool fits_set(const awg_server_t* s, const std::vector<const Request*>& set) {
   const double t_cta = ctamax * awgk::TILE / s->r_cta * (1.0 + (RESIDENT - 1) * std::min(1.0, load));
   double density = 0;
   for (const Request* q : set) {
-    const double window = (double)s->depth * q->period - H - s->a_gpu - 2.0 * t_cta;
-    if (window <= 0) return false;
+    const double window = lookahead(s, q) - H - s->a_gpu - 2.0 * t_cta - HOST_JITTER_S;
+    if (window <= round_time(s, q->weight * (double)q->chunk, cta_time(s, q))) return false;
     density += q->weight * (double)q->chunk / s->P / std::min(q->period, window);
   }
   return density <= 0.85 && kmax * awgk::TILE / s->P <= H;
@@ -419,7 +436,7 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
   if (cands.empty()) return;
   // work the device may take on now: fill the queue up to the horizon
   const double H = horizon(min_period);
-  const double queued = s->queued_work / s->P;
+  const double queued = s->queued_s;
   if (!s->flight.empty() && queued >= H) return;
   double w_left = std::max(0.5 * H, H - queued - s->a_gpu) * s->P;
   std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.due < y.due; });
@@ -429,6 +446,7 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
       rd->rec.first_due = cd.due;
       break;
     }
+  double t_cta_max = 0;
   for (const Cand& cd : cands) {
     if (w_left <= 0 && !rd->pieces.empty()) break;
     Request* r = cd.r;
@@ -441,6 +459,7 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
     }
     rd->pieces.push_back({r, r->issue_chunk, r->issue_off, take, take == remaining});
     rd->work += K * (double)take;
+    t_cta_max = std::max(t_cta_max, cta_time(s, r));
     w_left -= K * (double)take;
     r->issue_off += take;
     if (r->issue_off == r->chunk) {
@@ -448,6 +467,7 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
       ++r->issue_chunk;
     }
   }
+  rd->est_s = round_time(s, rd->work, t_cta_max);
 }
 
 // Issue a planned round on its set's stream (outside the lock: only this thread touches active
@@ -563,7 +583,7 @@ void complete_round(awg_server_t* s) {
   rd.rec.t_done = t_done;
   rd.rec.work = rd.work;
   s->trace_rounds.push(rd.rec);
-  s->queued_work = std::max(0.0, s->queued_work - rd.work);
+  s->queued_s = std::max(0.0, s->queued_s - rd.est_s);
   ++s->rounds;
   s->batched += (int64_t)rd.pieces.size();
   s->max_batch = std::max(s->max_batch, (int64_t)rd.pieces.size());
@@ -697,7 +717,7 @@ void sched_main(awg_server_t* s) {
       {
         std::lock_guard<std::mutex> lk(s->mu);
         plan_round(s, t_plan, &rd, &next_release);
-        s->queued_work += rd.work;
+        s->queued_s += rd.est_s;
       }
       if (!rd.pieces.empty()) {
         if (!issue_round(s, &rd)) {
