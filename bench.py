@@ -511,7 +511,8 @@ def late_chunk_breakdown(srv):
             if len(lead) else {}}
 
 
-def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, prefetch: int = 2):
+def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, prefetch: int = 2,
+               engine: int = 0, engine_min_tones: int = 1000):
     """Served rearrangement stream: Poisson arrivals of requests (50-10,000 tones, up to 100 chirping
     over 0.1-2 ms, 8 chunks of 2^16-2^20 samples) at rho x capacity / mean request work, submitted in
     real time; admission by memory and deadline; continuous batching.  capacity is the server's own
@@ -521,6 +522,8 @@ def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, p
     from paper_2403_15582_gb300 import workloads as wl
     srv = awg.Server(fs, 16 << 30, 256)
     srv.set_prefetch(prefetch)
+    if engine:
+        srv.set_static_engine(engine, engine_min_tones)
     capacity = srv.stats()["est_throughput"]
     mean_K = (10000 - 50) / math.log(10000 / 50)
     mean_chunk = sum(1 << e for e in range(16, 21)) / 5
@@ -539,7 +542,10 @@ def served_leg(awg, fs: float = 280e6, seconds: float = 2.0, rho: float = 0.8, p
     for rid in ids:
         srv.release(rid)
     srv.close()
-    return {"fs_hz": fs, "rho": rho, "capacity": capacity, "prefetch_chunks": prefetch, "arrival_rate_hz": rate,
+    return {"fs_hz": fs, "rho": rho, "capacity": capacity, "prefetch_chunks": prefetch,
+            "static_engine": ["direct", "gemm_fp16", "gemm_bf16"][engine],
+            "engine_min_tones": engine_min_tones if engine else None,
+            "engine_capacity": st["est_engine_throughput"] if engine else None, "arrival_rate_hz": rate,
             "seconds": seconds, "served_over_capacity": st["tone_samples_per_s"] / capacity,
             "requests": st["submitted"], "admitted": st["admitted"], "rejected_deadline": st["rejected_deadline"],
             "rejected_memory": st["rejected_memory"], "completed": st["completed"], "chunks": st["chunks"],
@@ -734,6 +740,9 @@ def main():
         line["table"] = table_leg(awg, stream, K=tk, log2_len=tl, gpu=local)
     if not args.no_served:
         line["served"] = {f"rho{r}": served_leg(awg, rho=r) for r in (0.5, 0.8, 1.0)}
+        # requests of >= 1000 tones on the tensor-core static engine, at the same and at twice the
+        # arrival rate (rho relative to the direct path's capacity)
+        line["served_engine"] = {f"rho{r}": served_leg(awg, rho=r, engine=awg.STATIC_GEMM_FP16) for r in (1.0, 2.0)}
     if not args.no_stream:
         line["stream"] = {f"{int(fs_/1e6)}MSps": stream_leg(awg, fs_, stream) for fs_ in (280e6, 50e6)}
         line["stream"]["280MSps_gemm"] = stream_leg(awg, 280e6, stream, engine=awg.STATIC_GEMM_FP16)

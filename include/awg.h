@@ -382,9 +382,9 @@ const int16_t* awg_ring_slot(const awg_ring_t* r, int32_t i);
  * Timing: chunk 0 is rendered as soon as the request is set up on the device; playback starts
  * when it is complete (t_play; its latency from submission is reported as the first-chunk time).
  * Chunk c >= 1 is due when chunk c-1 ends playing, t_play + c chunk/fs (a chunk completed after
- * that is a deadline miss: an underrun of the player), and is released for rendering a look-ahead
- * earlier -- `depth` chunk periods (awg_server_set_prefetch; default 2), and at least 1 ms -- but
- * not before t_play: like a FIFO that holds the chunks ahead of the DAC.
+ * that is a deadline miss: an underrun of the player), and is released for rendering `depth`
+ * chunk periods earlier (awg_server_set_prefetch; default 2), but not before t_play: like a FIFO
+ * that holds the chunks ahead of the DAC.
  * Admission: a request is admitted while the device-memory budget and max_active allow and the
  * real-time budget holds with it: each chunk's window (its look-ahead less the queue horizon, the
  * round cost, twice the longest CTA that cannot be preempted and an allowance for the host's
@@ -431,12 +431,13 @@ typedef struct {
   int64_t rounds;
   double mean_batch;                /* pieces (requests) per round */
   int64_t max_batch;
-  double tone_samples_per_s;        /* over the span from the first round to the last */
+  double tone_samples_per_s;        /* tones x samples rendered, over the span from the first round to the last */
   double samples_per_s;
   double busy_fraction;             /* device time of the rounds / that span */
   double est_throughput;            /* cost model: static-tone samples/s of a busy device */
   double est_round_cost_ms;         /* cost model: fixed device time of one round */
   double est_cta_rate;              /* cost model: tone-samples/s of one render CTA alone on an SM */
+  double est_engine_throughput;     /* cost model: static tone-samples/s of the tensor-core engine */
 } awg_server_stats_t;
 
 /* Server for sample rate fs on the current device, with a device-memory budget (bytes) for the
@@ -445,9 +446,16 @@ typedef struct {
 awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes, int32_t max_active,
                                 double max_queue_ms);
 
+/* Static tones of requests with at least min_tones tones on the tensor-core engine (engine
+ * AWG_STATIC_GEMM_FP16 or _BF16, as awg_set_static_engine): each piece's static tones are summed by
+ * the split-precision GEMM over the piece (within 1 LSB of the oracle, not bit-identical to the
+ * direct render), only the tones that chirp or ramp in it go through the batched render kernel.
+ * A served request equals a standalone render with the same engine bit for bit.  AWG_STATIC_DIRECT
+ * (the default) renders every tone directly.  Set before the first request; AWG_ESTATE after. */
+int awg_server_set_static_engine(awg_server_t* s, int32_t engine, int32_t min_tones);
+
 /* Chunks rendered ahead of playback (1 .. 16, default 2): chunk c is released when chunk c - depth
- * starts playing (or 1 ms before it is due, if that is earlier).  Set before the first request;
- * AWG_ESTATE after. */
+ * starts playing.  Set before the first request; AWG_ESTATE after. */
 int awg_server_set_prefetch(awg_server_t* s, int32_t chunks);
 
 /* Stop the scheduler, wait for in-flight work and free everything.  NULL is allowed. */

@@ -40,6 +40,7 @@ SIGNATURES = [
     ("awg_server_create", P, [dbl, i64, i32, dbl]),
     ("awg_server_destroy", None, [P]),
     ("awg_server_set_prefetch", ctypes.c_int, [P, i32]),
+    ("awg_server_set_static_engine", ctypes.c_int, [P, i32, i32]),
     ("awg_server_submit", i64, [P, P]),
     ("awg_server_poll", ctypes.c_int, [P, i64, P, P]),
     ("awg_server_read", ctypes.c_int, [P, i64, P, i64]),
@@ -415,7 +416,7 @@ class ServerStats(ctypes.Structure):
                 ("first_chunk_p50_ms", dbl),
                 ("first_chunk_p99_ms", dbl), ("rounds", i64), ("mean_batch", dbl), ("max_batch", i64),
                 ("tone_samples_per_s", dbl), ("samples_per_s", dbl), ("busy_fraction", dbl), ("est_throughput", dbl),
-                ("est_round_cost_ms", dbl), ("est_cta_rate", dbl)]
+                ("est_round_cost_ms", dbl), ("est_cta_rate", dbl), ("est_engine_throughput", dbl)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -445,6 +446,9 @@ class Server:
 
     def set_prefetch(self, chunks: int):
         _check(lib().awg_server_set_prefetch(self._s, int(chunks)))
+
+    def set_static_engine(self, engine: int, min_tones: int):
+        _check(lib().awg_server_set_static_engine(self._s, int(engine), int(min_tones)))
 
     def submit(self, freq_hz, amp, phase_rad, chunk: int, n_chunks: int, chirps=(), full_scale: float = 0.0) -> int:
         f, a, th = _f64(freq_hz), _f64(amp), _f64(phase_rad)

@@ -503,6 +503,11 @@ struct awg {
   int32_t* d_list = nullptr;           // tensor-core engine: tones not static in some tile of the window
   size_t cap_list = 0;
   std::vector<int32_t> list;
+  // tones that hold a chirp or an amplitude ramp, ascending (the static engine's render part);
+  // rebuilt on demand after tones, chirps or ramps change
+  std::vector<int32_t> flagged;
+  double amax = 0;                     // largest |amplitude| (ramp targets included), with `flagged`
+  bool flagged_ok = false;
   // periodic hand-off: from sample periodic_start on, x[n] = periodic table[n mod 2^periodic_log2]
   int16_t* d_periodic = nullptr;
   size_t cap_periodic = 0;
@@ -758,13 +763,18 @@ int upload_runs(T* dev, const std::vector<T>& host, const std::vector<int32_t>& 
 }
 
 // Largest |amplitude| any tone takes (its ramp target included), in FP32 as the kernels hold it.
-double max_amplitude(const awg_t* h) {
+double max_amplitude_scan(const awg_t* h) {
   double m = 0;
   for (const ToneRec& t : h->tones) {
     m = std::max(m, (double)std::fabs(t.A));
     if (t.flags & awgk::TONE_AMP_RAMP) m = std::max(m, (double)std::fabs(t.A_end));
   }
   return m;
+}
+const std::vector<int32_t>& flagged_tones(awg_t* h);
+double max_amplitude(awg_t* h) {
+  (void)flagged_tones(h);   // refreshes the cached maximum with the flagged tones
+  return h->amax;
 }
 
 double default_full_scale(const awg_t* h) {
@@ -808,6 +818,7 @@ int set_tones_common(awg_t* h, const double* f, const double* amp, const double*
   h->tones.swap(tones);
   h->amp.swap(a);
   h->K = n;
+  h->flagged_ok = false;
   h->periodic_start = -1;
   h->chirps.clear();
   h->free_slots.clear();
@@ -1066,44 +1077,99 @@ namespace {
 // chirp); the others by the render kernel, which skips the static ones and adds the GEMM's FP32
 // sum before quantising.  The split depends on the tile and the tone state only, so a sample's
 // value does not depend on how the stream is cut into calls.  Pieces of at most 2^26 samples.
+
+// The render part's tone split: the tones that hold a chirp or a ramp at all (they change only when
+// chirps, ramps or tones are set, never while rendering), about the same number of them in each of
+// the split's tone ranges.  With every tone holding one this is the plain split.
+struct EngineSplit {
+  int32_t n_flagged = 0, split = 1;
+  int32_t bounds[awgk::MAX_SPLIT + 1];
+};
+const std::vector<int32_t>& flagged_tones(awg_t* h) {
+  if (!h->flagged_ok) {
+    h->amax = max_amplitude_scan(h);
+    h->flagged.clear();
+    for (size_t k = 0; k < h->tones.size(); ++k)
+      if (h->tones[k].slot >= 0 || (h->tones[k].flags & awgk::TONE_AMP_RAMP)) h->flagged.push_back((int32_t)k);
+    h->flagged_ok = true;
+  }
+  return h->flagged;
+}
+EngineSplit engine_split(awg_t* h) {
+  EngineSplit es;
+  const std::vector<int32_t>& fl = flagged_tones(h);
+  es.n_flagged = (int32_t)fl.size();
+  es.split = awgk::tone_split_for(es.n_flagged);
+  es.bounds[0] = 0;
+  es.bounds[es.split] = h->K;
+  // range r starts at the flagged tone at position floor(n_flagged r / split)
+  for (int32_t r = 1; r < es.split; ++r) es.bounds[r] = fl[(size_t)((int64_t)es.n_flagged * r / es.split)];
+  return es;
+}
+
+// The tones that are not static (tile_segment_static) in some tile of the window [c, c + m): a
+// chirp or an amplitude ramp meets the tile span.  The render visits only these, in ascending
+// order, and still skips them in the tiles where they are static.
+void engine_list(awg_t* h, int64_t c, int64_t m, std::vector<int32_t>* list) {
+  const int64_t t_first = c / awgk::TILE, t_last = (c + m - 1) / awgk::TILE;
+  const int64_t s0 = t_first * awgk::TILE, s1 = (t_last + 1) * awgk::TILE - 1;
+  list->clear();
+  for (int32_t k : flagged_tones(h)) {
+    const ToneRec& t = h->tones[(size_t)k];
+    if ((t.slot >= 0 && !(s1 < t.n_s || s0 > t.n_e)) ||
+        ((t.flags & awgk::TONE_AMP_RAMP) && !(s1 <= t.a_ns || s0 >= t.a_ns + t.a_L)))
+      list->push_back(k);
+  }
+}
+
+// GEMM arguments of the window [c, c + m) into out_q (every tone static there) or the FP32 sum
+// out_f.  two_segments: some tone of the handle has held a chirp or a ramp (four columns per tone).
+awgk::TableArgs2 engine_gemm_args(awg_t* h, int64_t c, int64_t m, bool two_segments, int16_t* out_q, float* out_f) {
+  const size_t Kp = two_segments ? awgk::table_kp_window(std::max(h->K, 1)) : awgk::table_kp(std::max(h->K, 1));
+  const size_t b_elems = (size_t)256 * Kp;
+  awgk::TableArgs2 t;
+  std::memset(&t, 0, sizeof(t));
+  t.tones = h->d_tones;
+  t.K = h->K;
+  t.nb_log2 = 8;
+  t.row_base = c >> 8;
+  t.M = ((c + m - 1) >> 8) - t.row_base + 1;
+  t.win_start = c;
+  t.win_end = c + m;
+  t.window_mode = two_segments ? 1 : 0;
+  t.invariant = 1;
+  t.precision = h->static_engine == AWG_STATIC_GEMM_FP16 ? AWG_PREC_FP16 : AWG_PREC_BF16;
+  t.b_hi = h->d_gemm;
+  t.b_lo = h->d_gemm + b_elems;
+  t.out_q = out_q;
+  t.out_f = out_f;
+  t.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
+  t.a_scale = awgk::table_amp_scale(max_amplitude(h));
+  t.status = h->d_status;
+  return t;
+}
+
+// B operand of the handle's GEMM (cos, sin of 2 pi n2 F / 2^64 per tone and segment, hi + lo).
+int engine_operand(awg_t* h, bool two_segments, cudaStream_t s) {
+  const size_t Kp = two_segments ? awgk::table_kp_window(std::max(h->K, 1)) : awgk::table_kp(std::max(h->K, 1));
+  int st = ensure(&h->d_gemm, &h->cap_gemm, 2 * (size_t)256 * Kp, h, "table GEMM operands");
+  if (st) return st;
+  const awgk::TableArgs2 t = engine_gemm_args(h, h->cursor, awgk::TILE, two_segments, nullptr, nullptr);
+  cudaError_t e;
+  if ((e = counted(h, awgk::launch_table_prep(t, s))) != cudaSuccess) return cuda_fail(e, "static operand launch");
+  return AWG_OK;
+}
+
 int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* stream, int32_t q_stride) {
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t PIECE = (int64_t)1 << 26;
+  const EngineSplit es = engine_split(h);
+  // no tone has ever held a chirp or a ramp: every tone is static in one segment everywhere, and
+  // the GEMM takes the table's two columns per tone instead of four (half the work)
+  const bool two_segments = es.n_flagged > 0;
   for (int64_t off = 0; off < n; off += PIECE) {
     const int64_t m = std::min(PIECE, n - off), c = h->cursor;
-    // the tones that are not static (tile_segment_static) in some tile the piece touches: a chirp
-    // or an amplitude ramp meets the tile span.  The render visits only these, in ascending order,
-    // and still skips them in the tiles where they are static.  None: the GEMM writes the output.
-    const int64_t t_first = c / awgk::TILE, t_last = (c + m - 1) / awgk::TILE;
-    const int64_t s0 = t_first * awgk::TILE, s1 = (t_last + 1) * awgk::TILE - 1;
-    h->list.clear();
-    int32_t n_flagged = 0;
-    for (size_t k = 0; k < h->tones.size(); ++k) {
-      const ToneRec& t = h->tones[k];
-      n_flagged += (t.slot >= 0 || (t.flags & awgk::TONE_AMP_RAMP)) ? 1 : 0;
-      if ((t.slot >= 0 && !(s1 < t.n_s || s0 > t.n_e)) ||
-          ((t.flags & awgk::TONE_AMP_RAMP) && !(s1 <= t.a_ns || s0 >= t.a_ns + t.a_L)))
-        h->list.push_back((int32_t)k);
-    }
-    // The render's split and its CTAs' tone ranges come from the tones that hold a chirp or a ramp
-    // at all (they change only when chirps, ramps or tones are set, never while rendering): about
-    // the same number of them in each range.  With every tone holding one this is the plain split.
-    const int32_t list_split = awgk::tone_split_for(n_flagged);
-    int32_t bounds[awgk::MAX_SPLIT + 1];
-    bounds[0] = 0;
-    bounds[list_split] = h->K;
-    for (int32_t r = 1, p = 0, k = 0; r < list_split; ++r) {
-      // the first tone of range r: the flagged tone at position floor(n_flagged r / list_split)
-      const int32_t want = (int32_t)((int64_t)n_flagged * r / list_split);
-      for (; k < h->K; ++k) {
-        const ToneRec& t = h->tones[(size_t)k];
-        if (t.slot >= 0 || (t.flags & awgk::TONE_AMP_RAMP)) {
-          if (p == want) break;
-          ++p;
-        }
-      }
-      bounds[r] = k;
-    }
+    engine_list(h, c, m, &h->list);
     const bool all_static = q_stride == 1 && h->K > 0 && h->list.empty();
     int16_t* oq = out_q ? out_q + (size_t)off * (size_t)q_stride : nullptr;
     float* of = out_f ? out_f + off : nullptr;
@@ -1112,36 +1178,12 @@ int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
       if ((st = render_direct(h, m, of, oq, stream, q_stride, nullptr, 0))) return st;
       continue;
     }
-    // no tone has ever held a chirp or a ramp: every tone is static in one segment everywhere, and
-    // the GEMM takes the table's two columns per tone instead of four (half the work)
-    const bool two_segments = n_flagged > 0;
-    const size_t Kp = two_segments ? awgk::table_kp_window(std::max(h->K, 1)) : awgk::table_kp(std::max(h->K, 1));
-    const size_t b_elems = (size_t)256 * Kp;
-    if ((st = ensure(&h->d_gemm, &h->cap_gemm, 2 * b_elems, h, "table GEMM operands"))) return st;
     if (!all_static && (st = ensure(&h->d_base, &h->cap_base, (size_t)m, h, "static sum"))) return st;
-    awgk::TableArgs2 t;
-    std::memset(&t, 0, sizeof(t));
-    t.tones = h->d_tones;
-    t.K = h->K;
-    t.nb_log2 = 8;
-    t.row_base = c >> 8;
-    t.M = ((c + m - 1) >> 8) - t.row_base + 1;
-    t.win_start = c;
-    t.win_end = c + m;
-    t.window_mode = two_segments ? 1 : 0;
-    t.invariant = 1;
-    t.precision = h->static_engine == AWG_STATIC_GEMM_FP16 ? AWG_PREC_FP16 : AWG_PREC_BF16;
-    t.b_hi = h->d_gemm;
-    t.b_lo = h->d_gemm + b_elems;
-    t.out_q = all_static ? oq : nullptr;
-    t.out_f = all_static ? of : h->d_base;
-    t.scale = h->full_scale > 0 ? (float)(32767.0 / h->full_scale) : 0.f;
-    t.a_scale = awgk::table_amp_scale(max_amplitude(h));
-    t.status = h->d_status;
     cudaError_t e;
     if ((e = order_after_uploads(h, s)) != cudaSuccess) return cuda_fail(e, "upload ordering");
     if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
-    if ((e = counted(h, awgk::launch_table_prep(t, s))) != cudaSuccess) return cuda_fail(e, "static operand launch");
+    if ((st = engine_operand(h, two_segments, s))) return st;
+    const awgk::TableArgs2 t = engine_gemm_args(h, c, m, two_segments, all_static ? oq : nullptr, all_static ? of : h->d_base);
     if ((e = counted(h, awgk::launch_table_gemm(t, s))) != cudaSuccess) return cuda_fail(e, "static GEMM launch");
     if (all_static) {
       if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
@@ -1162,7 +1204,7 @@ int render_engine(awg_t* h, int64_t n, float* out_f, int16_t* out_q, void* strea
         return cuda_fail(e, "tone list upload");
     }
     if ((st = render_direct(h, m, of, oq, stream, q_stride, h->d_base, 1, use_list ? h->d_list : nullptr, n_list,
-                            list_split, bounds)))
+                            es.split, es.bounds)))
       return st;
   }
   return AWG_OK;
@@ -1182,6 +1224,70 @@ size_t awgk::render_recs_needed(const awg_t* h, int64_t n) {
 }
 
 size_t awgk::render_slots(const awg_t* h) { return h ? h->chirps.size() : 0; }
+
+int awgk::engine_setup(awg_t* h, int32_t engine, cudaStream_t s, int32_t* render_split) {
+  if (!h || (engine != AWG_STATIC_GEMM_FP16 && engine != AWG_STATIC_GEMM_BF16))
+    return fail(AWG_EINVAL, "engine_setup: bad arguments");
+  h->static_engine = engine;
+  const EngineSplit es = engine_split(h);
+  cudaError_t e = order_after_uploads(h, s);
+  if (e != cudaSuccess) return cuda_fail(e, "upload ordering");
+  const int st = engine_operand(h, es.n_flagged > 0, s);
+  if (st) return st;
+  if (render_split) *render_split = es.split;
+  return AWG_OK;
+}
+
+size_t awgk::engine_list_needed(awg_t* h, int64_t n) {
+  if (!h || n <= 0) return 0;
+  std::vector<int32_t> list;
+  engine_list(h, h->cursor, n, &list);
+  return list.size();
+}
+
+int awgk::prepare_render_engine(awg_t* h, int64_t n, int16_t* out_q, cudaStream_t s, awgk::RenderArgs* ra,
+                                awgk::TileRec* recs, size_t recs_cap, int32_t* act, float* base, int32_t* d_list,
+                                int32_t* h_list, size_t list_cap, bool* need_render) {
+  if (!h || n <= 0 || !out_q || !ra || !base || !need_render || h->K == 0 || h->static_engine == AWG_STATIC_DIRECT)
+    return fail(AWG_EINVAL, "prepare_render_engine: bad arguments");
+  const int64_t c = h->cursor;
+  const EngineSplit es = engine_split(h);
+  std::vector<int32_t> list;
+  engine_list(h, c, n, &list);
+  const bool all_static = list.empty();
+  cudaError_t e = order_after_uploads(h, s);
+  if (e != cudaSuccess) return cuda_fail(e, "upload ordering");
+  const awgk::TableArgs2 t = engine_gemm_args(h, c, n, es.n_flagged > 0, all_static ? out_q : nullptr, all_static ? nullptr : base);
+  if ((e = counted(h, awgk::launch_table_gemm(t, s))) != cudaSuccess) return cuda_fail(e, "static GEMM launch");
+  if (all_static) {
+    *need_render = false;
+    std::memset(ra, 0, sizeof(*ra));
+    h->cursor = c + n;
+    return AWG_OK;
+  }
+  // the listed tones through the render kernel, with the GEMM's sum added before quantising
+  const int32_t n_list = (int32_t)list.size();
+  const bool use_list = n_list < h->K;
+  if (use_list) {
+    if ((size_t)n_list > list_cap || !d_list || !h_list) return fail(AWG_ENOMEM, "prepare_render_engine: list arena too small");
+    std::memcpy(h_list, list.data(), (size_t)n_list * sizeof(int32_t));
+    if ((e = cudaMemcpyAsync(d_list, h_list, (size_t)n_list * sizeof(int32_t), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+      return cuda_fail(e, "tone list upload");
+  }
+  const int st = awgk::prepare_render(h, n, out_q, nullptr, s, ra, recs, recs_cap, act);
+  if (st) {
+    h->cursor = c;
+    return st;
+  }
+  ra->base = base;
+  ra->skip_static = 1;
+  ra->tone_list = use_list ? d_list : nullptr;
+  ra->n_list = n_list;
+  ra->split = es.split;
+  for (int r = 0; r <= es.split; ++r) ra->bounds[r] = es.bounds[r];
+  *need_render = true;
+  return AWG_OK;
+}
 
 int awgk::prepare_render(awg_t* h, int64_t n, int16_t* out_q, float* out_f, cudaStream_t s, awgk::RenderArgs* ra,
                          awgk::TileRec* recs, size_t recs_cap, int32_t* act, size_t* recs_need) {
@@ -1631,6 +1737,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     t.phi_post_ref = phi_end - (uint64_t)t.n_e * p.F1;
     t.flags = (t.flags & (awgk::TONE_AMP_RAMP | awgk::TONE_AMP_MINJERK)) | c.flags;
   }
+  h->flagged_ok = false;
   // only the records that changed go to the device (the whole chirp array if it had to grow)
   std::sort(changed_tones.begin(), changed_tones.end());
   std::sort(changed_slots.begin(), changed_slots.end());
@@ -1694,6 +1801,7 @@ int awg_set_amp_ramps(awg_t* h, const int32_t* tone, const double* amp_end, cons
   for (int32_t i = 0; i < n; ++i) {
     ToneRec& t = h->tones[(size_t)tone[i]];
     if (t.flags & awgk::TONE_AMP_RAMP) t.A = t.A_end;   // fold the finished ramp
+    h->flagged_ok = false;
     t.a_ns = start_sample[i];
     t.a_L = (int32_t)L[(size_t)i];
     t.A_end = (float)amp_end[i];

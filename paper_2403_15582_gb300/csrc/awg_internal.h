@@ -279,6 +279,20 @@ int prepare_render(struct awg* h, int64_t n, int16_t* out_q, float* out_f, cudaS
                    size_t* recs_need = nullptr);
 // Tile records prepare_render needs for the window [cursor, cursor + n).
 size_t render_recs_needed(const struct awg* h, int64_t n);
+// The tensor-core static engine for a served request (its tone state is fixed while it is served):
+// engine_setup selects `engine` (AWG_STATIC_GEMM_FP16 / _BF16) for h, prepares its GEMM's B operand
+// on stream s (the caller synchronises s before the first render) and returns the tone split of the
+// render part (tones that hold a chirp or a ramp).  prepare_render_engine does what prepare_render
+// does for the window [cursor, cursor + n), with the engine: the GEMM of the window's static tones
+// is launched on s into `base` (n floats), or straight into out_q when no tone chirps or ramps in
+// the window (*need_render false: no render item); otherwise the listed tones (d_list, staged
+// through the pinned h_list, list_cap entries) are rendered with base added, and the chirp tile
+// records go to recs / act as in prepare_render.  engine_list_needed: entries of that list.
+int engine_setup(struct awg* h, int32_t engine, cudaStream_t s, int32_t* render_split);
+int prepare_render_engine(struct awg* h, int64_t n, int16_t* out_q, cudaStream_t s, RenderArgs* ra, TileRec* recs,
+                          size_t recs_cap, int32_t* act, float* base, int32_t* d_list, int32_t* h_list,
+                          size_t list_cap, bool* need_render);
+size_t engine_list_needed(struct awg* h, int64_t n);
 // Entries of the slot -> record map of h (its chirp slots).
 size_t render_slots(const struct awg* h);
 // CTAs per tile (tone split) for K tones; depends on K only.

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdint>
 #include <cstring>
@@ -48,8 +49,10 @@ struct Request {
   size_t mem = 0, out_bytes = 0;
   bool ready = false;          // set-up done: renderable
   bool release_requested = false;
-  int32_t split = 1;
-  double weight = 0;           // device cost per sample, in static-tone units: K + n_chirps / 2
+  int32_t split = 1;           // tone split of its render (of the render part, with the engine)
+  bool engine = false;         // static tones on the tensor-core engine (awg_server_set_static_engine)
+  double weight = 0;           // device cost per sample, in static-tone units: K + n_chirps / 2, or
+                               // with the engine K / engine_gain + 1.5 n_chirps
   double cta_tones = 0;        // tones one CTA sums (K / tone split, rounded up)
   int32_t issue_chunk = 0;     // next piece to issue: chunk index and offset in it
   int64_t issue_off = 0;
@@ -71,8 +74,8 @@ struct Piece {
 struct Round {
   int set = 0;                 // staging buffers and events in use
   std::vector<Piece> pieces;
-  double work = 0;             // tone-samples
-  double est_s = 0;            // estimated device time (round_time)
+  double work = 0;             // cost in static-tone samples (Request::weight x samples)
+  double tone_samples = 0;     // tone-samples rendered (tones x samples)
   double host_s = 0;           // host time to plan and issue
   awg_round_record_t rec{};
 };
@@ -118,6 +121,9 @@ struct awg_server {
   int64_t budget = 0;
   int32_t max_active = 0;
   int32_t depth = 2;           // chunks rendered ahead of playback (awg_server_set_prefetch)
+  int32_t engine = AWG_STATIC_DIRECT;   // static-tone engine for requests of >= engine_min_tones tones
+  int32_t engine_min_tones = 0;
+  cudaStream_t setup_stream = nullptr;  // the worker's stream (engine operands at set-up)
   double max_queue_s = 0;
   int device = 0;
   clk::time_point t0;
@@ -150,9 +156,16 @@ struct awg_server {
   float* d_part[NSETS] = {};
   unsigned long long* d_tctr[NSETS] = {};
   size_t cap_part[NSETS] = {}, cap_tctr[NSETS] = {};
+  // tensor-core engine pieces: the GEMM's FP32 sums and the tone lists of the round (device, and
+  // the lists' pinned staging)
+  float* d_base[NSETS] = {};
+  int32_t* d_list[NSETS] = {};
+  int32_t* h_list[NSETS] = {};
+  size_t cap_base[NSETS] = {}, cap_list[NSETS] = {};
   std::deque<Round> flight;
   int64_t round_seq = 0;
-  double queued_s = 0;         // estimated device time of the rounds issued and not yet complete
+  double queued_work = 0;      // tone-samples issued and not yet accounted complete (rounds on the
+                               // three streams overlap: the queue drains at the busy-device rate P)
   double busy_end = -1;        // end of the device's current busy interval (server clock)
   // cost model (calibrated at creation): the device renders P static-tone samples/s when it is
   // kept busy (updated from busy rounds within [0.6, 1.2] of the calibration); a round costs a_gpu
@@ -160,6 +173,7 @@ struct awg_server {
   double P = 2.5e12, P_cal = 2.5e12;
   double a_gpu = 20e-6;
   double r_cta = 1e10;         // tone-samples/s of one CTA alone on its SM
+  double P_engine = 0;         // static tone-samples/s of the tensor-core engine on a busy device
   double host_s = 30e-6;
   // statistics
   int64_t submitted = 0, admitted = 0, rej_deadline = 0, rej_memory = 0, completed = 0;
@@ -177,22 +191,39 @@ namespace {
 double now_s(const awg_server_t* s) { return std::chrono::duration<double>(clk::now() - s->t0).count(); }
 
 // Release and due time of chunk c >= 1 of a playing request (server clock): due when chunk c-1
-// ends playing, t_play + c period; released a look-ahead earlier -- `depth` periods, and at least
-// MIN_LOOKAHEAD_S so that short chunks keep room for host and queue delays -- but not before
-// chunk 0 is complete (t_play).  With depth 1 and long chunks a chunk is released when the one
-// before starts playing (double buffering).
-constexpr double MIN_LOOKAHEAD_S = 1e-3;
-double lookahead(const awg_server_t* s, const Request* r) {
-  return std::max((double)s->depth * r->period, MIN_LOOKAHEAD_S);
-}
+// ends playing, t_play + c period; released a look-ahead of `depth` periods earlier, but not
+// before chunk 0 is complete (t_play).  With depth 1 a chunk is released when the one before
+// starts playing (double buffering).  (A minimum look-ahead of 1 ms for short chunks was tried:
+// chunks released that early crowded the device queue and more of them missed.)
+double lookahead(const awg_server_t* s, const Request* r) { return (double)s->depth * r->period; }
 double chunk_due(const Request* r, int32_t c) { return r->t_play + (double)c * r->period; }
 double chunk_release(const awg_server_t* s, const Request* r, int32_t c) {
   return std::max(r->t_play, chunk_due(r, c) - lookahead(s, r));
 }
 
+// The request's cost in static-tone units per sample and its longest CTA in tones: direct render
+// K + n_chirps / 2 (a chirping tone costs about one and a half static ones) and K / split tones per
+// CTA; with the engine, K times the engine's cost ratio plus the chirping tones, and the longer of
+// a render CTA and a GEMM CTA (128 rows of 256 samples over a quarter of the tones) in the same
+// units.
+void set_cost(const awg_server_t* s, Request* r) {
+  const double K = (double)r->f.size(), nc = (double)r->c_tone.size();
+  if (r->engine && s->P_engine > 0) {
+    r->weight = K * s->P / s->P_engine + 1.5 * nc;
+    const int split = awgk::tone_split_for((int)r->c_tone.size());
+    const double render_cta = std::ceil(nc / split);
+    const double gemm_cta_s = 32768.0 * std::max(1.0, K / 4.0) / (s->P_engine / (double)awgk::device_sm_count());
+    r->cta_tones = std::max(render_cta, gemm_cta_s * s->r_cta / awgk::TILE);
+  } else {
+    r->weight = K + 0.5 * nc;
+    const int split = awgk::tone_split_for((int)r->f.size());
+    r->cta_tones = (double)(((int)r->f.size() + split - 1) / split);
+  }
+}
+
 // Device time of one CTA of request r alone on an SM (its tones per CTA over the calibrated rate
-// of a lone CTA), and of a round: its fixed cost plus the larger of its work at the busy-device
-// rate and its longest CTA (a small round cannot spread over the device).
+// of a lone CTA), and of a chunk or a round alone: its fixed cost plus the larger of its work at
+// the busy-device rate and its longest CTA (a small round cannot spread over the device).
 double cta_time(const awg_server_t* s, const Request* r) { return r->cta_tones * awgk::TILE / s->r_cta; }
 double round_time(const awg_server_t* s, double work, double t_cta_max) {
   return s->a_gpu + std::max(work / s->P, t_cta_max);
@@ -269,6 +300,11 @@ bool start_request(awg_server_t* s, Request* r) {
     return false;
   if (awg_set_full_scale(r->h, r->full_scale)) return false;
   r->split = awg_tone_split(r->h);
+  awg_set_static_engine(r->h, AWG_STATIC_DIRECT);
+  if (r->engine) {   // B operand of the request's GEMM, once: its tone state is fixed from here on
+    if (awgk::engine_setup(r->h, s->engine, s->setup_stream, &r->split) != AWG_OK) return false;
+    if (cudaStreamSynchronize(s->setup_stream) != cudaSuccess) return false;
+  }
   r->out_bytes = std::max<size_t>((size_t)r->n_chunks * (size_t)r->chunk * sizeof(int16_t), 16);
   {
     std::lock_guard<std::mutex> lk(s->mu);
@@ -436,7 +472,7 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
   if (cands.empty()) return;
   // work the device may take on now: fill the queue up to the horizon
   const double H = horizon(min_period);
-  const double queued = s->queued_s;
+  const double queued = s->queued_work / s->P;
   if (!s->flight.empty() && queued >= H) return;
   double w_left = std::max(0.5 * H, H - queued - s->a_gpu) * s->P;
   std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.due < y.due; });
@@ -446,7 +482,6 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
       rd->rec.first_due = cd.due;
       break;
     }
-  double t_cta_max = 0;
   for (const Cand& cd : cands) {
     if (w_left <= 0 && !rd->pieces.empty()) break;
     Request* r = cd.r;
@@ -459,7 +494,7 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
     }
     rd->pieces.push_back({r, r->issue_chunk, r->issue_off, take, take == remaining});
     rd->work += K * (double)take;
-    t_cta_max = std::max(t_cta_max, cta_time(s, r));
+    rd->tone_samples += (double)r->f.size() * (double)take;
     w_left -= K * (double)take;
     r->issue_off += take;
     if (r->issue_off == r->chunk) {
@@ -467,7 +502,6 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
       ++r->issue_chunk;
     }
   }
-  rd->est_s = round_time(s, rd->work, t_cta_max);
 }
 
 // Issue a planned round on its set's stream (outside the lock: only this thread touches active
@@ -500,6 +534,35 @@ bool issue_round(awg_server_t* s, Round* rd) {
     s->d_act[set] = a;
     s->cap_act[set] = ncap;
   }
+  // engine pieces: the GEMM's sum of the piece's samples and its tone list
+  std::vector<size_t> base0(rd->pieces.size() + 1, 0), list0(rd->pieces.size() + 1, 0);
+  for (size_t i = 0; i < rd->pieces.size(); ++i) {
+    const Piece& p = rd->pieces[i];
+    base0[i + 1] = base0[i] + (p.r->engine ? (size_t)p.n : 0);
+    list0[i + 1] = list0[i] + (p.r->engine ? awgk::engine_list_needed(p.r->h, p.n) : 0);
+  }
+  if (base0.back() > s->cap_base[set]) {
+    const size_t ncap = std::max(base0.back(), 2 * s->cap_base[set]);
+    float* a = nullptr;
+    if (cudaMalloc((void**)&a, ncap * sizeof(float)) != cudaSuccess) return false;
+    cudaFree(s->d_base[set]);
+    s->d_base[set] = a;
+    s->cap_base[set] = ncap;
+  }
+  if (list0.back() > s->cap_list[set]) {
+    const size_t ncap = std::max(list0.back(), 2 * s->cap_list[set]);
+    int32_t *a = nullptr, *b = nullptr;
+    if (cudaMalloc((void**)&a, ncap * sizeof(int32_t)) != cudaSuccess) return false;
+    if (cudaHostAlloc((void**)&b, ncap * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
+      cudaFree(a);
+      return false;
+    }
+    cudaFree(s->d_list[set]);
+    cudaFreeHost(s->h_list[set]);
+    s->d_list[set] = a;
+    s->h_list[set] = b;
+    s->cap_list[set] = ncap;
+  }
   std::vector<awgk::RenderArgs> ra(rd->pieces.size());
   size_t n_items = 0;
   bool ok = cudaEventRecord(s->ev_beg[set], st) == cudaSuccess;
@@ -507,8 +570,17 @@ bool issue_round(awg_server_t* s, Round* rd) {
     const Piece& p = rd->pieces[i];
     int16_t* out = p.r->d_out + (size_t)p.chunk * (size_t)p.r->chunk + (size_t)p.off;
     const bool own = rec0[i + 1] > rec0[i];   // chirp tile records in this piece
-    ok = awgk::prepare_render(p.r->h, p.n, out, nullptr, st, &ra[i], own ? s->d_arena[set] + rec0[i] : nullptr,
-                              rec0[i + 1] - rec0[i], own ? s->d_act[set] + act0[i] : nullptr) == AWG_OK;
+    if (p.r->engine) {
+      bool need = false;
+      ok = awgk::prepare_render_engine(p.r->h, p.n, out, st, &ra[i], own ? s->d_arena[set] + rec0[i] : nullptr,
+                                       rec0[i + 1] - rec0[i], own ? s->d_act[set] + act0[i] : nullptr,
+                                       s->d_base[set] + base0[i], s->d_list[set] + list0[i],
+                                       s->h_list[set] + list0[i], list0[i + 1] - list0[i], &need) == AWG_OK;
+      if (!need) ra[i].n_tiles = 0;   // the GEMM wrote the samples: no render item
+    } else {
+      ok = awgk::prepare_render(p.r->h, p.n, out, nullptr, st, &ra[i], own ? s->d_arena[set] + rec0[i] : nullptr,
+                                rec0[i + 1] - rec0[i], own ? s->d_act[set] + act0[i] : nullptr) == AWG_OK;
+    }
     n_items += (size_t)ra[i].n_tiles;
   }
   rd->rec.pieces = (int32_t)rd->pieces.size();
@@ -583,11 +655,11 @@ void complete_round(awg_server_t* s) {
   rd.rec.t_done = t_done;
   rd.rec.work = rd.work;
   s->trace_rounds.push(rd.rec);
-  s->queued_s = std::max(0.0, s->queued_s - rd.est_s);
+  s->queued_work = std::max(0.0, s->queued_work - rd.work);
   ++s->rounds;
   s->batched += (int64_t)rd.pieces.size();
   s->max_batch = std::max(s->max_batch, (int64_t)rd.pieces.size());
-  s->tone_samples += rd.work;
+  s->tone_samples += rd.tone_samples;
   if (s->first_t < 0) s->first_t = t_start;
   s->last_t = std::max(s->last_t, t_done);
   // a round that found the device busy measures the sustained rate: its work over the advance of
@@ -650,6 +722,45 @@ void fail_rounds(awg_server_t* s, const std::string& what) {
   s->cv.notify_all();
 }
 
+// The tensor-core engine's rate: rounds of one request of K static tones over N samples with the
+// engine (best of three, after a warm-up), through the same path as the served rounds.
+int calibrate_engine(awg_server_t* s, int32_t K, int64_t N) {
+  std::vector<double> f(K), a(K, 1.0 / K), th(K, 0.0);
+  for (int32_t k = 0; k < K; ++k) f[k] = s->fs * (0.01 + 0.4 * (double)k / K);
+  awg_t* h = awg_create(s->fs);
+  int16_t* out = nullptr;
+  int st = h ? AWG_OK : AWG_ECUDA;
+  if (!st && cudaMalloc((void**)&out, (size_t)N * sizeof(int16_t)) != cudaSuccess)
+    st = awgk::set_error(AWG_ENOMEM, "calibration buffer");
+  if (!st) st = awg_set_tones(h, f.data(), a.data(), th.data(), K);
+  Request r;
+  r.h = h;
+  r.d_out = out;
+  r.chunk = N;
+  r.n_chunks = 1;
+  r.engine = true;
+  if (!st) st = awgk::engine_setup(h, AWG_STATIC_GEMM_FP16, s->streams[0], &r.split);
+  double best = 1e30;
+  for (int rep = 0; rep < 4 && !st; ++rep) {
+    awg_seek(h, 0);
+    Round rd;
+    rd.set = 0;
+    rd.pieces.push_back({&r, 0, 0, N, true});
+    float ms = 0.f;
+    if (!issue_round(s, &rd) || cudaEventSynchronize(s->ev_end[0]) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, s->ev_beg[0], s->ev_end[0]) != cudaSuccess) {
+      st = awgk::set_error(AWG_ECUDA, "engine calibration round failed");
+      break;
+    }
+    if (rep > 0) best = std::min(best, 1e-3 * (double)ms);
+  }
+  if (out) cudaFree(out);
+  if (h) awg_destroy(h);
+  if (st) return st;
+  s->P_engine = (double)K * (double)N / std::max(1e-6, best - s->a_gpu);
+  return AWG_OK;
+}
+
 // Cost model calibration, through the same path as the served rounds (best of three each): a round
 // of one tile of one tone (fixed cost a_gpu), of 2048 static tones over 2^19 samples (rate P), and
 // of one tile of 96 x MAX_SPLIT tones (one CTA of 96 tones per SM: the rate of a CTA alone).
@@ -694,7 +805,7 @@ int calibrate(awg_server_t* s) {
   s->a_gpu = std::max(2e-6, best[0]);
   s->P = s->P_cal = (double)K * (double)N / std::max(1e-6, best[1] - s->a_gpu);
   s->r_cta = 96.0 * awgk::TILE / std::max(1e-6, best[2] - s->a_gpu);
-  return AWG_OK;
+  return calibrate_engine(s, K, N);
 }
 
 // Scheduler: up to NSETS rounds in flight on their own streams; the host plans the next round
@@ -717,7 +828,7 @@ void sched_main(awg_server_t* s) {
       {
         std::lock_guard<std::mutex> lk(s->mu);
         plan_round(s, t_plan, &rd, &next_release);
-        s->queued_s += rd.est_s;
+        s->queued_work += rd.work;
       }
       if (!rd.pieces.empty()) {
         if (!issue_round(s, &rd)) {
@@ -784,6 +895,7 @@ awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes,
     if (e == cudaSuccess) e = cudaEventCreate(&s->ev_end[i]);
   }
   if (e == cudaSuccess) e = cudaEventCreate(&s->ev_ref);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->setup_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = awgk::render_setup_attributes();
   // reference point between the device's event clock and the server clock
   if (e == cudaSuccess) e = cudaEventRecord(s->ev_ref, s->streams[0]);
@@ -820,6 +932,18 @@ awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes,
   return s;
 }
 
+int awg_server_set_static_engine(awg_server_t* s, int32_t engine, int32_t min_tones) {
+  if (!s) return awgk::set_error(AWG_EINVAL, "null server");
+  if (engine != AWG_STATIC_DIRECT && engine != AWG_STATIC_GEMM_FP16 && engine != AWG_STATIC_GEMM_BF16)
+    return awgk::set_error(AWG_EINVAL, "unknown static engine");
+  if (min_tones < 1) return awgk::set_error(AWG_EINVAL, "min_tones must be >= 1");
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (!s->all.empty()) return awgk::set_error(AWG_ESTATE, "the static engine is set before the first request");
+  s->engine = engine;
+  s->engine_min_tones = min_tones;
+  return AWG_OK;
+}
+
 int awg_server_set_prefetch(awg_server_t* s, int32_t chunks) {
   if (!s) return awgk::set_error(AWG_EINVAL, "null server");
   if (chunks < 1 || chunks > 16) return awgk::set_error(AWG_EINVAL, "prefetch depth must be 1 .. 16 chunks");
@@ -852,12 +976,16 @@ void awg_server_destroy(awg_server_t* s) {
     cudaFree(s->d_tctr[i]);
     cudaFree(s->d_reqs[i]);
     cudaFree(s->d_items[i]);
+    cudaFree(s->d_base[i]);
+    cudaFree(s->d_list[i]);
+    cudaFreeHost(s->h_list[i]);
     cudaFreeHost(s->h_reqs[i]);
     cudaFreeHost(s->h_items[i]);
     if (s->ev_beg[i]) cudaEventDestroy(s->ev_beg[i]);
     if (s->ev_end[i]) cudaEventDestroy(s->ev_end[i]);
   }
   if (s->ev_ref) cudaEventDestroy(s->ev_ref);
+  if (s->setup_stream) cudaStreamDestroy(s->setup_stream);
   for (int i = 0; i < NSETS; ++i)
     if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
   delete s;
@@ -885,13 +1013,10 @@ int64_t awg_server_submit(awg_server_t* s, const awg_request_t* q) {
   r->n_chunks = q->n_chunks;
   r->full_scale = q->full_scale;
   r->period = (double)q->chunk / s->fs;
-  r->weight = (double)q->n_tones + 0.5 * (double)q->n_chirps;
-  {
-    const int split = awgk::tone_split_for(q->n_tones);
-    r->cta_tones = (double)((q->n_tones + split - 1) / split);
-  }
   {
     std::lock_guard<std::mutex> lk(s->mu);
+    r->engine = s->engine != AWG_STATIC_DIRECT && q->n_tones > 0 && q->n_tones >= s->engine_min_tones;
+    set_cost(s, r);
     r->id = s->next_id++;
     r->t_arrival = now_s(s);
     s->all[r->id] = r;
@@ -982,6 +1107,7 @@ int awg_server_stats(awg_server_t* s, awg_server_stats_t* out) {
   out->est_throughput = s->P;
   out->est_round_cost_ms = 1e3 * s->a_gpu;
   out->est_cta_rate = s->r_cta;
+  out->est_engine_throughput = s->P_engine;
   return AWG_OK;
 }
 

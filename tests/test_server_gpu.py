@@ -34,11 +34,12 @@ def _request(seed, fs, K, chunk, n_chunks, n_chirps):
     return f, a, th, chirps, chunk, n_chunks
 
 
-def _standalone(awg, fs, req):
+def _standalone(awg, fs, req, engine=0):
     f, a, th, chirps, chunk, n_chunks = req
     s = awg.Synth(fs)
     s.set_tones(f, a, th)
     s.set_chirp_list(chirps)
+    s.set_static_engine(engine)
     out = torch.empty(chunk * n_chunks, dtype=torch.int16, device="cuda")
     for c in range(n_chunks):
         s.render(chunk, out[c * chunk:])
@@ -108,6 +109,30 @@ def test_two_split_sizes_in_one_round_match_the_oracle(awg, oracle):
     for rid, r in zip(ids, reqs):
         got = srv.read(rid, r[4] * r[5])
         assert np.array_equal(got, _standalone(awg, fs, r)), rid
+        _check_against_oracle(oracle, fs, r, got)
+        srv.release(rid)
+    srv.close()
+
+
+def test_served_requests_on_the_tensor_core_engine(awg, oracle):
+    """Requests of at least 1000 tones have their static tones summed by the split-precision GEMM
+    (FP16 hi + lo), only their chirping tones through the batched render; a request without chirps
+    is written by the GEMM alone.  Each equals a standalone render with the same engine bit for bit
+    and the oracle within 1 LSB; a small request in the same rounds stays on the direct path."""
+    fs = 20e6
+    reqs = [_request(31, fs, 3000, 1 << 17, 3, 60), _request(32, fs, 200, 1 << 16, 4, 20),
+            _request(33, fs, 1200, 1 << 17, 2, 0)]
+    srv = awg.Server(fs, 8 << 30, 64)
+    srv.set_static_engine(awg.STATIC_GEMM_FP16, 1000)
+    assert srv.stats()["est_engine_throughput"] > srv.stats()["est_throughput"]
+    ids = [srv.submit(r[0], r[1], r[2], r[4], r[5], r[3]) for r in reqs]
+    srv.drain(60000)
+    st = srv.stats()
+    assert st["completed"] == 3, st
+    for rid, r in zip(ids, reqs):
+        got = srv.read(rid, r[4] * r[5])
+        engine = awg.STATIC_GEMM_FP16 if len(r[0]) >= 1000 else awg.STATIC_DIRECT
+        assert np.array_equal(got, _standalone(awg, fs, r, engine)), rid
         _check_against_oracle(oracle, fs, r, got)
         srv.release(rid)
     srv.close()
