@@ -21,7 +21,7 @@ constexpr int STAGE = 32;          // tones staged in shared memory at a time (d
 constexpr int SINE_SFU = 0;        // static segments: SFU sine of every sample's phase
 constexpr int SINE_ROTATOR = 1;    // static segments: exact sin/cos at the run start, then rotations
 constexpr int MAX_SPLIT = 16;      // cluster size limit (non-portable 16 on sm_100-class parts)
-constexpr int MAX_ACTIVE_PER_LAUNCH = 1024;
+constexpr int MAX_ACTIVE_PER_LAUNCH = 7168;   // chirp slots per prep launch (kernel parameters: < 32 KB)
 
 constexpr int64_t NO_CHIRP = INT64_MAX;
 
@@ -114,7 +114,10 @@ struct alignas(16) TileRec {
 };
 static_assert(sizeof(TileRec) == 176, "TileRec layout");
 
-struct PrepArgs {
+// Arguments of one prep launch, the active chirp slots inline (kernel parameters are copied with
+// the launch: a launch of up to 1024 slots passes the small form, larger ones the full 7168).
+template <int CAP>
+struct PrepArgsT {
   const ChirpRec* chirps;
   TileRec* recs;          // [n_active][n_tiles]
   int32_t* act_of_slot;   // slot -> active index (written here)
@@ -124,8 +127,11 @@ struct PrepArgs {
   int32_t act_base;       // active index of slots[0]
   int64_t W[7][7];        // W[q][i] = Delta^q_j C(j RUN, i) at j = 0
   uint64_t inv_odd[3][3]; // inverses mod 2^192 of 3, 15, 45
-  int32_t slots[MAX_ACTIVE_PER_LAUNCH];
+  int32_t slots[CAP];
 };
+using PrepArgs = PrepArgsT<MAX_ACTIVE_PER_LAUNCH>;
+constexpr int SMALL_PREP = 1024;
+static_assert(sizeof(PrepArgs) <= 32764, "prep kernel parameters fit the 32 KB parameter space");
 
 struct RenderArgs {
   const ToneRec* tones;

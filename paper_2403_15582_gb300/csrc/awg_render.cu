@@ -424,8 +424,8 @@ __device__ __forceinline__ uint64_t round_q64(unsigned __int128 v) {
 
 // The stride-RUN records of a tile from the unit-stride forward differences h[1..DEG] of the
 // chirp phase at the tile start (Q64.64 words, mod 2^128) and its phase word B0.
-template <int DEG>
-__device__ __forceinline__ void stride_records(const unsigned __int128* h, uint64_t B0, const PrepArgs& a,
+template <int DEG, class Args>
+__device__ __forceinline__ void stride_records(const unsigned __int128* h, uint64_t B0, const Args& a,
                                                TileRec& out) {
 #pragma unroll
   for (int q = 0; q < 7; ++q) {
@@ -460,8 +460,8 @@ __device__ __forceinline__ void stride_records(const unsigned __int128* h, uint6
 // DEG = 2 (linear chirps) or 6 (minimum-jerk).  The unit-stride differences at the tile start
 // are exact (192-bit); the stride-RUN transform that follows only needs the word-level result,
 // so it runs on the upper 128 bits (error < W 2^-64 word per term, below 2^-20 word).
-template <int DEG>
-__device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const PrepArgs& a, TileRec& out) {
+template <int DEG, class Args>
+__device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const Args& a, TileRec& out) {
   U192 bin[DEG + 1];
   binomials_deg<DEG>(m, a.inv_odd, bin);
   U192 acc[DEG + 1];
@@ -482,7 +482,8 @@ __device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const Pre
 // start are C e^(alpha m) q^k (k >= 1, q = e^alpha - 1), in FP64 (a few 1e-10 turn), cut after
 // order 6: the set-up gives a chirp a per-sample table instead when the dropped orders could
 // reach 2^-26 turn over a tile.
-__device__ __forceinline__ void prep_exp(const ChirpRec& c, int64_t m, const PrepArgs& a, TileRec& out) {
+template <class Args>
+__device__ __forceinline__ void prep_exp(const ChirpRec& c, int64_t m, const Args& a, TileRec& out) {
   const double alpha = __longlong_as_double((long long)c.d[2]);
   const double C = __longlong_as_double((long long)c.d[3]);
   const double q = __longlong_as_double((long long)c.d[4]);
@@ -516,7 +517,8 @@ __device__ bool wait_counter(const unsigned long long* ctr, unsigned long long t
   return true;
 }
 
-__global__ void __launch_bounds__(128, 5) prep_kernel(const __grid_constant__ PrepArgs a) {
+template <class Args>
+__global__ void __launch_bounds__(128, 5) prep_kernel(const __grid_constant__ Args a) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t total = (int64_t)a.n_active * a.n_tiles;
   if (idx >= total) return;
@@ -1236,7 +1238,24 @@ cudaError_t launch_prep(const PrepArgs& a, cudaStream_t s) {
   const int64_t total = (int64_t)a.n_active * a.n_tiles;
   if (total == 0) return cudaSuccess;
   const int blocks = (int)((total + 127) / 128);
-  prep_kernel<<<blocks, 128, 0, s>>>(a);
+  if (a.n_active <= SMALL_PREP) {   // the small parameter form: fewer bytes copied with the launch
+    PrepArgsT<SMALL_PREP> b;
+    b.chirps = a.chirps;
+    b.recs = a.recs;
+    b.act_of_slot = a.act_of_slot;
+    b.tile0 = a.tile0;
+    b.n_tiles = a.n_tiles;
+    b.n_active = a.n_active;
+    b.act_base = a.act_base;
+    for (int q = 0; q < 7; ++q)
+      for (int i = 0; i < 7; ++i) b.W[q][i] = a.W[q][i];
+    for (int q = 0; q < 3; ++q)
+      for (int i = 0; i < 3; ++i) b.inv_odd[q][i] = a.inv_odd[q][i];
+    for (int i = 0; i < a.n_active; ++i) b.slots[i] = a.slots[i];
+    prep_kernel<PrepArgsT<SMALL_PREP>><<<blocks, 128, 0, s>>>(b);
+  } else {
+    prep_kernel<PrepArgs><<<blocks, 128, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 
