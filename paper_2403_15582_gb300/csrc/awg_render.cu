@@ -152,7 +152,11 @@ __device__ __forceinline__ uint64_t exact_word(const ToneRec& t, const ChirpRec*
 // ------------------------------------------------------------------------------------------
 constexpr uint64_t P_OFFSET = 1ull << 40;   // makes the 23-bit truncation of p round to nearest
 constexpr uint64_t HALF32 = 1ull << 31;
+// P_OFFSET plus half a turn: folded into the records' B_0 (stride_records)
+constexpr uint64_t B0_OFFSET = P_OFFSET + (1ull << 63);
 
+// A run's 32-bit cascade state: p is the run-start phase plus half a turn (the centred form that
+// sin_centred takes), f, g, h its first three differences.
 struct RunPoly {
   uint32_t p, f, g, h;
 };
@@ -194,9 +198,9 @@ struct Top32 {
   uint64_t lo;
   uint32_t hi;
 };
-// start from word x plus an offset (the rounding offsets P_OFFSET and HALF32)
-__device__ __forceinline__ Top32 top_init(uint64_t x, uint64_t off) {
-  return Top32{(uint64_t)(uint32_t)x + (uint32_t)off, (uint32_t)(x >> 32) + (uint32_t)(off >> 32)};
+// start from word x (the records carry the rounding offsets in their order-0 words)
+__device__ __forceinline__ Top32 top_init(uint64_t x) {
+  return Top32{(uint64_t)(uint32_t)x, (uint32_t)(x >> 32)};
 }
 __device__ __forceinline__ void top_mac(Top32& t, uint64_t x, uint32_t c) {
   t.lo += (uint64_t)(uint32_t)x * c;
@@ -212,41 +216,43 @@ __device__ __forceinline__ uint32_t top_get(const Top32& t) { return t.hi + (uin
 constexpr uint64_t HALF32_OFF = 1ull << 31;
 
 // (p, f, g, h) at run j from the stride-RUN records: p = sum_q B_q C(j,q), f = sum_q E_q C(j,q),
-// g = sum_q G_q C(j,q), h = sum_q H_q C(j,q), all mod 2^64, then to 32-bit fixed point: p with the
-// 2^8 offset of the sine argument (floor of (p + 2^40) / 2^32), f, g, h rounded to nearest.
+// g = sum_q G_q C(j,q), h = sum_q H_q C(j,q), all mod 2^64, then the top 32 bits.  The records'
+// order-0 words carry the offsets (stride_records): B_0 the 2^8 offset of the sine argument and
+// half a turn, so p is floor((phase + 2^40) / 2^32) + 2^31; E_0, G_0, H_0 half a unit, so f, g, h
+// round to nearest.
 __device__ __forceinline__ RunPoly poly_state(const TileRec& rc, const RunBin& b, bool linear) {
   RunPoly r;
   if (linear) {   // B_q (q >= 3), E_q (q >= 2), G_q (q >= 1) and H are exactly zero
-    Top32 p = top_init(rc.B[0], 1ull << 40);
+    Top32 p = top_init(rc.B[0]);
     top_mac(p, rc.B[1], b.c1);
     top_mac(p, rc.B[2], b.c2);
-    Top32 f = top_init(rc.E[0], HALF32_OFF);
+    Top32 f = top_init(rc.E[0]);
     top_mac(f, rc.E[1], b.c1);
     r.p = top_get(p);
     r.f = top_get(f);
-    r.g = (uint32_t)((rc.G[0] + HALF32_OFF) >> 32);
+    r.g = (uint32_t)(rc.G[0] >> 32);
     r.h = 0;
     return r;
   }
-  Top32 p = top_init(rc.B[0], 1ull << 40);
+  Top32 p = top_init(rc.B[0]);
   top_mac(p, rc.B[1], b.c1);
   top_mac(p, rc.B[2], b.c2);
   top_mac(p, rc.B[3], b.c3);
   top_mac(p, rc.B[4], b.c4);
   top_mac(p, rc.B[5], b.c5);
   top_mac64(p, rc.B[6], b.c6);
-  Top32 f = top_init(rc.E[0], HALF32_OFF);
+  Top32 f = top_init(rc.E[0]);
   top_mac(f, rc.E[1], b.c1);
   top_mac(f, rc.E[2], b.c2);
   top_mac(f, rc.E[3], b.c3);
   top_mac(f, rc.E[4], b.c4);
   top_mac(f, rc.E[5], b.c5);
-  Top32 g = top_init(rc.G[0], HALF32_OFF);
+  Top32 g = top_init(rc.G[0]);
   top_mac(g, rc.G[1], b.c1);
   top_mac(g, rc.G[2], b.c2);
   top_mac(g, rc.G[3], b.c3);
   top_mac(g, rc.G[4], b.c4);
-  Top32 h = top_init(rc.H[0], HALF32_OFF);
+  Top32 h = top_init(rc.H[0]);
   top_mac(h, rc.H[1], b.c1);
   top_mac(h, rc.H[2], b.c2);
   top_mac(h, rc.H[3], b.c3);
@@ -259,20 +265,20 @@ __device__ __forceinline__ RunPoly poly_state(const TileRec& rc, const RunBin& b
 
 // poly_state for a degree-6 chirp whose h is known to round to 0 (TONE_FLAT3): no H polynomial.
 __device__ __forceinline__ RunPoly poly_state_flat3(const TileRec& rc, const RunBin& b) {
-  Top32 p = top_init(rc.B[0], 1ull << 40);
+  Top32 p = top_init(rc.B[0]);
   top_mac(p, rc.B[1], b.c1);
   top_mac(p, rc.B[2], b.c2);
   top_mac(p, rc.B[3], b.c3);
   top_mac(p, rc.B[4], b.c4);
   top_mac(p, rc.B[5], b.c5);
   top_mac64(p, rc.B[6], b.c6);
-  Top32 f = top_init(rc.E[0], HALF32_OFF);
+  Top32 f = top_init(rc.E[0]);
   top_mac(f, rc.E[1], b.c1);
   top_mac(f, rc.E[2], b.c2);
   top_mac(f, rc.E[3], b.c3);
   top_mac(f, rc.E[4], b.c4);
   top_mac(f, rc.E[5], b.c5);
-  Top32 g = top_init(rc.G[0], HALF32_OFF);
+  Top32 g = top_init(rc.G[0]);
   top_mac(g, rc.G[1], b.c1);
   top_mac(g, rc.G[2], b.c2);
   top_mac(g, rc.G[3], b.c3);
@@ -283,18 +289,18 @@ __device__ __forceinline__ RunPoly poly_state_flat3(const TileRec& rc, const Run
 // poly_state for a TONE_LOW6 chirp: FLAT3, and the set-up bounds B_6, E_5 and G_2..G_4 below 64
 // units of 2^-32 turn of phase over a run, so they are left out.
 __device__ __forceinline__ RunPoly poly_state_low6(const TileRec& rc, const RunBin& b) {
-  Top32 p = top_init(rc.B[0], 1ull << 40);
+  Top32 p = top_init(rc.B[0]);
   top_mac(p, rc.B[1], b.c1);
   top_mac(p, rc.B[2], b.c2);
   top_mac(p, rc.B[3], b.c3);
   top_mac(p, rc.B[4], b.c4);
   top_mac(p, rc.B[5], b.c5);
-  Top32 f = top_init(rc.E[0], HALF32_OFF);
+  Top32 f = top_init(rc.E[0]);
   top_mac(f, rc.E[1], b.c1);
   top_mac(f, rc.E[2], b.c2);
   top_mac(f, rc.E[3], b.c3);
   top_mac(f, rc.E[4], b.c4);
-  Top32 g = top_init(rc.G[0], HALF32_OFF);
+  Top32 g = top_init(rc.G[0]);
   top_mac(g, rc.G[1], b.c1);
   return RunPoly{top_get(p), top_get(f), top_get(g), 0u};
 }
@@ -423,7 +429,9 @@ __device__ __forceinline__ uint64_t round_q64(unsigned __int128 v) {
 }
 
 // The stride-RUN records of a tile from the unit-stride forward differences h[1..DEG] of the
-// chirp phase at the tile start (Q64.64 words, mod 2^128) and its phase word B0.
+// chirp phase at the tile start (Q64.64 words, mod 2^128) and its phase word B0.  The order-0
+// words take the run set-up's rounding offsets (poly_state): B_0 + 2^40 + 2^63, E_0, G_0 and
+// H_0 + 2^31.
 template <int DEG, class Args>
 __device__ __forceinline__ void stride_records(const unsigned __int128* h, uint64_t B0, const Args& a,
                                                TileRec& out) {
@@ -432,7 +440,7 @@ __device__ __forceinline__ void stride_records(const unsigned __int128* h, uint6
     unsigned __int128 s = 0;
 #pragma unroll
     for (int i = q; i <= DEG; ++i) s += h[i] * (unsigned __int128)(__int128)a.W[q][i];
-    out.B[q] = (q == 0) ? B0 : (q <= DEG ? round_q64(s) : 0);
+    out.B[q] = (q == 0) ? B0 + B0_OFFSET : (q <= DEG ? round_q64(s) : 0);
   }
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
@@ -440,6 +448,7 @@ __device__ __forceinline__ void stride_records(const unsigned __int128* h, uint6
 #pragma unroll
     for (int i = q; i + 1 <= DEG; ++i) s += h[i + 1] * (unsigned __int128)(__int128)a.W[q][i];
     out.E[q] = (q + 1 <= DEG) ? round_q64(s) : 0;
+    if (q == 0) out.E[0] += HALF32_OFF;
   }
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
@@ -447,6 +456,7 @@ __device__ __forceinline__ void stride_records(const unsigned __int128* h, uint6
 #pragma unroll
     for (int i = q; i + 2 <= DEG; ++i) s += h[i + 2] * (unsigned __int128)(__int128)a.W[q][i];
     out.G[q] = (q + 2 <= DEG) ? round_q64(s) : 0;
+    if (q == 0) out.G[0] += HALF32_OFF;
   }
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -454,6 +464,7 @@ __device__ __forceinline__ void stride_records(const unsigned __int128* h, uint6
 #pragma unroll
     for (int i = q; i + 3 <= DEG; ++i) s += h[i + 3] * (unsigned __int128)(__int128)a.W[q][i];
     out.H[q] = (q + 3 <= DEG) ? round_q64(s) : 0;
+    if (q == 0) out.H[0] += HALF32_OFF;
   }
 }
 
@@ -578,7 +589,7 @@ __device__ __forceinline__ void static_loop(uint32_t p, uint32_t f, float A, Acc
 // Chirp cascade over N samples from acc pair B: p += f, f += g (and g += h with WITH_H).
 template <int B, int N, bool WITH_H>
 __device__ __forceinline__ void cascade(const RunPoly& q, float A, Acc& acc) {
-  uint32_t p = q.p + HALF_TURN, f = q.f, g = q.g;
+  uint32_t p = q.p, f = q.f, g = q.g;
   const uint32_t h = q.h;
 #pragma unroll
   for (int r = 0; r < N; r += 2) {
@@ -669,7 +680,7 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
     const int i2 = (int)max((int64_t)-1, min((int64_t)RUN, tr.n_e - n0));
     uint32_t qa = static_p0(tr.phi_ref, tr.F, n0) + HALF_TURN, qb = static_p0(tr.phi_post_ref, tr.F_end, n0) + HALF_TURN;
     const uint32_t fa = static_f(tr.F), fb = static_f(tr.F_end);
-    uint32_t pp = st.p + HALF_TURN, ff = st.f, gg = st.g;
+    uint32_t pp = st.p, ff = st.f, gg = st.g;
     const uint32_t hh = st.h;
 #pragma unroll
     for (int r = 0; r < RUN; r += 2) {
@@ -717,8 +728,8 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
   } else {
     // a segment boundary inside this run, or a table chirp: choose the segment per sample; the
     // sines go to the run's column of the partial-sum buffer, then into the accumulators
-    const uint32_t p_pre = static_p0(tr.phi_ref, tr.F, n0), f_pre = static_f(tr.F);
-    const uint32_t p_post = static_p0(tr.phi_post_ref, tr.F_end, n0), f_post = static_f(tr.F_end);
+    const uint32_t p_pre = static_p0(tr.phi_ref, tr.F, n0) + HALF_TURN, f_pre = static_f(tr.F);
+    const uint32_t p_post = static_p0(tr.phi_post_ref, tr.F_end, n0) + HALF_TURN, f_post = static_f(tr.F_end);
     const bool exact = (tr.flags & TONE_EXACT) != 0;
     RunPoly st = {0, 0, 0, 0};
     if (!exact && tcls == TILE_CHIRP) st = poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0);
@@ -728,8 +739,8 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
       uint32_t ph;
       if (r < r1) ph = p_pre + (uint32_t)r * f_pre;
       else if (r > r2) ph = p_post + (uint32_t)r * f_post;
-      else ph = exact ? exact_tab[tr.tab_off + (int32_t)(r - r1)] : pp;
-      col[r * RUNS] = sin_centred(ph + HALF_TURN);
+      else ph = exact ? exact_tab[tr.tab_off + (int32_t)(r - r1)] + HALF_TURN : pp;
+      col[r * RUNS] = sin_centred(ph);
       pp += ff;
       ff += gg;
       gg += st.h;
@@ -894,6 +905,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   __shared__ alignas(16) ToneRec s_tone[2][STAGE];
   __shared__ alignas(16) TileRec s_rec[2][STAGE];
   __shared__ alignas(16) Desc s_desc[2][STAGE];
+  __shared__ uint8_t s_order[2][STAGE];          // visit order: linear chirps, LOW6 chirps, the rest
+  __shared__ int s_ngrp[2][3];                    // ends of the linear, LOW6 and static groups
   __shared__ alignas(16) float s_red[TILE];       // general paths: [r][run]; cluster sums: [i][thread]
   __shared__ alignas(8) uint64_t s_bar[4];        // tones[0], tones[1], records[0], records[1]
 
@@ -963,6 +976,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     const int cnt = min(STAGE, l_end - (l_begin + st * STAGE));
     bool need = false;
     const TileRec* src = nullptr;
+    int kind = -1;
     if (tid < cnt) {
       const ToneRec& tr = s_tone[b][tid];
       Desc d;
@@ -995,7 +1009,25 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
       if (ramp && T0 + TILE - 1 > tr.a_ns && T0 < tr.a_ns + tr.a_L) d.kind = DESC_MIXED;
       if (a.skip_static && tile_static(tr, T0)) d.kind = DESC_SKIP;   // summed by the tensor-core engine
       s_desc[b][tid] = d;
+      kind = d.kind;
     }
+    // visit order: the chirps that cover the tile in linear form, those in LOW6 form, the static
+    // tones (SFU or rotator), then the rest; tone order within each group.  The first three
+    // groups run in loops without a per-tone dispatch.  The order of the FP32 sums then depends
+    // on which tones share a stage; with a tone list (the window's listed tones) that changes with
+    // the window, so listed renders keep plain tone order, and every window cut gives the same bits.
+    const int grp = a.tone_list ? 3
+                    : kind == DESC_LINEAR ? 0 : kind == DESC_LOW6 ? 1 : (kind == DESC_STATIC || kind == DESC_STATIC_ROT) ? 2 : 3;
+    const unsigned below = (1u << tid) - 1u;
+    int pos = 0, end = 0;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+      const unsigned m = __ballot_sync(0xffffffffu, tid < cnt && grp == g);
+      if (grp == g) pos = end + __popc(m & below);
+      end += __popc(m);
+      if (tid == 0 && g < 3) s_ngrp[b][g] = end;
+    }
+    if (tid < cnt) s_order[b][pos] = (uint8_t)tid;
     const unsigned mask = __ballot_sync(0xffffffffu, need);
     if (tid == 0) {
       fence_proxy_async();
@@ -1031,35 +1063,56 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     ok &= mbar_wait(&s_bar[2 + b], par);
     if (ok) {
       const int cnt = min(STAGE, l_end - (l_begin + st * STAGE));
-      for (int i = 0; i < cnt; ++i) {
+      const int e_lin = s_ngrp[b][0], e_low6 = s_ngrp[b][1], e_static = s_ngrp[b][2];
+      auto linear = [&](int i) { cascade<0, RUN, false>(poly_state(s_rec[b][i], rb0, true), s_desc[b][i].A, acc); };
+      // LOW6, FLAT3: the third difference rounds to 0 everywhere (set-up bound), g is constant
+      auto low6 = [&](int i) { cascade<0, RUN, false>(poly_state_low6(s_rec[b][i], rb0), s_desc[b][i].A, acc); };
+      auto flat3 = [&](int i) { cascade<0, RUN, false>(poly_state_flat3(s_rec[b][i], rb0), s_desc[b][i].A, acc); };
+      auto static_sfu = [&](int i) {
+        const Desc& d = s_desc[b][i];
+        static_loop<0, RUN>((uint32_t)((mac_u32(d.p0 + P_OFFSET, d.F, run_off)) >> 32) + HALF_TURN, static_f(d.F), d.A, acc);
+      };
+      auto static_rot = [&](int i) {
+        // the exact phase word at the run start, SFU sine and cosine once, then 31 rotations by
+        // the per-sample step on the FP32 pipe (amplitude folded into the phasor)
+        const Desc& d = s_desc[b][i];
+        const float c = d.c, s = d.s;
+        const uint64_t w = d.p0 + (uint64_t)run_off * d.F;
+        float sn, cs;
+        __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
+        float im = d.A * sn, re = d.A * cs;
+#pragma unroll
+        for (int r = 0; r < RUN; ++r) {
+          if (r & 1) acc[r / 2].y += im;
+          else acc[r / 2].x += im;
+          const float t = fmaf(re, c, -im * s);
+          im = fmaf(re, s, im * c);
+          re = t;
+        }
+      };
+      for (int o = 0; o < e_lin; ++o) linear(s_order[b][o]);
+      for (int o = e_lin; o < e_low6; ++o) low6(s_order[b][o]);
+      if (a.sine_mode == SINE_ROTATOR) {
+        for (int o = e_low6; o < e_static; ++o) static_rot(s_order[b][o]);
+      } else {
+        for (int o = e_low6; o < e_static; ++o) static_sfu(s_order[b][o]);
+      }
+      for (int o = e_static; o < cnt; ++o) {
+        const int i = s_order[b][o];
         const Desc& d = s_desc[b][i];
         const int kind = d.kind;
         const float A = d.A;
         if (kind == DESC_SKIP) continue;
         if (kind == DESC_STATIC) {
-          static_loop<0, RUN>((uint32_t)((mac_u32(d.p0 + P_OFFSET, d.F, run_off)) >> 32) + HALF_TURN, static_f(d.F), A, acc);
+          static_sfu(i);
         } else if (kind == DESC_STATIC_ROT) {
-          // the exact phase word at the run start, SFU sine and cosine once, then 31 rotations by
-          // the per-sample step on the FP32 pipe (amplitude folded into the phasor)
-          const float c = d.c, s = d.s;
-          const uint64_t w = d.p0 + (uint64_t)run_off * d.F;
-          float sn, cs;
-          __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
-          float im = A * sn, re = A * cs;
-#pragma unroll
-          for (int r = 0; r < RUN; ++r) {
-            if (r & 1) acc[r / 2].y += im;
-            else acc[r / 2].x += im;
-            const float t = fmaf(re, c, -im * s);
-            im = fmaf(re, s, im * c);
-            re = t;
-          }
+          static_rot(i);
         } else if (kind == DESC_LINEAR) {
-          cascade<0, RUN, false>(poly_state(s_rec[b][i], rb0, true), A, acc);
-        } else if (kind == DESC_FLAT3 || kind == DESC_LOW6) {
-          // the third difference rounds to 0 everywhere (set-up bound): g is constant over the run
-          const TileRec& rc = s_rec[b][i];
-          cascade<0, RUN, false>(kind == DESC_LOW6 ? poly_state_low6(rc, rb0) : poly_state_flat3(rc, rb0), A, acc);
+          linear(i);
+        } else if (kind == DESC_LOW6) {
+          low6(i);
+        } else if (kind == DESC_FLAT3) {
+          flat3(i);
         } else if (kind == DESC_MINJERK) {
           // third difference below 2^-33 turn (long ramps): g is constant over the run, the same
           // integers as the loop with h
@@ -1177,7 +1230,7 @@ __device__ __noinline__ uint32_t phase32_at(const ToneRec& t, const TileRec* rec
   } else {
     q = poly_state(*rec, b, (t.flags & TONE_LINEAR) != 0);
   }
-  return q.p + ur * q.f + c2 * q.g + c3 * q.h;
+  return q.p - HALF_TURN + ur * q.f + c2 * q.g + c3 * q.h;
 }
 
 // Exact phase words of the first n tones at one sample (test hook).
