@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <condition_variable>
@@ -526,7 +527,7 @@ struct awg {
   std::vector<cudaEvent_t> prof_ev;   // 4 per recorded render call
   size_t prof_calls = 0;
   int64_t prof_launches = 0;
-  int64_t W[7][7];
+  uint32_t W[7][7];
   uint64_t inv_odd[3][3];
 };
 
@@ -546,7 +547,8 @@ void fill_constants(awg_t* h) {
           for (int t = 0; t < i; ++t) c = c * (m - t) / (t + 1);
         s += (((q - l) & 1) ? -1 : 1) * bq * c;
       }
-      h->W[q][i] = (int64_t)s;
+      if (s < 0 || s > (s128)UINT32_MAX) std::abort();   // RUN = 32: every entry lies in [0, 2^32)
+      h->W[q][i] = (uint32_t)s;
     }
   const uint64_t odd[3] = {3, 15, 45};
   for (int i = 0; i < 3; ++i) {

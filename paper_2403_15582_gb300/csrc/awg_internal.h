@@ -125,7 +125,7 @@ struct PrepArgsT {
   int32_t n_tiles;
   int32_t n_active;
   int32_t act_base;       // active index of slots[0]
-  int64_t W[7][7];        // W[q][i] = Delta^q_j C(j RUN, i) at j = 0
+  uint32_t W[7][7];       // W[q][i] = Delta^q_j C(j RUN, i) at j = 0 (all below 2^32)
   uint64_t inv_odd[3][3]; // inverses mod 2^192 of 3, 15, 45
   int32_t slots[CAP];
 };

@@ -439,14 +439,14 @@ __device__ __forceinline__ void stride_records(const unsigned __int128* h, uint6
   for (int q = 0; q < 7; ++q) {
     unsigned __int128 s = 0;
 #pragma unroll
-    for (int i = q; i <= DEG; ++i) s += h[i] * (unsigned __int128)(__int128)a.W[q][i];
+    for (int i = q; i <= DEG; ++i) s += h[i] * (unsigned __int128)a.W[q][i];
     out.B[q] = (q == 0) ? B0 + B0_OFFSET : (q <= DEG ? round_q64(s) : 0);
   }
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
     unsigned __int128 s = 0;
 #pragma unroll
-    for (int i = q; i + 1 <= DEG; ++i) s += h[i + 1] * (unsigned __int128)(__int128)a.W[q][i];
+    for (int i = q; i + 1 <= DEG; ++i) s += h[i + 1] * (unsigned __int128)a.W[q][i];
     out.E[q] = (q + 1 <= DEG) ? round_q64(s) : 0;
     if (q == 0) out.E[0] += HALF32_OFF;
   }
@@ -454,7 +454,7 @@ __device__ __forceinline__ void stride_records(const unsigned __int128* h, uint6
   for (int q = 0; q < 5; ++q) {
     unsigned __int128 s = 0;
 #pragma unroll
-    for (int i = q; i + 2 <= DEG; ++i) s += h[i + 2] * (unsigned __int128)(__int128)a.W[q][i];
+    for (int i = q; i + 2 <= DEG; ++i) s += h[i + 2] * (unsigned __int128)a.W[q][i];
     out.G[q] = (q + 2 <= DEG) ? round_q64(s) : 0;
     if (q == 0) out.G[0] += HALF32_OFF;
   }
@@ -462,26 +462,96 @@ __device__ __forceinline__ void stride_records(const unsigned __int128* h, uint6
   for (int q = 0; q < 4; ++q) {
     unsigned __int128 s = 0;
 #pragma unroll
-    for (int i = q; i + 3 <= DEG; ++i) s += h[i + 3] * (unsigned __int128)(__int128)a.W[q][i];
+    for (int i = q; i + 3 <= DEG; ++i) s += h[i + 3] * (unsigned __int128)a.W[q][i];
     out.H[q] = (q + 3 <= DEG) ? round_q64(s) : 0;
     if (q == 0) out.H[0] += HALF32_OFF;
   }
 }
 
+// d c mod 2^192 for a multiplier c whose 64-bit limbs above the first L are zero: the partial
+// products of those limbs are left out (the same value as mul192).
+template <int L>
+__device__ __forceinline__ U192 mul192_limbs(U192 d, U192 c) {
+  const unsigned __int128 p00 = (unsigned __int128)d.w0 * c.w0;
+  const unsigned __int128 p10 = (unsigned __int128)d.w1 * c.w0;
+  unsigned __int128 mid = (p00 >> 64) + (uint64_t)p10;
+  uint64_t top = (uint64_t)(p10 >> 64) + d.w2 * c.w0;
+  if (L >= 2) {
+    const unsigned __int128 p01 = (unsigned __int128)d.w0 * c.w1;
+    mid += (uint64_t)p01;
+    top += (uint64_t)(p01 >> 64) + d.w1 * c.w1;
+  }
+  if (L >= 3) top += d.w0 * c.w2;
+  return U192{(uint64_t)p00, (uint64_t)mid, top + (uint64_t)(mid >> 64)};
+}
+
+// Inverses of 3 and 5 modulo 2^128 / 2^192 (3 * 0xA..AB = 1 and 5 * 0xC..CD = 1 modulo the power of
+// two): an exact quotient by 3 or 5 is a product with the inverse.
+constexpr uint64_t INV3_W = 0xAAAAAAAAAAAAAAAAull, INV3_W0 = 0xAAAAAAAAAAAAAAABull;
+constexpr uint64_t INV5_W = 0xCCCCCCCCCCCCCCCCull, INV5_W0 = 0xCCCCCCCCCCCCCCCDull;
+
+// C(m, j), j = 0..DEG, for 0 <= m < 2^29 (every tile a chirp covers), each from the one before:
+// C(m, j) = C(m, j-1) (m - j + 1) / j.  C(m, 1), C(m, 2) < 2^57 fit one 64-bit limb, C(m, 3) and
+// C(m, 4) < 2^112 two, C(m, 5), C(m, 6) < 2^165 three; the quotients are exact, so a division by 3
+// or 5 is a product with the inverse modulo 2^128 or 2^192 and a division by 2 or 4 a shift.
+template <int DEG>
+__device__ __forceinline__ void binomials_pos(uint64_t m, U192 c[DEG + 1]) {
+  c[0] = U192{1, 0, 0};
+  c[1] = U192{m, 0, 0};
+  const uint64_t c2 = (m * (m - 1)) >> 1;
+  c[2] = U192{c2, 0, 0};
+  if (DEG >= 3) {
+    unsigned __int128 t = (unsigned __int128)c2 * (m - 2);                 // 3 C(m, 3) < 2^86
+    t *= ((unsigned __int128)INV3_W << 64) | INV3_W0;
+    c[3] = U192{(uint64_t)t, (uint64_t)(t >> 64), 0};
+    t = (t * (unsigned __int128)(m - 3)) >> 2;                              // C(m, 4) < 2^112
+    c[4] = U192{(uint64_t)t, (uint64_t)(t >> 64), 0};
+    U192 u = mul192_limbs<1>(c[4], U192{m - 4, 0, 0});                      // 5 C(m, 5)
+    c[5] = mul192(u, U192{INV5_W0, INV5_W, INV5_W});
+    u = mul192_limbs<1>(c[5], U192{m - 5, 0, 0});                           // 6 C(m, 6)
+    u = mul192(u, U192{INV3_W0, INV3_W, INV3_W});                           // 2 C(m, 6)
+    c[6] = U192{(u.w0 >> 1) | (u.w1 << 63), (u.w1 >> 1) | (u.w2 << 63), u.w2 >> 1};
+  }
+}
+
+// sum over i >= k of d_i C(m, i - k), the products by C(m, j) taking its limb count
+template <int DEG>
+__device__ __forceinline__ U192 newton_shift_pos(const ChirpRec& c, const U192* bin, int k) {
+  U192 s = dword(c, k);
+#pragma unroll
+  for (int j = 1; j <= DEG; ++j) {
+    if (k + j > DEG) break;
+    const U192 d = dword(c, k + j);
+    if (j <= 2) s = add192(s, mul192_limbs<1>(d, bin[j]));
+    else if (j <= 4) s = add192(s, mul192_limbs<2>(d, bin[j]));
+    else s = add192(s, mul192_limbs<3>(d, bin[j]));
+  }
+  return s;
+}
+
 // DEG = 2 (linear chirps) or 6 (minimum-jerk).  The unit-stride differences at the tile start
 // are exact (192-bit); the stride-RUN transform that follows only needs the word-level result,
-// so it runs on the upper 128 bits (error < W 2^-64 word per term, below 2^-20 word).
+// so it runs on the upper 128 bits (error < W 2^-64 word per term, below 2^-20 word).  Tiles
+// from the chirp's start on (0 <= m < 2^29) take the binomials' limb counts into account; a tile
+// that begins before the chirp (m < 0) takes signed binomials (both the same integers).
 template <int DEG, class Args>
 __device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const Args& a, TileRec& out) {
-  U192 bin[DEG + 1];
-  binomials_deg<DEG>(m, a.inv_odd, bin);
   U192 acc[DEG + 1];
+  if (m >= 0 && m < ((int64_t)1 << 29)) {
+    U192 bin[DEG + 1];
+    binomials_pos<DEG>((uint64_t)m, bin);
 #pragma unroll
-  for (int k = 0; k <= DEG; ++k) {
-    U192 s = {0, 0, 0};
+    for (int k = 0; k <= DEG; ++k) acc[k] = newton_shift_pos<DEG>(c, bin, k);
+  } else {
+    U192 bin[DEG + 1];
+    binomials_deg<DEG>(m, a.inv_odd, bin);
 #pragma unroll
-    for (int i = k; i <= DEG; ++i) s = add192(s, mul192(dword(c, i), bin[i - k]));
-    acc[k] = s;
+    for (int k = 0; k <= DEG; ++k) {
+      U192 s = {0, 0, 0};
+#pragma unroll
+      for (int i = k; i <= DEG; ++i) s = add192(s, mul192(dword(c, i), bin[i - k]));
+      acc[k] = s;
+    }
   }
   unsigned __int128 h[DEG + 1];
 #pragma unroll
