@@ -13,18 +13,28 @@ def run_stream(synth, ring, chirps, n_chunks: int, stream=None, prefill: int = 2
     pushed, every chirp starting before the chunk's end is handed to the synthesiser.
     producer_delay_s: extra host delay before each push (to provoke underruns in tests).
     Returns the ring statistics (dict) plus the producer's wall time."""
+    import numpy as np
     order = sorted(chirps, key=lambda c: c.get("start_sample", 0))
+    # each chunk's batch as arrays, built before playback starts: the loop below only hands them to
+    # the library
+    batches = []
     nxt = 0
+    for c in range(n_chunks):
+        end = (c + 1) * ring.chunk
+        first = nxt
+        while nxt < len(order) and order[nxt].get("start_sample", 0) < end:
+            nxt += 1
+        b = order[first:nxt]
+        batches.append(None if not b else (
+            np.array([x["tone"] for x in b], dtype=np.int32), np.array([x["f_start"] for x in b], dtype=np.float64),
+            np.array([x["f_end"] for x in b], dtype=np.float64), np.array([x["duration"] for x in b], dtype=np.float64),
+            np.array([x["profile"] for x in b], dtype=np.int32),
+            np.array([x.get("start_sample", 0) for x in b], dtype=np.int64)))
     ring.start(prefill, n_chunks, capture)
     t0 = time.perf_counter()
     for c in range(n_chunks):
-        end = (c + 1) * ring.chunk
-        batch = []
-        while nxt < len(order) and order[nxt].get("start_sample", 0) < end:
-            batch.append(order[nxt])
-            nxt += 1
-        if batch:
-            synth.set_chirp_list(batch)
+        if batches[c] is not None:
+            synth.set_chirps(*batches[c])
         if producer_delay_s:
             time.sleep(producer_delay_s)
         ring.push(stream, push_timeout_ms)
