@@ -10,17 +10,18 @@
 // memory and quantises in the epilogue.
 //
 // Kernel structure: a cluster of S CTAs per 128-row tile of X splits the K dimension (fewer FP32
-// accumulations per chain); each CTA (192 threads) has a 2-stage ring of
+// accumulations per chain); each CTA (320 threads) has a 2-stage ring of
 // {A_hi, A_lo (128 x 64), B_hi, B_lo (256 x 64)} tiles in the 128-byte-swizzled K-major layout:
 //   warp 0   TMA producer of the B tiles (prepared once per call, 256 x 2K, L2-resident),
 //            mbarrier transaction counts
 //   warp 1   allocates 512 TMEM columns; lane 0 issues tcgen05.mma (M 128, N 256, K 16) x 3 passes
 //            x 4 k-steps per stage, commits each stage back to the producers
-//   warps 2-5 generate the A tiles in shared memory (one tone per lane, every fourth row per warp:
+//   warps 2-9 generate the A tiles in shared memory (one tone per lane, every eighth row per warp:
 //            A_k sin a_k(n1), A_k cos a_k(n1) from the exact phase word, SFU sine and cosine, hi + lo
 //            split), so the M x 2K A
 //            operand never exists in HBM; then the epilogue: tcgen05.ld 32x32b of both
-//            accumulators into a padded FP32 partial tile in shared memory; the cluster sums the S
+//            accumulators (warp w reads TMEM lane quarter w mod 4, half of the columns) into a
+//            padded FP32 partial tile in shared memory; the cluster sums the S
 //            partial tiles through distributed shared memory in rank order, and each CTA scales,
 //            rounds, clamps and stores its rows.
 // Every wait is bounded (about 2 s); on a timeout the CTA records AWG_ETIMEOUT, lets in-flight
@@ -46,6 +47,11 @@ constexpr int TM = 128;               // rows of X per CTA (UMMA M)
 constexpr int TN = 256;               // NB: columns of X (UMMA N)
 constexpr int TK = 64;                // K elements per stage (128 bytes of 16-bit values)
 constexpr int NSTAGE = 2;
+// A-operand generator warps (rows g, g + NGEN, ...): eight keep the tensor pipe fed (four left the
+// MMAs waiting for the A tiles: 1.44 -> 1.29 ms on the 10,000-tone 2^24 table; sixteen, no faster)
+constexpr int NGEN = 8;
+constexpr int GEMM_THREADS = 32 * (2 + NGEN);
+static_assert(NGEN % 4 == 0 && TM % NGEN == 0, "generator warps cover every TMEM lane quarter and every row");
 constexpr uint32_t A_TILE = TM * TK * 2;   // 16 KB
 constexpr uint32_t B_TILE = TN * TK * 2;   // 32 KB
 constexpr uint32_t STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // 96 KB
@@ -203,15 +209,15 @@ __device__ __forceinline__ void gen_a_tile(const TableGemmArgs& a, int kt0, uint
     }
     const uint64_t f8 = F << a.nb_log2;
     w = phi + (uint64_t)(a.row_base + (int64_t)row0 + g) * f8;
-    step = f8 << 2;
+    step = f8 * (uint64_t)NGEN;
     amp = A * a.a_scale;
     amp_end *= a.a_scale;
   }
   const uint32_t col = (uint32_t)(lane & 3) * 4u;
   const uint32_t chunk = (uint32_t)(lane >> 2);
 #pragma unroll 8
-  for (int i = 0; i < TM / 4; ++i) {
-    const uint32_t r = (uint32_t)(g + 4 * i);
+  for (int i = 0; i < TM / NGEN; ++i) {
+    const uint32_t r = (uint32_t)(g + NGEN * i);
     float sn, cs;
     __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
     float a_row = amp;
@@ -239,12 +245,12 @@ __device__ __forceinline__ void gen_a_rows(const TableGemmArgs& a, uint64_t phi,
                                            int g, int lane, uint32_t tile_hi, uint32_t tile_lo) {
   const uint64_t f8 = F << a.nb_log2;
   uint64_t w = phi + (uint64_t)(a.row_base + (int64_t)row0 + g) * f8;
-  const uint64_t step = f8 << 2;
+  const uint64_t step = f8 * (uint64_t)NGEN;
   const uint32_t col = (uint32_t)(lane & 3) * 4u;
   const uint32_t chunk = (uint32_t)(lane >> 2);
 #pragma unroll 8
-  for (int i = 0; i < TM / 4; ++i) {
-    const uint32_t r = (uint32_t)(g + 4 * i);
+  for (int i = 0; i < TM / NGEN; ++i) {
+    const uint32_t r = (uint32_t)(g + NGEN * i);
     float sn, cs;
     __sincosf((float)(int32_t)(w >> 32) * 1.46291807926715968e-9f, &sn, &cs);   // 2 pi / 2^32
     const float sv = A * sn, cv = A * cs;
@@ -259,7 +265,7 @@ __device__ __forceinline__ void gen_a_rows(const TableGemmArgs& a, uint64_t phi,
 }
 
 template <typename T, bool WINDOW>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(GEMM_THREADS, 1)
     table_gemm_kernel(const __grid_constant__ CUtensorMap mB_hi, const __grid_constant__ CUtensorMap mB_lo,
                       const __grid_constant__ TableGemmArgs a) {
   extern __shared__ uint8_t dyn_smem[];
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(192, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(full0 + 8 * s, 1 + 4);   // the B copies' transaction arrive + four generator warps
+      mbar_init(full0 + 8 * s, 1 + NGEN);   // the B copies' transaction arrive + one per generator warp
       mbar_init(empty0 + 8 * s, 1);
     }
     mbar_init(done, 1);
@@ -347,7 +353,7 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp >= 2) {
     // ---------------- A operand generation ----------------
     {
-      const int g = warp - 2;   // rows g, g + 4, ...
+      const int g = warp - 2;   // rows g, g + NGEN, ...
       for (int kb = 0; kb < n_kb; ++kb) {
         const int s = kb % NSTAGE;
         // table mode: this k-block's tone words are loaded before the wait for the stage, so
@@ -382,9 +388,12 @@ __global__ void __launch_bounds__(192, 1)
     const int row = lane_base + lane;                // row of the tile = TMEM lane
     const bool go = __all_sync(0xffffffffu, ok && !s_fail);   // warp-uniform: tcgen05.ld is .aligned
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // stage memory becomes the partial tile
+    // warps with the same lane quarter take consecutive column ranges of the tile
+    constexpr int COLS = TN / (NGEN / 4);
+    const int c_begin = ((warp - 2) / 4) * COLS;
     if (go) {
 #pragma unroll 1
-      for (int c0 = 0; c0 < TN; c0 += 32) {
+      for (int c0 = c_begin; c0 < c_begin + COLS; c0 += 32) {
         uint32_t v[32], w[32];
         const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)c0;
         asm volatile(
@@ -593,7 +602,7 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
     if (!active[c]) {
       cudaLaunchConfig_t q = {};
       q.gridDim = dim3(c, 1, 1);
-      q.blockDim = dim3(192, 1, 1);
+      q.blockDim = dim3(GEMM_THREADS, 1, 1);
       q.dynamicSmemBytes = smem;
       cudaLaunchAttribute qa[1];
       qa[0].id = cudaLaunchAttributeClusterDimension;
@@ -618,7 +627,7 @@ cudaError_t launch_table_gemm(const TableArgs2& t, cudaStream_t s) {
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)tiles * split, 1, 1);
-  cfg.blockDim = dim3(192, 1, 1);
+  cfg.blockDim = dim3(GEMM_THREADS, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
