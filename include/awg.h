@@ -379,12 +379,13 @@ const int16_t* awg_ring_slot(const awg_ring_t* r, int32_t i);
  * Served request stream with continuous batching.  A request is a waveform (a comb of tones, some
  * of them chirped, as in the rearrangement of Sec. V-B) that asks for n_chunks consecutive chunks
  * of `chunk` samples, played back at fs one after another (the chunked streaming of Sec. IV).
- * Timing: chunk 0 is rendered as soon as the request is set up on the device; playback starts
- * when it is complete (t_play; its latency from submission is reported as the first-chunk time).
- * Chunk c >= 1 is due when chunk c-1 ends playing, t_play + c chunk/fs (a chunk completed after
+ * Timing: the first `depth` chunks (awg_server_set_prefetch; default 2; fewer if the request has
+ * fewer) are the start-up: rendered as soon as the request is set up on the device; playback
+ * starts when they are all complete (t_play; its latency from submission is reported as the
+ * first-chunk time), like a FIFO ahead of the DAC that is filled before the DAC starts.  Every
+ * later chunk c is due when chunk c-1 ends playing, t_play + c chunk/fs (a chunk completed after
  * that is a deadline miss: an underrun of the player), and is released for rendering `depth`
- * chunk periods earlier (awg_server_set_prefetch; default 2), but not before t_play: like a FIFO
- * that holds the chunks ahead of the DAC.
+ * chunk periods earlier.
  * Admission: a request is admitted while the device-memory budget and max_active allow and the
  * real-time budget holds with it: each chunk's window (its look-ahead less the queue horizon, the
  * round cost, twice the longest CTA that cannot be preempted and an allowance for the host's
@@ -422,11 +423,11 @@ typedef struct {
 typedef struct {
   int64_t submitted, admitted, rejected_deadline, rejected_memory, completed;
   int64_t chunks, deadline_misses;  /* chunks rendered; of those, completed after their deadline */
-  double latency_p50_ms;            /* chunks c >= 1: completion minus release */
+  double latency_p50_ms;            /* streamed chunks (c >= depth): completion minus release */
   double latency_p99_ms;
   double latency_max_ms;
-  double latency_p99_of_period;     /* chunks c >= 1: p99 of (completion - release) / playback period */
-  double first_chunk_p50_ms;        /* chunk 0: completion minus submission (queue + set-up + render) */
+  double latency_p99_of_period;     /* streamed chunks: p99 of (completion - release) / playback period */
+  double first_chunk_p50_ms;        /* playback start (start-up complete) minus submission */
   double first_chunk_p99_ms;
   int64_t rounds;
   double mean_batch;                /* pieces (requests) per round */
@@ -454,8 +455,9 @@ awg_server_t* awg_server_create(double sample_rate_hz, int64_t mem_budget_bytes,
  * (the default) renders every tone directly.  Set before the first request; AWG_ESTATE after. */
 int awg_server_set_static_engine(awg_server_t* s, int32_t engine, int32_t min_tones);
 
-/* Chunks rendered ahead of playback (1 .. 16, default 2): chunk c is released when chunk c - depth
- * starts playing.  Set before the first request; AWG_ESTATE after. */
+/* Chunks rendered ahead of playback (1 .. 16, default 2): the first `depth` chunks are rendered
+ * before playback starts, and chunk c is released when chunk c - depth starts playing.  Set
+ * before the first request; AWG_ESTATE after. */
 int awg_server_set_prefetch(awg_server_t* s, int32_t chunks);
 
 /* Stop the scheduler, wait for in-flight work and free everything.  NULL is allowed. */
@@ -488,14 +490,14 @@ typedef struct {
   double t_issued;                  /* host: all launches of the round issued */
   double t_start, t_done;           /* device: round start and end */
   double work;                      /* tone-samples */
-  double first_due;                 /* earliest due time among the round's chunks (c >= 1) */
+  double first_due;                 /* earliest due time among the round's streamed chunks */
   int32_t pieces, tiles;
 } awg_round_record_t;
 
 typedef struct {
   int64_t id;                       /* request */
   int32_t chunk, late;              /* late: completed after its due time */
-  double release, due, done;        /* chunk 0: release = set-up done, due = release + period */
+  double release, due, done;        /* start-up chunk c: release = set-up done, due = release + (c+1) period */
 } awg_chunk_record_t;
 
 int32_t awg_server_trace_rounds(awg_server_t* s, awg_round_record_t* out, int32_t cap);

@@ -534,6 +534,20 @@ __device__ __forceinline__ U192 newton_shift_pos(const ChirpRec& c, const U192* 
 // so it runs on the upper 128 bits (error < W 2^-64 word per term, below 2^-20 word).  Tiles
 // from the chirp's start on (0 <= m < 2^29) take the binomials' limb counts into account; a tile
 // that begins before the chirp (m < 0) takes signed binomials (both the same integers).
+// the unit-stride differences at a tile that begins before the chirp (signed binomials)
+template <int DEG>
+__device__ __forceinline__ void newton_shift_signed(const ChirpRec& c, int64_t m, const uint64_t (*inv)[3], U192* acc) {
+  U192 bin[DEG + 1];
+  binomials_deg<DEG>(m, inv, bin);
+#pragma unroll
+  for (int k = 0; k <= DEG; ++k) {
+    U192 s = {0, 0, 0};
+#pragma unroll
+    for (int i = k; i <= DEG; ++i) s = add192(s, mul192(dword(c, i), bin[i - k]));
+    acc[k] = s;
+  }
+}
+
 template <int DEG, class Args>
 __device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const Args& a, TileRec& out) {
   U192 acc[DEG + 1];
@@ -543,15 +557,7 @@ __device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const Arg
 #pragma unroll
     for (int k = 0; k <= DEG; ++k) acc[k] = newton_shift_pos<DEG>(c, bin, k);
   } else {
-    U192 bin[DEG + 1];
-    binomials_deg<DEG>(m, a.inv_odd, bin);
-#pragma unroll
-    for (int k = 0; k <= DEG; ++k) {
-      U192 s = {0, 0, 0};
-#pragma unroll
-      for (int i = k; i <= DEG; ++i) s = add192(s, mul192(dword(c, i), bin[i - k]));
-      acc[k] = s;
-    }
+    newton_shift_signed<DEG>(c, m, a.inv_odd, acc);
   }
   unsigned __int128 h[DEG + 1];
 #pragma unroll

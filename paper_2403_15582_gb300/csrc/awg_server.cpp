@@ -58,7 +58,10 @@ struct Request {
   int64_t issue_off = 0;
   int32_t done_chunks = 0;     // chunks complete on the device
   double t_ready = -1;         // set-up finished
-  double t_play = -1;          // chunk 0 complete: playback starts
+  int32_t n_start = 1;         // start-up chunks (min(depth, n_chunks)), rendered before playback
+  int32_t start_done = 0;      // start-up chunks complete
+  double t_start_max = 0;      // latest completion among them
+  double t_play = -1;          // every start-up chunk complete: playback starts
   double t_pieces = 0;         // latest completion among the pieces of the chunk being completed
 };
 
@@ -190,11 +193,13 @@ namespace {
 
 double now_s(const awg_server_t* s) { return std::chrono::duration<double>(clk::now() - s->t0).count(); }
 
-// Release and due time of chunk c >= 1 of a playing request (server clock): due when chunk c-1
-// ends playing, t_play + c period; released a look-ahead of `depth` periods earlier, but not
-// before chunk 0 is complete (t_play).  With depth 1 a chunk is released when the one before
-// starts playing (double buffering).  (A minimum look-ahead of 1 ms for short chunks was tried:
-// chunks released that early crowded the device queue and more of them missed.)
+// Release and due time of a streamed chunk c >= depth of a playing request (server clock): due
+// when chunk c-1 ends playing, t_play + c period; released a look-ahead of `depth` periods
+// earlier, which is never before t_play.  The first `depth` chunks (the start-up) are rendered
+// before playback starts, so every streamed chunk has the whole look-ahead.  (With playback
+// starting after chunk 0 alone, chunk 1 had one period instead of `depth`: the chunks that missed
+// at low load.  A minimum look-ahead of 1 ms for short chunks was tried as well: chunks released
+// that early crowded the device queue and more of them missed.)
 double lookahead(const awg_server_t* s, const Request* r) { return (double)s->depth * r->period; }
 double chunk_due(const Request* r, int32_t c) { return r->t_play + (double)c * r->period; }
 double chunk_release(const awg_server_t* s, const Request* r, int32_t c) {
@@ -354,6 +359,7 @@ void worker_main(awg_server_t* s) {
       if (ok) {
         r->ready = true;
         r->t_ready = now_s(s);
+        r->n_start = std::max<int32_t>(1, std::min(s->depth, r->n_chunks));
       } else {
         s->error = std::string("request set-up failed: ") + awg_last_error();
         r->state = AWG_REQ_REJECTED;
@@ -440,9 +446,10 @@ void admit(awg_server_t* s) {
   if (changed) s->cv.notify_all();   // worker; awg_server_drain / poll
 }
 
-// Earliest-deadline-first plan of one round at time `now`.  Chunk 0 of a request is released when
-// its set-up is done; it starts playback when it completes (t_play), and chunk c >= 1 is due when
-// chunk c-1 ends (t_play + c period) and released `depth` periods earlier (chunk_release).  A round takes what fills the device's queue up to the horizon; a chunk
+// Earliest-deadline-first plan of one round at time `now`.  The start-up chunks of a request
+// (the first min(depth, n_chunks)) are released when its set-up is done; it starts playback when
+// they are all complete (t_play), and chunk c >= depth is due when chunk c-1 ends (t_play + c
+// period) and released `depth` periods earlier (chunk_release).  A round takes what fills the device's queue up to the horizon; a chunk
 // that does not fit is cut into whole tiles and continued in later rounds.
 // Returns the earliest future release in *next_release.  Lock held.
 void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
@@ -458,11 +465,11 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
     if (!r->ready || r->issue_chunk >= r->n_chunks) continue;
     const int32_t c = r->issue_chunk;
     double rel, due;
-    if (c == 0) {
+    if (c < r->n_start) {            // start-up chunk: released at once, ordered by index
       rel = r->t_ready;
-      due = r->t_ready + r->period;
+      due = r->t_ready + (double)(c + 1) * r->period;
     } else {
-      if (r->t_play < 0) continue;   // chunk 0 still in flight
+      if (r->t_play < 0) continue;   // start-up still in flight
       rel = chunk_release(s, r, c);
       due = chunk_due(r, c);
     }
@@ -478,7 +485,7 @@ void plan_round(awg_server_t* s, double now, Round* rd, double* next_release) {
   std::sort(cands.begin(), cands.end(), [](const Cand& x, const Cand& y) { return x.due < y.due; });
   rd->rec.first_due = 1e30;
   for (const Cand& cd : cands)
-    if (cd.r->issue_chunk > 0) {
+    if (cd.r->issue_chunk >= cd.r->n_start) {
       rd->rec.first_due = cd.due;
       break;
     }
@@ -685,11 +692,14 @@ void complete_round(awg_server_t* s) {
     cr.id = r->id;
     cr.chunk = p.chunk;
     cr.done = t_chunk;
-    if (p.chunk == 0) {
-      r->t_play = t_chunk;
-      s->ttfc.push_back(t_chunk - r->t_arrival);
+    if (p.chunk < r->n_start) {
+      r->t_start_max = std::max(r->t_start_max, t_chunk);
+      if (++r->start_done == r->n_start) {   // the player's buffer is full: playback starts
+        r->t_play = r->t_start_max;
+        s->ttfc.push_back(r->t_play - r->t_arrival);
+      }
       cr.release = r->t_ready;
-      cr.due = r->t_ready + r->period;
+      cr.due = r->t_ready + (double)(p.chunk + 1) * r->period;
     } else {
       const double rel = chunk_release(s, r, p.chunk);
       s->lat.push_back(t_chunk - rel);
