@@ -626,9 +626,9 @@ __global__ void __launch_bounds__(128, 5) prep_kernel(const __grid_constant__ Ar
 // render
 // ------------------------------------------------------------------------------------------
 // Accumulators: a thread's RUN partial sums as RUN / 2 pairs of consecutive samples (float2).
-// The static loop computes the sine arguments and the multiply-adds of two samples as packed FP32
-// pairs (each component rounds as fmaf, so the sums are the same bits as with scalar fmaf); the
-// chirp loops stay scalar (there the packed form lowered the issue rate more than it saved).
+// The static and chirp loops compute the sine arguments and the multiply-adds of two samples as
+// packed FP32 pairs (each component rounds as fmaf, so the sums are the same bits as with scalar
+// fmaf): one instruction per tone-sample fewer (8.5 -> 7.5 on the 1000-chirp record).
 typedef float2 Acc[RUN / 2];
 
 constexpr float TWO_PI_F = 6.28318530717958647692f;
@@ -672,7 +672,7 @@ __device__ __forceinline__ void cascade(const RunPoly& q, float A, Acc& acc) {
     const uint32_t p1 = p + f;
     uint32_t f1 = f + g;
     if (WITH_H) g += h;
-    acc_pair(acc[B + r / 2], A, A, p, p1);
+    acc_pair_packed(acc[B + r / 2], A, p, p1);
     p = p1 + f1;
     f = f1 + g;
     if (WITH_H) g += h;
