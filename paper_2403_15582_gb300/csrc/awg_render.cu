@@ -514,19 +514,23 @@ __device__ __forceinline__ void binomials_pos(uint64_t m, U192 c[DEG + 1]) {
   }
 }
 
-// sum over i >= k of d_i C(m, i - k), the products by C(m, j) taking its limb count
+// acc[k] = sum over i >= k of d_i C(m, i - k), k = 0..DEG, the products by C(m, j) taking its limb
+// count.  Each d_i is loaded once and added into every acc[k] it contributes to (the sums are
+// exact mod 2^192, so their order does not matter).
 template <int DEG>
-__device__ __forceinline__ U192 newton_shift_pos(const ChirpRec& c, const U192* bin, int k) {
-  U192 s = dword(c, k);
+__device__ __forceinline__ void newton_shift_pos(const ChirpRec& c, const U192* bin, U192* acc) {
 #pragma unroll
-  for (int j = 1; j <= DEG; ++j) {
-    if (k + j > DEG) break;
-    const U192 d = dword(c, k + j);
-    if (j <= 2) s = add192(s, mul192_limbs<1>(d, bin[j]));
-    else if (j <= 4) s = add192(s, mul192_limbs<2>(d, bin[j]));
-    else s = add192(s, mul192_limbs<3>(d, bin[j]));
+  for (int i = 0; i <= DEG; ++i) {
+    const U192 d = dword(c, i);
+    acc[i] = d;
+#pragma unroll
+    for (int k = 0; k < i; ++k) {
+      const int j = i - k;
+      if (j <= 2) acc[k] = add192(acc[k], mul192_limbs<1>(d, bin[j]));
+      else if (j <= 4) acc[k] = add192(acc[k], mul192_limbs<2>(d, bin[j]));
+      else acc[k] = add192(acc[k], mul192_limbs<3>(d, bin[j]));
+    }
   }
-  return s;
 }
 
 // DEG = 2 (linear chirps) or 6 (minimum-jerk).  The unit-stride differences at the tile start
@@ -554,8 +558,7 @@ __device__ __forceinline__ void prep_one(const ChirpRec& c, int64_t m, const Arg
   if (m >= 0 && m < ((int64_t)1 << 29)) {
     U192 bin[DEG + 1];
     binomials_pos<DEG>((uint64_t)m, bin);
-#pragma unroll
-    for (int k = 0; k <= DEG; ++k) acc[k] = newton_shift_pos<DEG>(c, bin, k);
+    newton_shift_pos<DEG>(c, bin, acc);
   } else {
     newton_shift_signed<DEG>(c, m, a.inv_odd, acc);
   }
