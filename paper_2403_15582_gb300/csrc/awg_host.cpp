@@ -2113,6 +2113,7 @@ int awg_table_gemm(awg_t* h, int32_t log2_len, int32_t precision, int16_t* out_q
   int st = ensure(&h->d_gemm, &h->cap_gemm, 2 * b_elems, h, "table GEMM operands");
   if (st) return st;
   awgk::TableArgs2 t;
+  std::memset(&t, 0, sizeof(t));   // every field not set below is 0 (a periodic table's K split is free)
   t.tones = h->d_tones;
   t.K = h->K;
   t.M = M;
