@@ -1368,10 +1368,6 @@ std::vector<int32_t> active_slots(const awg_t* h, int64_t c, int64_t n, int64_t*
     if (cr.tone < 0 || (cr.flags & awgk::TONE_EXACT)) continue;
     if (cr.n_s <= span1 && cr.n_s + cr.L >= span0) active.push_back((int32_t)sl);
   }
-  // linear chirps first: the set-up threads of one profile then share SMs and instruction cache
-  // (records are found through act_of_slot, so their order is free)
-  std::stable_partition(active.begin(), active.end(),
-                        [&](int32_t sl) { return (h->chirps[(size_t)sl].flags & awgk::TONE_LINEAR) != 0; });
   *tile0 = t0;
   *n_tiles = (int32_t)(t1 - t0 + 1);
   return active;
