@@ -125,19 +125,34 @@ Big big_shl(const Big& a, int s) {   // s < 512
   }
   return r;
 }
+// Division of n < 2^64 by an invariant divisor d < 2^32 through its reciprocal inv = floor((2^64 -
+// 1) / d): the estimate floor(n inv / 2^64) is below n / d by less than n / 2^64 + 1 < 2, so at
+// most two corrections give the exact quotient and remainder.
+struct Div32 {
+  uint64_t d, inv;
+  explicit Div32(uint64_t dd) : d(dd), inv(~0ull / dd) {}
+  uint64_t divmod(uint64_t n, uint64_t* r) const {
+    uint64_t q = (uint64_t)(((u128)n * inv) >> 64);
+    uint64_t rem = n - q * d;
+    while (rem >= d) {
+      rem -= d;
+      ++q;
+    }
+    *r = rem;
+    return q;
+  }
+};
+
 uint64_t big_divmod_u64(Big& a, uint64_t d) {   // a /= d, returns remainder
   int top = 7;
   while (top > 0 && a.l[top] == 0) --top;         // leading zero limbs stay zero
   if (d < (1ull << 32)) {
-    // 32-bit halves: every partial dividend is below 2^64, so 64-bit hardware division does
+    // 32-bit halves: every partial dividend is below 2^64, divided through the reciprocal of d
+    const Div32 dv(d);
     uint64_t rem = 0;
     for (int i = top; i >= 0; --i) {
-      const uint64_t hi = (rem << 32) | (a.l[i] >> 32);
-      const uint64_t qh = hi / d;
-      rem = hi - qh * d;
-      const uint64_t lo = (rem << 32) | (a.l[i] & 0xFFFFFFFFull);
-      const uint64_t ql = lo / d;
-      rem = lo - ql * d;
+      const uint64_t qh = dv.divmod((rem << 32) | (a.l[i] >> 32), &rem);
+      const uint64_t ql = dv.divmod((rem << 32) | (a.l[i] & 0xFFFFFFFFull), &rem);
       a.l[i] = (qh << 32) | ql;
     }
     return rem;
@@ -216,11 +231,12 @@ void binomials_w(int64_t m, W192 c[7]) {
       continue;
     }
     const W192 p = w_mul(c[k - 1], w_from_u64((uint64_t)(m - k + 1)));
-    u128 rem = 0;
+    const Div32 dv((uint64_t)k);   // 32-bit halves, as in big_divmod_u64
+    uint64_t rem = 0;
     for (int i = 2; i >= 0; --i) {
-      const u128 cur = (rem << 64) | p.w[i];
-      c[k].w[i] = (uint64_t)(cur / (uint64_t)k);
-      rem = cur % (uint64_t)k;
+      const uint64_t qh = dv.divmod((rem << 32) | (p.w[i] >> 32), &rem);
+      const uint64_t ql = dv.divmod((rem << 32) | (p.w[i] & 0xFFFFFFFFull), &rem);
+      c[k].w[i] = (qh << 32) | ql;
     }
   }
 }
