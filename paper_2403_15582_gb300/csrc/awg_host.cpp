@@ -1687,7 +1687,6 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   }
   int st;
   h->periodic_start = -1;
-  const size_t slots_before = h->chirps.size();
   // the coefficient words, end offsets and exact-table flags of every chirp: pure functions of
   // the chirp, computed on several host threads for large batches
   struct Coeffs {
@@ -1762,8 +1761,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   changed_slots.erase(std::unique(changed_slots.begin(), changed_slots.end()), changed_slots.end());
   bool any_exact = false;
   for (const ChirpRec& c : h->chirps) any_exact |= (c.tone >= 0 && (c.flags & awgk::TONE_EXACT));
-  if (h->chirps.size() > h->cap_chirps || slots_before == 0) {
-    // first chirps or a larger slot pool: synchronous (reallocation waits for the device anyway)
+  if (h->chirps.size() > h->cap_chirps) {
+    // a larger slot pool: synchronous (reallocation waits for the device anyway)
     if ((st = wait_idle(h))) return st;
     if ((st = upload_chirps(h))) return st;
     if ((st = build_exact_tables(h))) return st;

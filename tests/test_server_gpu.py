@@ -184,3 +184,36 @@ def test_chunks_cut_into_tile_pieces_match_standalone(awg, oracle):
         _check_against_oracle(oracle, fs, r, got)
         srv.release(rid)
     srv.close()
+
+
+@pytest.mark.parametrize("depth", [2, 3])
+def test_start_up_chunks_fill_the_buffer_before_playback(awg, depth):
+    """The timing model of a served request: its first `depth` chunks are the start-up, released
+    when its set-up is done; playback starts (t_play) when they are all complete; every later
+    chunk c is due at t_play + c period and released `depth` periods earlier, never before t_play,
+    so each streamed chunk has the whole look-ahead.  Read from the exported chunk traces of one
+    request on an otherwise idle server."""
+    fs, chunk, n_chunks = 20e6, 1 << 16, 7
+    period = chunk / fs
+    f, a, th, chirps, _, _ = _request(31, fs, 200, chunk, n_chunks, 20)
+    srv = awg.Server(fs, 8 << 30, 64)
+    srv.set_prefetch(depth)
+    rid = srv.submit(f, a, th, chunk, n_chunks, chirps)
+    srv.drain(60000)
+    tr = srv.trace_chunks()
+    tr = np.sort(tr[tr["id"] == rid], order="chunk")
+    assert list(tr["chunk"]) == list(range(n_chunks))
+    start, streamed = tr[:depth], tr[depth:]
+    t_ready = start["release"][0]
+    assert np.all(start["release"] == t_ready)
+    assert np.allclose(start["due"], t_ready + period * (np.arange(depth) + 1), rtol=0, atol=1e-9)
+    assert not np.any(start["late"])
+    t_play = float(np.max(start["done"]))
+    c = streamed["chunk"].astype(np.float64)
+    assert np.allclose(streamed["due"], t_play + c * period, rtol=0, atol=1e-9)
+    assert np.allclose(streamed["release"], t_play + (c - depth) * period, rtol=0, atol=1e-9)
+    assert np.all(streamed["release"] >= t_play - 1e-12)
+    assert not np.any(streamed["late"]) and np.all(streamed["done"] <= streamed["due"])
+    assert srv.stats()["deadline_misses"] == 0
+    srv.release(rid)
+    srv.close()
