@@ -313,6 +313,16 @@ int awg_device_status(awg_t* h);
  * (The paper has no counterpart: this checks the library's own failure path.) */
 int awg_test_wait_timeout(awg_t* h, int64_t limit_us, void* stream);
 
+/* Measurement hook: the rate the SFU sustains in the render kernel's own static-tone loop, with
+ * none of the render's staging, set-up or split sums around it -- a measured ceiling to set a
+ * render's sines per second against, beside the nominal SFU rate.  Launches on `stream` `blocks`
+ * CTAs of 128 threads; each thread runs `runs` runs of 32 samples of one static tone (one SFU
+ * sine per sample: blocks x 128 x runs x 32 sines) and writes one float (the sum of its partial
+ * sums) to out[thread], a caller-owned device buffer of blocks x 128 floats.  Asynchronous; time
+ * it with events on `stream`.  AWG_EINVAL for a null buffer or blocks, runs outside 1 .. 2^20.
+ * (The paper has no counterpart.) */
+int awg_sfu_rate_probe(float* out, int32_t blocks, int32_t runs, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Periodic table on tensor cores.
  * ---------------------------------------------------------------------------------------- */

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("awg_profile_end", ctypes.c_int, [P, P, P, i32, P]),
     ("awg_device_status", ctypes.c_int, [P]),
     ("awg_test_wait_timeout", ctypes.c_int, [P, i64, P]),
+    ("awg_sfu_rate_probe", ctypes.c_int, [P, i32, i32, P]),
 ]
 
 _lib = None
@@ -148,6 +149,12 @@ def chirp_coeffs(F_start: int, F_end: int, L: int, profile: int) -> list[int]:
     out = np.zeros(21, dtype=np.uint64)
     _check(lib().awg_chirp_coeffs(int(F_start), int(F_end), int(L), int(profile), _p(out)))
     return [int(out[3 * k]) | (int(out[3 * k + 1]) << 64) | (int(out[3 * k + 2]) << 128) for k in range(7)]
+
+
+def sfu_rate_probe(out, blocks: int, runs: int, stream=None):
+    """Launch the SFU-rate probe (the render's static loop alone): blocks x 128 x runs x 32 sines;
+    `out` is a device float tensor of at least blocks x 128 elements."""
+    _check(lib().awg_sfu_rate_probe(_ptr(out), int(blocks), int(runs), _stream_ptr(stream)))
 
 
 def _stream_ptr(stream):

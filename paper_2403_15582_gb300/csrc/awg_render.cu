@@ -1488,4 +1488,31 @@ cudaError_t launch_trace(const TraceArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The rate the SFU sustains in the render's own static loop (a measured ceiling for the sine
+// roofline): every thread runs `runs` runs of RUN samples of one static tone through static_loop,
+// with no staging, set-up or split sum, and writes the sum of its partial sums (so that nothing
+// is optimised away).  One sine per sample: blocks x RT x runs x RUN sines per launch.
+__global__ void __launch_bounds__(RT, AWG_RENDER_MIN_BLOCKS) sfu_rate_kernel(float* __restrict__ out, int runs) {
+  const uint32_t id = blockIdx.x * RT + threadIdx.x;
+  uint32_t p = id * 0x9E3779B9u;
+  const uint32_t f = (id * 0x85EBCA6Bu) | 1u;
+  const float A = 1e-3f;
+  Acc acc;
+#pragma unroll
+  for (int r = 0; r < RUN / 2; ++r) acc[r] = make_float2(0.f, 0.f);
+  for (int k = 0; k < runs; ++k) {
+    static_loop<0, RUN>(p, f, A, acc);
+    p += (uint32_t)RUN * f;
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int r = 0; r < RUN / 2; ++r) t += acc[r].x + acc[r].y;
+  out[id] = t;
+}
+
+cudaError_t launch_sfu_rate(float* out, int blocks, int runs, cudaStream_t s) {
+  sfu_rate_kernel<<<blocks, RT, 0, s>>>(out, runs);
+  return cudaGetLastError();
+}
+
 }  // namespace awgk

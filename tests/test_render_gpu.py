@@ -501,3 +501,18 @@ def test_chirp_boundaries_in_every_lane(awg, oracle, mode):
     q, x = render(s, n)
     assert s.device_status() == 0
     check(q, x, w, oracle, oracle.render(w, 0, n, nthreads=NTHREADS), s.tone_split)
+
+
+def test_sfu_rate_probe_runs(awg):
+    """The SFU-rate probe (the render's static loop alone) writes one finite float per thread and
+    refuses bad arguments."""
+    blocks, runs = 8, 4
+    out = torch.full((blocks * 128,), float("nan"), dtype=torch.float32, device="cuda")
+    awg.sfu_rate_probe(out, blocks, runs)
+    torch.cuda.synchronize()
+    v = out.cpu().numpy()
+    assert np.all(np.isfinite(v)) and np.max(np.abs(v)) <= runs * 32 * 1e-3 * 1.0001
+    with pytest.raises(awg.AwgError):
+        awg.sfu_rate_probe(out, 0, runs)
+    with pytest.raises(awg.AwgError):
+        awg.sfu_rate_probe(None, blocks, runs)
