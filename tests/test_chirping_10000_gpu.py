@@ -45,3 +45,41 @@ def test_ten_thousand_chirping_tones_against_the_oracle(awg, oracle):
         q_ref = oracle.quantize(oracle.render(w, n0, n, nthreads=NTHREADS), FS)
         dq = np.abs(q[n0:n0 + n].astype(np.int32) - q_ref.astype(np.int32))
         assert dq.max() <= 1, (n0, int(dq.max()))
+
+
+def test_rotating_stream_of_10000_tones_against_the_oracle(awg, oracle):
+    """The continuous 10,000-tone stream at 280 MS/s (groups of 100 tones ramping linearly for 1 ms in
+    turn) rendered as the stream driver does it: 2^20-sample chunks, each chunk's chirps handed to
+    the library just before the chunk.  120 ms, so that group 0 ramps twice and every tone's first
+    ramp is folded into its static state before its second; windows across group hand-overs, inside
+    a ramp and after a second ramp are compared element by element with the oracle (int16 within
+    1 LSB)."""
+    from paper_2403_15582_gb300 import workloads as wl
+    wk = wl.stream_rotating(seed=3, fs=280e6, seconds=0.12)
+    chunk = wk.chunk
+    n_chunks = -(-wk.n_samples // chunk)
+    s = awg.Synth(wk.fs)
+    s.set_tones(wk.freq_hz, wk.amp, wk.phase_rad)
+    out = torch.empty(n_chunks * chunk, dtype=torch.int16, device="cuda")
+    order = sorted(wk.chirps, key=lambda c: c["start_sample"])
+    nxt = 0
+    for c in range(n_chunks):
+        batch = []
+        while nxt < len(order) and order[nxt]["start_sample"] < (c + 1) * chunk:
+            batch.append(order[nxt])
+            nxt += 1
+        if batch:
+            s.set_chirp_list(batch)
+        s.render(chunk, out[c * chunk:])
+    torch.cuda.synchronize()
+    assert s.device_status() == 0
+    q = out.cpu().numpy()
+    FS = float(np.sum(np.abs(wk.amp)))
+    L = 280000                                                 # one 1 ms ramp
+    windows = [(0, 4096), (L - 2048, 4096), (37 * L + 140_001, 4096), (100 * L - 3000, 6000),
+               (100 * L + L // 2, 4096), (119 * L + 12_345, 4096)]
+    for n0, n in windows:
+        w = oracle.make_waveform_window(wk.fs, wk.freq_hz, wk.amp, wk.phase_rad, wk.chirps, n0, n)
+        q_ref = oracle.quantize(oracle.render(w, n0, n, nthreads=NTHREADS), FS)
+        dq = np.abs(q[n0:n0 + n].astype(np.int32) - q_ref.astype(np.int32))
+        assert dq.max() <= 1, (n0, int(dq.max()))
