@@ -424,6 +424,21 @@ bool low_order_negligible(uint64_t F0, uint64_t F1, int64_t L, int profile) {
   return words < 64.0 * 4294967296.0;
 }
 
+// Whether two lanes may share the chirp's run set-up (TONE_PAIR): the render then takes a run's
+// cascade state from the neighbouring run's exact set-up, moved by 32 samples with the cascade's
+// integer steps, so a cascade spans up to 63 steps instead of 31.  Linear chirps: the third
+// difference is exactly zero, the bound is the rounding of p, f, g over 63 steps (0.5 + 31.5 +
+// 976.5 units of 2^-32 turn).  LOW6 chirps: in addition the neglected third differences over 63
+// steps, C(63, 3) max |Delta^3 P|, must stay below 512 units, and LOW6's left-out stride terms
+// grow from 64 to at most 64 x 1953 / 465 = 269 units: at most 1790 units against the 2500 of an
+// unshared minimum-jerk run.
+bool pair_setup_ok(uint64_t F0, uint64_t F1, int64_t L, int profile, bool low6) {
+  if (profile == AWG_PROFILE_LINEAR) return true;
+  if (!low6) return false;
+  const double bound = third_difference_bound(F0, F1, L, profile);
+  return bound >= 0 && 39711.0 * bound < 512.0 * 4294967296.0;
+}
+
 // Phase offset at the end of an exponential chirp, R(L), the same FP64 formula as the render's.
 uint64_t exp_end_offset(uint64_t F0, uint64_t F1, int64_t L) {
   const ExpParams e = exp_params(F0, F1, L);
@@ -1692,7 +1707,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   struct Coeffs {
     W192 d[7];
     uint64_t end_offset;
-    bool exact, flat3, low6;
+    bool exact, flat3, low6, pair;
     float rot_c, rot_s;   // rotator constants of F_end
   };
   std::vector<Coeffs> co(pend.size());
@@ -1705,6 +1720,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
       co[i].exact = needs_exact(p.F0, p.F1, p.L, p.profile);
       co[i].flat3 = flat_third_difference(p.F0, p.F1, p.L, p.profile);
       co[i].low6 = co[i].flat3 && low_order_negligible(p.F0, p.F1, p.L, p.profile);
+      co[i].pair = !co[i].exact && pair_setup_ok(p.F0, p.F1, p.L, p.profile, co[i].low6);
       rotation_of(p.F1, &co[i].rot_c, &co[i].rot_s);
     }
   };
@@ -1743,7 +1759,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     c.tone = p.tone;
     c.flags = (co[pi].exact ? awgk::TONE_EXACT : 0) | (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0) |
               (p.profile == AWG_PROFILE_EXPONENTIAL ? awgk::TONE_EXP : 0) | (co[pi].flat3 ? awgk::TONE_FLAT3 : 0) |
-              (co[pi].low6 ? awgk::TONE_LOW6 : 0);
+              (co[pi].low6 ? awgk::TONE_LOW6 : 0) | (co[pi].pair ? awgk::TONE_PAIR : 0);
     const uint64_t phi_end = c.phi_start + co[pi].end_offset;
     t.slot = slot;
     t.n_s = p.ns;
@@ -2089,6 +2105,9 @@ int awg_render_phases(awg_t* h, int32_t tone, int64_t n0, int32_t count, uint32_
   ta.count = count;
   ta.tile0 = tile0;
   ta.n_tiles = n_tiles;
+  ta.K = h->K;
+  ta.split = h->split;
+  ta.listed = h->static_engine != AWG_STATIC_DIRECT;
   ta.out = h->d_trace;
   std::memcpy(ta.inv_odd, h->inv_odd, sizeof(ta.inv_odd));
   if (e == cudaSuccess) e = counted(h, awgk::launch_trace(ta, h->priv));

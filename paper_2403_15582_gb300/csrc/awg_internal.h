@@ -52,6 +52,9 @@ constexpr int32_t TONE_FLAT3 = 32;        // the chirp's third unit difference s
                                           // the run cascade's h rounds to 0 in every run
 constexpr int32_t TONE_LOW6 = 64;         // FLAT3, and B_6, E_5, G_2..G_4 move a run's phase by
                                           // < 64 units of 2^-32 turn: left out of the run set-up
+constexpr int32_t TONE_PAIR = 128;        // a lane pair may share the chirp's run set-up: linear, or
+                                          // LOW6 with C(63,3) max |Delta^3 P| below 512 units of 2^-32
+                                          // turn (the render's run set-up, see render_tile)
 constexpr int32_t TONE_EXP = 16;          // exponential chirp: ChirpRec::d[0..4] hold F_start, F_end
                                           // and the doubles alpha, C, e^alpha - 1 (bit patterns)
 
@@ -197,6 +200,8 @@ struct TraceArgs {      // per-sample render phases of one tone (test hook)
   int32_t count;
   int64_t tile0;
   int32_t n_tiles;
+  int32_t K, split;       // the render's tone count and split (its CTAs' tone ranges and stages)
+  int32_t listed;         // renders go through a tone list (static engine): no shared set-ups
   uint32_t* out;
   uint64_t inv_odd[3][3];
 };

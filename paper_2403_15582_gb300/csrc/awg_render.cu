@@ -854,6 +854,59 @@ __device__ __forceinline__ int chirp_inside_kind(int32_t flags) {
   return (flags & TONE_LINEAR) ? DESC_LINEAR : (flags & TONE_LOW6) ? DESC_LOW6 : (flags & TONE_FLAT3) ? DESC_FLAT3 : DESC_MINJERK;
 }
 
+// Descriptor kind of a tone in the tile [T0, T0 + TILE): DESC_STATIC for a static segment (the
+// stage turns it into DESC_STATIC_ROT under the rotator sine), a chirp kind for a chirp that covers
+// the tile without a table, DESC_MIXED for a chirp boundary, a table or an amplitude ramp in the
+// tile, DESC_SKIP for a static segment the tensor-core engine sums.
+__device__ __forceinline__ int tile_kind(const ToneRec& tr, int64_t T0, bool skip_static) {
+  const int tcls = classify_tile(tr, T0);
+  int kind;
+  if (tcls == TILE_PRE || tcls == TILE_POST) {
+    kind = DESC_STATIC;
+  } else {
+    const bool inside = T0 >= tr.n_s && T0 + TILE - 1 <= tr.n_e;
+    kind = (inside && !(tr.flags & TONE_EXACT)) ? chirp_inside_kind(tr.flags) : DESC_MIXED;
+  }
+  if ((tr.flags & TONE_AMP_RAMP) && T0 + TILE - 1 > tr.a_ns && T0 < tr.a_ns + tr.a_L) kind = DESC_MIXED;
+  if (skip_static && tile_static(tr, T0)) kind = DESC_SKIP;
+  return kind;
+}
+
+// Visit group of a stage's tone: chirps in linear form that may share their run set-up (TONE_PAIR),
+// the other linear ones, the same two for LOW6 form, static segments, then the rest (every tone of
+// a listed render).  Shared set-ups only in renders without the tensor-core engine (pair false).
+enum { GRP_LIN_PAIR = 0, GRP_LIN = 1, GRP_LOW6_PAIR = 2, GRP_LOW6 = 3, GRP_STATIC = 4, GRP_REST = 5, N_GRP = 6 };
+__device__ __forceinline__ int visit_group(int kind, bool listed, bool pair) {
+  if (listed) return GRP_REST;
+  if (kind == DESC_LINEAR) return pair ? GRP_LIN_PAIR : GRP_LIN;
+  if (kind == DESC_LOW6) return pair ? GRP_LOW6_PAIR : GRP_LOW6;
+  return (kind == DESC_STATIC || kind == DESC_STATIC_ROT) ? GRP_STATIC : GRP_REST;
+}
+
+// Run set-up shared by a lane pair.  Lanes 2m and 2m + 1 (runs j and j + 1) take two tones of a
+// group: each evaluates one tone's set-up exactly (the even lane the first tone's, the odd lane the
+// second's) and takes the other tone's from its partner, moved by one run with the cascade's own
+// integer steps (h = 0): forward from run j - 1, p + 32 f + 496 g and f + 32 g (the state the
+// partner's cascade reaches after 32 samples); backward from run j + 1, p - 32 f + 528 g and
+// f - 32 g (C(-32, 2) = 528).  The moved state's error is the cascade's over up to 63 steps
+// (pair_setup_ok on the host bounds it).  Every lane of the warp takes part.
+__device__ __forceinline__ RunPoly partner_state(const RunPoly& own, bool odd) {
+  const uint32_t p = __shfl_xor_sync(0xffffffffu, own.p, 1);
+  const uint32_t f = __shfl_xor_sync(0xffffffffu, own.f, 1);
+  const uint32_t g = __shfl_xor_sync(0xffffffffu, own.g, 1);
+  RunPoly q;
+  if (odd) {
+    q.p = p + 32u * f + 496u * g;
+    q.f = f + 32u * g;
+  } else {
+    q.p = p - 32u * f + 528u * g;
+    q.f = f - 32u * g;
+  }
+  q.g = g;
+  q.h = 0;
+  return q;
+}
+
 // Scale, round half to even, clamp and store sample n (inside the window), after adding the
 // tensor-core engine's static sum when there is one.
 __device__ __forceinline__ void store_sample(const RenderArgs& a, int64_t n, float x) {
@@ -985,7 +1038,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   __shared__ alignas(16) TileRec s_rec[2][STAGE];
   __shared__ alignas(16) Desc s_desc[2][STAGE];
   __shared__ uint8_t s_order[2][STAGE];          // visit order: linear chirps, LOW6 chirps, the rest
-  __shared__ int s_ngrp[2][3];                    // ends of the linear, LOW6 and static groups
+  __shared__ int s_ngrp[2][N_GRP - 1];            // ends of the visit groups before the last
   __shared__ alignas(16) float s_red[TILE];       // general paths: [r][run]; cluster sums: [i][thread]
   __shared__ alignas(8) uint64_t s_bar[4];        // tones[0], tones[1], records[0], records[1]
 
@@ -1053,7 +1106,7 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   auto prepare_stage = [&](int st) {
     const int b = st & 1;
     const int cnt = min(STAGE, l_end - (l_begin + st * STAGE));
-    bool need = false;
+    bool need = false, pairable = false;
     const TileRec* src = nullptr;
     int kind = -1;
     if (tid < cnt) {
@@ -1068,43 +1121,40 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
         const bool pre = tcls == TILE_PRE;
         d.F = pre ? tr.F : tr.F_end;
         d.p0 = (pre ? tr.phi_ref : tr.phi_post_ref) + (uint64_t)T0 * d.F;
-        d.kind = DESC_STATIC;
         if (a.sine_mode == SINE_ROTATOR) {
-          d.kind = DESC_STATIC_ROT;
           d.c = pre ? tr.rot_c : tr.rot_c_end;
           d.s = pre ? tr.rot_s : tr.rot_s_end;
         }
       } else {
         d.F = 0;
         d.p0 = 0;
-        const bool inside = T0 >= tr.n_s && T0 + TILE - 1 <= tr.n_e;
-        d.kind = (inside && !exact) ? chirp_inside_kind(tr.flags) : DESC_MIXED;
         if (!exact) {
           need = true;
           src = a.recs + (int64_t)a.act_of_slot[tr.slot] * (a.rec_stride ? a.rec_stride : a.n_tiles) + a.rec_tile0 + tile;
         }
       }
-      // an amplitude ramp inside the tile: the general per-sample path
-      if (ramp && T0 + TILE - 1 > tr.a_ns && T0 < tr.a_ns + tr.a_L) d.kind = DESC_MIXED;
-      if (a.skip_static && tile_static(tr, T0)) d.kind = DESC_SKIP;   // summed by the tensor-core engine
+      // a ramp inside the tile takes the general per-sample path; static segments the engine sums
+      // are skipped
+      d.kind = tile_kind(tr, T0, a.skip_static != 0);
+      if (d.kind == DESC_STATIC && a.sine_mode == SINE_ROTATOR) d.kind = DESC_STATIC_ROT;
       s_desc[b][tid] = d;
       kind = d.kind;
+      pairable = (tr.flags & TONE_PAIR) && !a.skip_static;
     }
     // visit order: the chirps that cover the tile in linear form, those in LOW6 form, the static
     // tones (SFU or rotator), then the rest; tone order within each group.  The first three
     // groups run in loops without a per-tone dispatch.  The order of the FP32 sums then depends
     // on which tones share a stage; with a tone list (the window's listed tones) that changes with
     // the window, so listed renders keep plain tone order, and every window cut gives the same bits.
-    const int grp = a.tone_list ? 3
-                    : kind == DESC_LINEAR ? 0 : kind == DESC_LOW6 ? 1 : (kind == DESC_STATIC || kind == DESC_STATIC_ROT) ? 2 : 3;
+    const int grp = visit_group(kind, a.tone_list != nullptr, pairable);
     const unsigned below = (1u << tid) - 1u;
     int pos = 0, end = 0;
 #pragma unroll
-    for (int g = 0; g < 4; ++g) {
+    for (int g = 0; g < N_GRP; ++g) {
       const unsigned m = __ballot_sync(0xffffffffu, tid < cnt && grp == g);
       if (grp == g) pos = end + __popc(m & below);
       end += __popc(m);
-      if (tid == 0 && g < 3) s_ngrp[b][g] = end;
+      if (tid == 0 && g < N_GRP - 1) s_ngrp[b][g] = end;
     }
     if (tid < cnt) s_order[b][pos] = (uint8_t)tid;
     const unsigned mask = __ballot_sync(0xffffffffu, need);
@@ -1142,7 +1192,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     ok &= mbar_wait(&s_bar[2 + b], par);
     if (ok) {
       const int cnt = min(STAGE, l_end - (l_begin + st * STAGE));
-      const int e_lin = s_ngrp[b][0], e_low6 = s_ngrp[b][1], e_static = s_ngrp[b][2];
+      const int e_lp = s_ngrp[b][GRP_LIN_PAIR], e_lin = s_ngrp[b][GRP_LIN], e_l6p = s_ngrp[b][GRP_LOW6_PAIR],
+                e_low6 = s_ngrp[b][GRP_LOW6], e_static = s_ngrp[b][GRP_STATIC];
       auto linear = [&](int i) { cascade<0, RUN, false>(poly_state(s_rec[b][i], rb0, true), s_desc[b][i].A, acc); };
       // LOW6, FLAT3: the third difference rounds to 0 everywhere (set-up bound), g is constant
       auto low6 = [&](int i) { cascade<0, RUN, false>(poly_state_low6(s_rec[b][i], rb0), s_desc[b][i].A, acc); };
@@ -1169,8 +1220,26 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
           re = t;
         }
       };
-      for (int o = 0; o < e_lin; ++o) linear(s_order[b][o]);
-      for (int o = e_lin; o < e_low6; ++o) low6(s_order[b][o]);
+      // the sharing groups two tones at a time: one set-up per lane, the other tone's state from the
+      // partner lane (partner_state); per sample the first tone's multiply-add, then the second's,
+      // as in two single loops; an odd group's last tone alone
+      const bool odd = (tid & 1) != 0;
+      for (int o = 0; o + 1 < e_lp; o += 2) {
+        const int i = s_order[b][o], k = s_order[b][o + 1];
+        const RunPoly own = poly_state(s_rec[b][odd ? k : i], rb0, true);
+        const RunPoly oth = partner_state(own, odd);
+        cascade<0, RUN, false>(odd ? oth : own, s_desc[b][i].A, acc);
+        cascade<0, RUN, false>(odd ? own : oth, s_desc[b][k].A, acc);
+      }
+      for (int o = e_lp & ~1; o < e_lin; ++o) linear(s_order[b][o]);
+      for (int o = e_lin; o + 1 < e_l6p; o += 2) {
+        const int i = s_order[b][o], k = s_order[b][o + 1];
+        const RunPoly own = poly_state_low6(s_rec[b][odd ? k : i], rb0);
+        const RunPoly oth = partner_state(own, odd);
+        cascade<0, RUN, false>(odd ? oth : own, s_desc[b][i].A, acc);
+        cascade<0, RUN, false>(odd ? own : oth, s_desc[b][k].A, acc);
+      }
+      for (int o = e_lin + ((e_l6p - e_lin) & ~1); o < e_low6; ++o) low6(s_order[b][o]);
       if (a.sine_mode == SINE_ROTATOR) {
         for (int o = e_low6; o < e_static; ++o) static_rot(s_order[b][o]);
       } else {
@@ -1289,8 +1358,10 @@ __global__ void __launch_bounds__(RT, AWG_RENDER_MIN_BLOCKS) render_batch_split_
 
 // The 32-bit phase the render feeds to the sine for sample s of the tile [T0, T0 + TILE) (any
 // segment), by the same integer steps as the render's loops: run j = s / RUN, sample r = s % RUN.
+// role: 0 the tone's own run set-up, 1 / 2 the first / second tone of a lane pair sharing its
+// set-up (the first tone's state is the odd lanes' partner state, the second's the even lanes').
 __device__ __noinline__ uint32_t phase32_at(const ToneRec& t, const TileRec* rec, const ChirpRec* chirps, int64_t T0,
-                                            int s, const uint64_t (*inv)[3]) {
+                                            int s, const uint64_t (*inv)[3], int role = 0) {
   const int j = s / RUN, r = s % RUN;
   const int64_t n0 = T0 + (int64_t)j * RUN, n = T0 + s;
   const uint32_t ur = (uint32_t)r;
@@ -1300,13 +1371,27 @@ __device__ __noinline__ uint32_t phase32_at(const ToneRec& t, const TileRec* rec
   if (t.flags & TONE_EXACT) return (uint32_t)((exact_chirp_word(chirps[t.slot], n - t.n_s, inv) + P_OFFSET) >> 32);
   const bool ramp_in_tile = (t.flags & TONE_AMP_RAMP) && T0 + TILE - 1 > t.a_ns && T0 < t.a_ns + t.a_L;
   const bool inside = T0 >= t.n_s && T0 + TILE - 1 <= t.n_e;
-  const RunBin b = run_binomials(j);
   RunPoly q;
   if (!ramp_in_tile && inside) {   // the tile's kind decides the set-up (LOW6 leaves terms out)
     const int kind = chirp_inside_kind(t.flags);
+    const bool odd = (j & 1) != 0;
+    // a shared set-up: the lane of the other parity evaluated it one run away
+    const bool moved = (role == 1 && odd) || (role == 2 && !odd);
+    const int js = moved ? (odd ? j - 1 : j + 1) : j;
+    const RunBin b = run_binomials(js);
     q = kind == DESC_LOW6 ? poly_state_low6(*rec, b)
         : kind == DESC_FLAT3 ? poly_state_flat3(*rec, b) : poly_state(*rec, b, kind == DESC_LINEAR);
+    if (moved) {
+      if (odd) {
+        q.p = q.p + 32u * q.f + 496u * q.g;
+        q.f = q.f + 32u * q.g;
+      } else {
+        q.p = q.p - 32u * q.f + 528u * q.g;
+        q.f = q.f - 32u * q.g;
+      }
+    }
   } else {
+    const RunBin b = run_binomials(j);
     q = poly_state(*rec, b, (t.flags & TONE_LINEAR) != 0);
   }
   return q.p - HALF_TURN + ur * q.f + c2 * q.g + c3 * q.h;
@@ -1326,6 +1411,31 @@ __global__ void exact_table_kernel(const __grid_constant__ TableArgs a, int64_t 
   a.out[m] = (uint32_t)((exact_chirp_word(a.chirps[a.slot], m, a.inv_odd) + P_OFFSET) >> 32);
 }
 
+// Whether tone k shares its run set-up in tile T0 of a render without a tone list or the tensor-
+// core engine, by the render's own visit: the CTA whose tone range [K c / split, K (c + 1) / split)
+// holds k, its stage of STAGE tones, and k's place among the stage's tones of its sharing group
+// (in tone order, taken two at a time).  0: own set-up, 1 / 2: first / second tone of a pair.
+__device__ __noinline__ int pair_role(const TraceArgs& a, int k, int64_t T0) {
+  if (a.listed || !(a.tones[k].flags & TONE_PAIR)) return 0;
+  const int g = visit_group(tile_kind(a.tones[k], T0, false), false, true);
+  if (g != GRP_LIN_PAIR && g != GRP_LOW6_PAIR) return 0;
+  const int64_t K = a.K, S = a.split;
+  int c = (int)((int64_t)k * S / K);
+  while (c + 1 < S && K * (c + 1) / S <= k) ++c;
+  while (c > 0 && K * c / S > k) --c;
+  const int lb = (int)(K * c / S), le = (int)(K * (c + 1) / S);
+  const int s0 = lb + (k - lb) / STAGE * STAGE, s1 = min(s0 + STAGE, le);
+  int pos = 0, n = 0;
+  for (int u = s0; u < s1; ++u) {
+    const ToneRec& t = a.tones[u];
+    if (visit_group(tile_kind(t, T0, false), false, (t.flags & TONE_PAIR) != 0) != g) continue;
+    if (u == k) pos = n;
+    ++n;
+  }
+  if (pos & 1) return 2;
+  return pos + 1 < n ? 1 : 0;
+}
+
 // The render's per-sample 32-bit phases of one tone (test hook).
 __global__ void trace_kernel(const __grid_constant__ TraceArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1337,7 +1447,7 @@ __global__ void trace_kernel(const __grid_constant__ TraceArgs a) {
   const TileRec* rec = nullptr;
   if (classify_tile(t, T0) == TILE_CHIRP && !(t.flags & TONE_EXACT))
     rec = a.recs + (int64_t)a.act_of_slot[t.slot] * a.n_tiles + (tile_abs - a.tile0);
-  a.out[i] = phase32_at(t, rec, a.chirps, T0, (int)(n - T0), a.inv_odd);
+  a.out[i] = phase32_at(t, rec, a.chirps, T0, (int)(n - T0), a.inv_odd, pair_role(a, a.tone, T0));
 }
 
 }  // namespace

@@ -119,25 +119,30 @@ def test_phase_words_long_chirps(awg, oracle):
 def test_render_phase_cascade_within_bound(awg, oracle, dur_ms):
     """The 32-bit phases the kernel feeds to the sine stay within the stated bound of the exact
     words: 2500 units of 2^-32 turn for minimum-jerk runs (g, h rounding over 31 steps of a
-    32-sample run; or, for a one-cascade 64-sample run, f and g rounding over 63 steps plus the
-    neglected third order, 31.5 + 976.5 + 512 + 64), 1100 for linear chirps (f and g rounding over
-    63 steps: 31.5 + 976.5), 40 for static segments (f rounding over 63 steps)."""
+    32-sample run; or, where two lanes share a run set-up and a cascade spans 63 steps, f and g
+    rounding over 63 steps plus the neglected third order and LOW6 terms, 31.5 + 976.5 + 512 +
+    269), 1100 for linear chirps (f and g rounding over 63 steps: 31.5 + 976.5), 40 for static
+    segments.  Tones 0 and 2 (minimum-jerk) and 1 and 4 (linear) form the render's lane pairs
+    where their chirps allow it, so both roles of a shared set-up are traced."""
     fs = 280e6
     L = int(round(dur_ms * 1e-3 * fs))
-    f = [90e6, 100e6, 120e6, 60e6]
+    f = [90e6, 100e6, 120e6, 60e6, 70e6]
+    A = [1, 1, 1, 1, 1]
+    th = [0.1, 0.2, 0.3, 0.4, 0.5]
     s = awg.Synth(fs)
-    s.set_tones(f, [1, 1, 1, 1], [0.1, 0.2, 0.3, 0.4])
+    s.set_tones(f, A, th)
     ns = 5000
     chirps = [dict(tone=0, f_start=90e6, f_end=179e6, duration=L / fs, profile=1, start_sample=ns),
               dict(tone=1, f_start=100e6, f_end=1e6, duration=L / fs, profile=0, start_sample=ns + 17),
-              dict(tone=2, f_start=125e6, f_end=80e6, duration=L / fs, profile=1, start_sample=ns + 4096)]
+              dict(tone=2, f_start=125e6, f_end=80e6, duration=L / fs, profile=1, start_sample=ns + 4096),
+              dict(tone=4, f_start=70e6, f_end=150e6, duration=L / fs, profile=0, start_sample=ns + 33)]
     s.set_chirp_list(chirps)
-    w = oracle.make_waveform(fs, f, [1, 1, 1, 1], [0.1, 0.2, 0.3, 0.4], chirps)
+    w = oracle.make_waveform(fs, f, A, th, chirps)
     for n0 in (0, ns + L // 2 - 30000, ns + L - 20000):
         n0 = max(n0, 0)
         cnt = 60000
         idx = np.arange(n0, n0 + cnt, dtype=np.int64)
-        for k, bound in ((0, 2500), (1, 1100), (2, 2500), (3, 40)):
+        for k, bound in ((0, 2500), (1, 1100), (2, 2500), (3, 40), (4, 1100)):
             got = s.render_phases(k, n0, cnt)
             words = oracle.phase_words_at(w, k, idx)
             ref = ((words.astype(object) + (1 << 40)) >> 32) % (1 << 32)
