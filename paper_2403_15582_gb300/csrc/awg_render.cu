@@ -1333,15 +1333,19 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   }
 }
 
-// 96 registers: five CTAs of RT threads per SM
+// 96 registers: five CTAs of RT threads per SM (the cluster and batched renders)
 #define AWG_RENDER_MIN_BLOCKS 5
+// The direct render: six CTAs per SM (80 registers, a few spills, 216 KB of shared memory with the
+// carveout at its maximum) ran the 1000-chirp record 1.6 % faster than five; the batched render of
+// the served stream, whose spills grow more, stays at five.
+#define AWG_RENDER_SPLIT_MIN_BLOCKS 6
 __global__ void __launch_bounds__(RT, AWG_RENDER_MIN_BLOCKS) render_kernel(const __grid_constant__ RenderArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   render_tile<true>(a, blockIdx.x / a.split, (int)cluster.block_rank(), a.split);
 }
 
 // The same without clusters (a.part set): CTA blockIdx.x takes rank blockIdx.x % split.
-__global__ void __launch_bounds__(RT, AWG_RENDER_MIN_BLOCKS) render_split_kernel(const __grid_constant__ RenderArgs a) {
+__global__ void __launch_bounds__(RT, AWG_RENDER_SPLIT_MIN_BLOCKS) render_split_kernel(const __grid_constant__ RenderArgs a) {
   render_tile<false>(a, blockIdx.x / a.split, blockIdx.x % a.split, a.split);
 }
 
@@ -1466,6 +1470,8 @@ int device_sm_count() {
 
 cudaError_t render_setup_attributes() {
   cudaError_t e = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  // all of the SM's shared memory for AWG_RENDER_SPLIT_MIN_BLOCKS CTAs of 36 KB
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(render_split_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   return e;
 }
 
