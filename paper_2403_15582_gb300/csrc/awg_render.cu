@@ -1190,6 +1190,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     }
     ok &= mbar_wait(&s_bar[b], par);
     ok &= mbar_wait(&s_bar[2 + b], par);
+    // the same decision in every lane of the warp: the loops below exchange values between lanes
+    ok = __all_sync(0xffffffffu, ok);
     if (ok) {
       const int cnt = min(STAGE, l_end - (l_begin + st * STAGE));
       const int e_lp = s_ngrp[b][GRP_LIN_PAIR], e_lin = s_ngrp[b][GRP_LIN], e_l6p = s_ngrp[b][GRP_LOW6_PAIR],
