@@ -269,11 +269,14 @@ int32_t awg_tone_split(const awg_t* h);
 float awg_last_render_ms(awg_t* h);
 
 /* Profiling mode: while on, every render records CUDA events on its stream around its chirp
- * set-up kernels and around its render kernel.  awg_profile_begin clears the
- * record.  awg_profile_end waits for the last recorded event, writes per render call the device
- * time (ms) of the set-up kernel(s) and of the render kernel into prep_ms[i] / render_ms[i] for
- * i < cap (either may be NULL), stores the number of kernels launched in *launches (may be NULL),
- * stops recording and returns the number of render calls recorded (or a negative AWG_E* code). */
+ * set-up kernels and around its render kernel; a pipelined sequence (awg_render_chunks,
+ * awg_render_stream) records them at its start, after the set-up of its first group of chunks
+ * and after its last join, so its "render" time spans every chunk render of the sequence (they
+ * overlap) and any later group's set-up.  awg_profile_begin clears the record.  awg_profile_end
+ * waits for the last recorded event, writes per render call the device time (ms) of the set-up
+ * kernel(s) and of the render kernel(s) into prep_ms[i] / render_ms[i] for i < cap (either may be
+ * NULL), stores the number of kernels launched in *launches (may be NULL), stops recording and
+ * returns the number of render calls recorded (or a negative AWG_E* code). */
 int awg_profile_begin(awg_t* h);
 int awg_profile_end(awg_t* h, float* prep_ms, float* render_ms, int32_t cap, int64_t* launches);
 

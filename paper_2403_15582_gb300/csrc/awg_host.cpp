@@ -1470,8 +1470,21 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
   if (h->split > 1 && (st = ensure_split_scratch(h, (int32_t)(chunk / awgk::TILE + 2), h->split))) return st;
   st = ensure(&h->d_seq_act, &h->cap_seq_act, std::max<size_t>(1, h->chirps.size()), h, "slot map");
   if (st) return st;
+  // profiling: events at the start, after the first group's set-up (twice: the set-up's end and the
+  // renders' start) and after the last join; the first render then starts in plain stream order
+  cudaEvent_t pe[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (h->profiling) {
+    while (h->prof_ev.size() < 4 * (h->prof_calls + 1)) {
+      cudaEvent_t ev;
+      if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(e, "profiling event");
+      h->prof_ev.push_back(ev);
+    }
+    for (int i = 0; i < 4; ++i) pe[i] = h->prof_ev[4 * h->prof_calls + (size_t)i];
+  }
+  const int64_t launches0 = h->n_launches;
   if ((e = order_after_uploads(h, s)) != cudaSuccess) return cuda_fail(e, "upload ordering");
   if ((e = cudaEventRecord(h->ev0, s)) != cudaSuccess) return cuda_fail(e, "event");
+  if (pe[0] && (e = cudaEventRecord(pe[0], s)) != cudaSuccess) return cuda_fail(e, "event");
   for (const Group& grp : groups) {
     const int32_t g0 = grp.g0, g1 = grp.g1;
     const int64_t tile0 = grp.tile0;
@@ -1491,6 +1504,10 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
       std::memcpy(pa.inv_odd, h->inv_odd, sizeof(pa.inv_odd));
       for (int i = 0; i < pa.n_active; ++i) pa.slots[i] = active[b + (size_t)i];
       if ((e = counted(h, awgk::launch_prep(pa, s))) != cudaSuccess) return cuda_fail(e, "prep launch");
+    }
+    if (pe[1] && g0 == 0) {
+      if ((e = cudaEventRecord(pe[1], s)) != cudaSuccess) return cuda_fail(e, "event");
+      if ((e = cudaEventRecord(pe[2], s)) != cudaSuccess) return cuda_fail(e, "event");
     }
     for (int32_t c = g0; c < g1; ++c) {
       const int64_t wc = c0 + (int64_t)c * chunk, len = span(c, c + 1);
@@ -1527,6 +1544,11 @@ int render_chunks_impl(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, 
     if ((e = counted(h, awgk::launch_join(h->d_seq_exit, h->seq_exit_target, h->d_status, awgk::JOIN_LIMIT_NS, s))) !=
         cudaSuccess)
       return cuda_fail(e, "join launch");
+  }
+  if (pe[3]) {
+    if ((e = cudaEventRecord(pe[3], s)) != cudaSuccess) return cuda_fail(e, "event");
+    ++h->prof_calls;
+    h->prof_launches += h->n_launches - launches0;
   }
   if ((e = cudaEventRecord(h->ev1, s)) != cudaSuccess) return cuda_fail(e, "event");
   if ((e = cudaEventRecord(h->ev_done, s)) != cudaSuccess) return cuda_fail(e, "event");
@@ -2006,10 +2028,10 @@ int awg_render_chunks(awg_t* h, int64_t chunk, int32_t n_chunks, int16_t* out, v
   if (!out) return fail(AWG_EINVAL, "null output");
   if (chunk > (INT64_MAX - h->cursor) / n_chunks) return fail(AWG_EINVAL, "sample index overflow");
   if (chunk / awgk::TILE + 2 > (int64_t)(INT32_MAX / awgk::MAX_SPLIT)) return fail(AWG_EINVAL, "chunk too long");
-  if (n_chunks == 1 || h->profiling || h->periodic_start >= 0 || h->static_engine != AWG_STATIC_DIRECT ||
+  if (n_chunks == 1 || h->periodic_start >= 0 || h->static_engine != AWG_STATIC_DIRECT ||
       (h->split > 1 && chunk / awgk::TILE + 2 > SPLIT_LAUNCH_TILES)) {
-    // per-call profiling events would split the pipeline; a periodic tail is replayed per chunk;
-    // chunks above SPLIT_LAUNCH_TILES tiles go out in several launches each
+    // a periodic tail is replayed per chunk; chunks above SPLIT_LAUNCH_TILES tiles go out in
+    // several launches each (a pipelined sequence records its profiling events itself)
     for (int32_t c = 0; c < n_chunks; ++c) {
       const int st = render_impl(h, chunk, nullptr, out + (size_t)c * (size_t)chunk, stream);
       if (st) return st;
@@ -2031,7 +2053,7 @@ int awg_render_stream(awg_t* h, int64_t n, int64_t chunk, int16_t* out, void* st
   if (n / chunk > (int64_t)INT32_MAX - 1) return fail(AWG_EINVAL, "too many chunks");
   const int32_t full = (int32_t)(n / chunk);
   const int64_t tail = n - (int64_t)full * chunk;
-  if (full + (tail > 0 ? 1 : 0) <= 1 || h->profiling || h->periodic_start >= 0 || h->static_engine != AWG_STATIC_DIRECT ||
+  if (full + (tail > 0 ? 1 : 0) <= 1 || h->periodic_start >= 0 || h->static_engine != AWG_STATIC_DIRECT ||
       (h->split > 1 && chunk / awgk::TILE + 2 > SPLIT_LAUNCH_TILES)) {
     for (int64_t c = 0; c < n; c += chunk) {
       const int st = render_impl(h, std::min(chunk, n - c), nullptr, out + c, stream);
