@@ -264,6 +264,18 @@ def test_render_chunks_pipelined_equals_chunk_by_chunk(awg, oracle):
     idx = np.unique(rng.integers(0, total, 400))
     q_ref = oracle.quantize(oracle.render_at(w, idx, nthreads=NTHREADS), w.full_scale())
     assert np.max(np.abs(g[idx].astype(np.int32) - q_ref)) <= 1
+    # profiling mode: a sequence stays pipelined and records one call (set-up, then the span of its
+    # renders), with the same samples
+    s4 = make()
+    got4 = torch.full((total,), 12345, dtype=torch.int16, device="cuda")
+    s4.profile_begin()
+    before = s4.launch_count
+    s4.render_stream(total, 70_001, got4)
+    torch.cuda.synchronize()
+    prep_ms, rend_ms, launches = s4.profile_end()
+    assert len(prep_ms) == 1 and len(rend_ms) == 1 and prep_ms[0] > 0 and rend_ms[0] > 0
+    assert launches == s4.launch_count - before >= 3
+    assert np.array_equal(r, got4.cpu().numpy())
 
 
 @pytest.mark.parametrize("K", [1, 63, 64, 65, 129, 1000, 2000])
