@@ -719,7 +719,7 @@ __device__ __forceinline__ float ramp_amp_at(const RampRun& rr, int r) {
 // chirp boundary, an amplitude ramp or a per-sample phase table; col is the run's column of the
 // partial-sum buffer ([r][run], stride RUNS).
 __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, const RunBin& rb, float* col,
-                                         Acc& acc, int64_t T0, int64_t n0, const uint32_t* exact_tab) {
+                                         Acc& acc, int64_t T0, int64_t n0, const uint32_t* exact_tab, int cs) {
   constexpr int B = 0;
   const bool ramp = (tr.flags & TONE_AMP_RAMP) != 0;
   const bool ramp_run = ramp && n0 + RUN - 1 > tr.a_ns && n0 < tr.a_ns + tr.a_L;   // a(n) varies in the run
@@ -819,7 +819,7 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
       if (r < r1) ph = p_pre + (uint32_t)r * f_pre;
       else if (r > r2) ph = p_post + (uint32_t)r * f_post;
       else ph = exact ? exact_tab[tr.tab_off + (int32_t)(r - r1)] + HALF_TURN : pp;
-      col[r * RUNS] = sin_centred(ph);
+      col[r * cs] = sin_centred(ph);
       pp += ff;
       ff += gg;
       gg += st.h;
@@ -828,10 +828,10 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
       const RampRun rr = ramp_run_setup(tr, n0);
 #pragma unroll
       for (int r = 0; r < RUN; r += 2)
-        acc_pair_s(acc[B + r / 2], ramp_amp_at(rr, r), ramp_amp_at(rr, r + 1), col[r * RUNS], col[(r + 1) * RUNS]);
+        acc_pair_s(acc[B + r / 2], ramp_amp_at(rr, r), ramp_amp_at(rr, r + 1), col[r * cs], col[(r + 1) * cs]);
     } else {
 #pragma unroll
-      for (int r = 0; r < RUN; r += 2) acc_pair_s(acc[B + r / 2], A, A, col[r * RUNS], col[(r + 1) * RUNS]);
+      for (int r = 0; r < RUN; r += 2) acc_pair_s(acc[B + r / 2], A, A, col[r * cs], col[(r + 1) * cs]);
     }
   }
 }
@@ -1039,7 +1039,11 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
   __shared__ alignas(16) Desc s_desc[2][STAGE];
   __shared__ uint8_t s_order[2][STAGE];          // visit order: linear chirps, LOW6 chirps, the rest
   __shared__ int s_ngrp[2][N_GRP - 1];            // ends of the visit groups before the last
-  __shared__ alignas(16) float s_red[TILE];       // general paths: [r][run]; cluster sums: [i][thread]
+  // cluster sums through distributed shared memory: [i][thread]; without clusters the general
+  // per-sample path keeps its run's sines in a local array (lcol) instead, so that the CTA's
+  // shared memory (20 KB) leaves room for AWG_RENDER_SPLIT_MIN_BLOCKS CTAs per SM
+  __shared__ alignas(16) float s_red[CLUSTER ? TILE : 4];
+  float lcol[RUN];
   __shared__ alignas(8) uint64_t s_bar[4];        // tones[0], tones[1], records[0], records[1]
 
   cg::cluster_group cluster = cg::this_cluster();
@@ -1270,7 +1274,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
           if (__all_sync(0xffffffffu, q0.h == 0)) cascade<0, RUN, false>(q0, A, acc);
           else cascade<0, RUN, true>(q0, A, acc);
         } else {
-          tone_run(s_tone[b][i], &s_rec[b][i], rb0, &s_red[tid], acc, T0, n0, a.exact_tab);
+          if constexpr (CLUSTER) tone_run(s_tone[b][i], &s_rec[b][i], rb0, &s_red[tid], acc, T0, n0, a.exact_tab, RUNS);
+          else tone_run(s_tone[b][i], &s_rec[b][i], rb0, lcol, acc, T0, n0, a.exact_tab, 1);
         }
       }
     }
@@ -1337,10 +1342,10 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
 
 // 96 registers: five CTAs of RT threads per SM (the cluster and batched renders)
 #define AWG_RENDER_MIN_BLOCKS 5
-// The direct render: six CTAs per SM (80 registers, a few spills, 216 KB of shared memory with the
-// carveout at its maximum) ran the 1000-chirp record 1.6 % faster than five; the batched render of
-// the served stream, whose spills grow more, stays at five.
-#define AWG_RENDER_SPLIT_MIN_BLOCKS 6
+// The direct render: seven CTAs per SM (72 registers, some spills, 20 KB of shared memory each) ran
+// the 1000-chirp record 1.6 % faster than six and six 1.6 % faster than five; the batched render
+// of the served stream, whose spills grow more, stays at five.
+#define AWG_RENDER_SPLIT_MIN_BLOCKS 7
 __global__ void __launch_bounds__(RT, AWG_RENDER_MIN_BLOCKS) render_kernel(const __grid_constant__ RenderArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   render_tile<true>(a, blockIdx.x / a.split, (int)cluster.block_rank(), a.split);
@@ -1472,7 +1477,7 @@ int device_sm_count() {
 
 cudaError_t render_setup_attributes() {
   cudaError_t e = cudaFuncSetAttribute(render_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  // all of the SM's shared memory for AWG_RENDER_SPLIT_MIN_BLOCKS CTAs of 36 KB
+  // shared memory before L1 for AWG_RENDER_SPLIT_MIN_BLOCKS CTAs
   if (e == cudaSuccess) e = cudaFuncSetAttribute(render_split_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   return e;
 }
