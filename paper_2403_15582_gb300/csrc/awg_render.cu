@@ -716,8 +716,9 @@ __device__ __forceinline__ float ramp_amp_at(const RampRun& rr, int r) {
 }
 
 // The general paths for the thread's run (samples n0 .. n0 + RUN - 1), used where a tile holds a
-// chirp boundary, an amplitude ramp or a per-sample phase table; col is the run's column of the
-// partial-sum buffer ([r][run], stride RUNS).
+// chirp boundary, an amplitude ramp or a per-sample phase table; col holds the run's RUN sines,
+// sample r at col[r * cs] (a column of the cluster render's shared tile buffer, stride RUNS, or a
+// local array, stride 1).
 __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, const RunBin& rb, float* col,
                                          Acc& acc, int64_t T0, int64_t n0, const uint32_t* exact_tab, int cs) {
   constexpr int B = 0;
@@ -806,7 +807,7 @@ __device__ __forceinline__ void tone_run(const ToneRec& tr, const TileRec* rec, 
     cascade<B, RUN, true>(poly_state(*rec, rb, (tr.flags & TONE_LINEAR) != 0), A, acc);
   } else {
     // a segment boundary inside this run, or a table chirp: choose the segment per sample; the
-    // sines go to the run's column of the partial-sum buffer, then into the accumulators
+    // sines go to col, then into the accumulators
     const uint32_t p_pre = static_p0(tr.phi_ref, tr.F, n0) + HALF_TURN, f_pre = static_f(tr.F);
     const uint32_t p_post = static_p0(tr.phi_post_ref, tr.F_end, n0) + HALF_TURN, f_post = static_f(tr.F_end);
     const bool exact = (tr.flags & TONE_EXACT) != 0;
