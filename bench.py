@@ -274,25 +274,27 @@ def chirping_leg(awg, stream, K: int, fs: float = 280e6, chunk: int = 1 << 20, s
             "slots": n_slots, "prefill": prefill, "segment_samples": S}
 
 
-def sfu_probe(awg, stream, n_sm: int, achieved: float, runs: int = 1024, reps: int = 5):
-    """The rate the SFU sustains in the render kernel's own static loop alone (no staging, set-up
+def sfu_probe(awg, stream, n_sm: int, achieved: float, runs: int = 1024, reps: int = 5, probe=None, what="static"):
+    """The rate the SFU sustains in one of the render kernel's own loops alone (no staging, set-up
     or split sums; one wave of 5 CTAs per SM), best of a few launches: a measured ceiling beside
     the nominal SFU rate, and the render's rate in the timed steps against it."""
     import torch
+    probe = probe or awg.sfu_rate_probe
     blocks = 5 * n_sm
     out = torch.empty(blocks * 128, dtype=torch.float32, device="cuda")
-    awg.sfu_rate_probe(out, blocks, runs, stream)       # warm-up
+    probe(out, blocks, runs, stream)       # warm-up
     best = 1e30
     for _ in range(reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        awg.sfu_rate_probe(out, blocks, runs, stream)
+        probe(out, blocks, runs, stream)
         e1.record(stream)
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
     rate = blocks * 128 * runs * 32 / (best * 1e-3) / 1e12
+    name = "awg_sfu_rate_probe" if what == "static" else "awg_chirp_rate_probe"
     return {"value": rate, "unit": "Tsin/s", "frac": achieved / rate,
-            "source": f"awg_sfu_rate_probe: the render's static sine loop alone, {blocks} CTAs x 128 threads x {runs} runs of 32 samples, best of {reps}"}
+            "source": f"{name}: the render's {what} sine loop alone, {blocks} CTAs x 128 threads x {runs} runs of 32 samples, best of {reps}"}
 
 
 def measured_peaks():
@@ -761,7 +763,8 @@ def main():
                                     "basis": "timed steps: sines / step time (set-up and join included)"},
                      "isolated_launch": {"achieved": achieved_isolated, "frac": achieved_isolated / peak,
                                          "basis": "chunk-by-chunk pass: sines / render kernel event time"},
-                     "measured_sfu": sfu_probe(awg, stream, n_sm, achieved)},
+                     "measured_sfu": sfu_probe(awg, stream, n_sm, achieved),
+                     "measured_chirp_loop": sfu_probe(awg, stream, n_sm, achieved, probe=awg.chirp_rate_probe, what="chirp")},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 2 * N},
         "gpu_launches": int(launches),
         "clocks": clocks,

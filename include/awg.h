@@ -326,6 +326,13 @@ int awg_test_wait_timeout(awg_t* h, int64_t limit_us, void* stream);
  * (The paper has no counterpart.) */
 int awg_sfu_rate_probe(float* out, int32_t blocks, int32_t runs, void* stream);
 
+/* Measurement hook: the same for the render kernel's chirp loop (the 32-bit phase cascade
+ * p += f, f += g of linear and LOW6 chirps, then the sine and the multiply-add): each thread
+ * runs `runs` runs of 32 samples of one chirp state (blocks x 128 x runs x 32 sines) and writes
+ * the sum of its partial sums to out[thread].  Same buffer, stream and error rules as
+ * awg_sfu_rate_probe.  (The paper has no counterpart.) */
+int awg_chirp_rate_probe(float* out, int32_t blocks, int32_t runs, void* stream);
+
 /* ------------------------------------------------------------------------------------------
  * Periodic table on tensor cores.
  * ---------------------------------------------------------------------------------------- */

@@ -80,6 +80,7 @@ SIGNATURES = [
     ("awg_device_status", ctypes.c_int, [P]),
     ("awg_test_wait_timeout", ctypes.c_int, [P, i64, P]),
     ("awg_sfu_rate_probe", ctypes.c_int, [P, i32, i32, P]),
+    ("awg_chirp_rate_probe", ctypes.c_int, [P, i32, i32, P]),
 ]
 
 _lib = None
@@ -155,6 +156,12 @@ def sfu_rate_probe(out, blocks: int, runs: int, stream=None):
     """Launch the SFU-rate probe (the render's static loop alone): blocks x 128 x runs x 32 sines;
     `out` is a device float tensor of at least blocks x 128 elements."""
     _check(lib().awg_sfu_rate_probe(_ptr(out), int(blocks), int(runs), _stream_ptr(stream)))
+
+
+def chirp_rate_probe(out, blocks: int, runs: int, stream=None):
+    """Launch the chirp-loop rate probe (the render's chirp cascade alone): blocks x 128 x runs x 32
+    sines; `out` is a device float tensor of at least blocks x 128 elements."""
+    _check(lib().awg_chirp_rate_probe(_ptr(out), int(blocks), int(runs), _stream_ptr(stream)))
 
 
 def _stream_ptr(stream):

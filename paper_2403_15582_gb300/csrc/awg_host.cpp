@@ -2350,6 +2350,15 @@ int awg_sfu_rate_probe(float* out, int32_t blocks, int32_t runs, void* stream) {
   return AWG_OK;
 }
 
+int awg_chirp_rate_probe(float* out, int32_t blocks, int32_t runs, void* stream) {
+  if (!out) return fail(AWG_EINVAL, "null output");
+  if (blocks < 1 || blocks > (1 << 20)) return fail(AWG_EINVAL, "blocks must be in 1 .. 2^20");
+  if (runs < 1 || runs > (1 << 20)) return fail(AWG_EINVAL, "runs must be in 1 .. 2^20");
+  cudaError_t e = awgk::launch_chirp_rate(out, blocks, runs, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "probe launch");
+  return AWG_OK;
+}
+
 int awg_device_status(awg_t* h) {
   if (!h) return fail(AWG_EINVAL, "null handle");
   int32_t v = 0;

@@ -232,6 +232,7 @@ cudaError_t launch_render_batch_split(const RenderArgs* reqs, const int2* items,
 cudaError_t launch_phase_words(const PhaseArgs& a, cudaStream_t s);
 cudaError_t launch_trace(const TraceArgs& a, cudaStream_t s);
 cudaError_t launch_sfu_rate(float* out, int blocks, int runs, cudaStream_t s);   // RT threads per block
+cudaError_t launch_chirp_rate(float* out, int blocks, int runs, cudaStream_t s); // RT threads per block
 cudaError_t render_setup_attributes();
 // Number of SMs of the current device (queried once per device, then cached); grid sizes of the
 // grid-stride kernels are multiples of it.

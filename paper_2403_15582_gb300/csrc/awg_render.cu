@@ -1639,4 +1639,33 @@ cudaError_t launch_sfu_rate(float* out, int blocks, int runs, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// The same for the render's chirp loop (cascade without h, the loop of linear and LOW6 chirps):
+// each run takes a chirp state (p, f, g) from the thread's id, one sine per sample.
+__global__ void __launch_bounds__(RT, AWG_RENDER_MIN_BLOCKS) chirp_rate_kernel(float* __restrict__ out, int runs) {
+  const uint32_t id = blockIdx.x * RT + threadIdx.x;
+  RunPoly q;
+  q.p = id * 0x9E3779B9u;
+  q.f = (id * 0x85EBCA6Bu) | 1u;
+  q.g = (id * 0xC2B2AE35u) >> 8;
+  q.h = 0;
+  const float A = 1e-3f;
+  Acc acc;
+#pragma unroll
+  for (int r = 0; r < RUN / 2; ++r) acc[r] = make_float2(0.f, 0.f);
+  for (int k = 0; k < runs; ++k) {
+    cascade<0, RUN, false>(q, A, acc);
+    q.p += 32u * q.f + 496u * q.g;   // the state after the run
+    q.f += 32u * q.g;
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int r = 0; r < RUN / 2; ++r) t += acc[r].x + acc[r].y;
+  out[id] = t;
+}
+
+cudaError_t launch_chirp_rate(float* out, int blocks, int runs, cudaStream_t s) {
+  chirp_rate_kernel<<<blocks, RT, 0, s>>>(out, runs);
+  return cudaGetLastError();
+}
+
 }  // namespace awgk

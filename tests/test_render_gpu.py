@@ -533,3 +533,18 @@ def test_sfu_rate_probe_runs(awg):
         awg.sfu_rate_probe(out, 0, runs)
     with pytest.raises(awg.AwgError):
         awg.sfu_rate_probe(None, blocks, runs)
+
+
+def test_chirp_rate_probe_runs(awg):
+    """The chirp-loop rate probe (the render's chirp cascade alone) writes one finite float per
+    thread and refuses bad arguments."""
+    blocks, runs = 8, 4
+    out = torch.full((blocks * 128,), float("nan"), dtype=torch.float32, device="cuda")
+    awg.chirp_rate_probe(out, blocks, runs)
+    torch.cuda.synchronize()
+    v = out.cpu().numpy()
+    assert np.all(np.isfinite(v)) and np.max(np.abs(v)) <= runs * 32 * 1e-3 * 1.0001
+    with pytest.raises(awg.AwgError):
+        awg.chirp_rate_probe(out, blocks, 0)
+    with pytest.raises(awg.AwgError):
+        awg.chirp_rate_probe(None, blocks, runs)
