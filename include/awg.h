@@ -3,14 +3,14 @@
  *
  * It computes x[n] = sum_k A_k sin(phi_k(n)) (additive synthesis, Sec. II Eq. main and the
  * dynamic form Eq. dynamicandstatic of Tu & Subhankar, "Fast real-time arbitrary waveform
- * generation using graphic processing units") for static tones and tones chirped along linear
- * or minimum-jerk frequency ramps (Eq. freqchirp), and writes scaled int16 DAC samples (and,
+ * generation using graphic processing units") for static tones and tones chirped along linear,
+ * minimum-jerk (Eq. freqchirp) or exponential frequency ramps, and writes scaled int16 DAC samples (and,
  * on request, the FP32 sum) chunk by chunk.
  *
  * Phase model.  A tone's phase is an integer word Phi in units of 2^-64 turn.  Static tones:
- * Phi(n) = Phi_ref + n*F (mod 2^64).  A chirp over samples n_s..n_s+L follows a degree <= 6
- * polynomial held as seven 2^128-scaled forward differences (192-bit words); its phase words
- * are exact integers, the same ones a sequential 192-bit accumulator cascade produces, so
+ * Phi(n) = Phi_ref + n*F (mod 2^64).  A linear or minimum-jerk chirp over samples n_s..n_s+L
+ * follows a degree <= 6 polynomial held as seven 2^128-scaled forward differences (192-bit
+ * words); its phase words are exact integers, the same ones a sequential 192-bit accumulator cascade produces, so
  * there is no drift over arbitrarily long streams.  After the chirp the tone is static at the
  * end frequency, continuing from the phase reached at n_s+L (Eq. freqchirp case 2).
  *

@@ -246,3 +246,34 @@ def test_same_samples_for_long_and_short_calls(awg, with_ramps):
         c += m
     torch.cuda.synchronize()
     assert np.array_equal(one.cpu().numpy(), cut.cpu().numpy())
+
+
+def test_every_tone_chirping_with_the_engine(awg, oracle):
+    """Every tone holds a long linear or minimum-jerk chirp in the window, so the engine's render
+    part takes all K tones without a tone list (chirps in linear and LOW6 form visited in their
+    groups, without the lane-pair set-up sharing of the direct path): against the oracle at sampled
+    indices and within one LSB of the direct render."""
+    rng = np.random.default_rng(29)
+    K, n, n0 = 64, 60_000, 1_000_000
+    f = rng.uniform(20e6, 120e6, K)
+    a = rng.uniform(0.2, 1.0, K) / K
+    th = rng.uniform(0, 2 * np.pi, K)
+    chirps = [dict(tone=k, f_start=float(f[k]), f_end=float(rng.uniform(20e6, 120e6)), duration=20e-3,
+                   profile=k % 2, start_sample=int(rng.integers(0, 4096))) for k in range(K)]
+
+    def make(engine):
+        s = awg.Synth(FS)
+        s.set_tones(f, a, th)
+        s.set_chirp_list(chirps)
+        if engine:
+            s.set_static_engine(awg.STATIC_GEMM_FP16)
+        return s
+
+    q_eng, _ = render(make(True), n, n0)
+    q_dir, _ = render(make(False), n, n0)
+    assert np.max(np.abs(q_eng.astype(np.int32) - q_dir)) <= 1
+    w = oracle.make_waveform(FS, f, a, th, chirps)
+    idx = np.unique(np.concatenate([rng.integers(0, n, 500), [0, n - 1]]))
+    q_ref = oracle.quantize(oracle.render_at(w, idx + n0, nthreads=NTHREADS), w.full_scale())
+    assert np.max(np.abs(q_eng[idx].astype(np.int32) - q_ref)) <= 1
+    assert np.max(np.abs(q_dir[idx].astype(np.int32) - q_ref)) <= 1
