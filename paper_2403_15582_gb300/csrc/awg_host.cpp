@@ -424,6 +424,37 @@ bool low_order_negligible(uint64_t F0, uint64_t F1, int64_t L, int profile) {
   return words < 64.0 * 4294967296.0;
 }
 
+// Whether a TONE_LOW6 chirp may also drop B_5, E_3 and E_4 of its run set-up (TONE_LOW3): every
+// left-out stride difference, bounded as in low_order_negligible (B_q: 32^q max |P^(q)|, E_q: with
+// P^(q+1), G_q: with P^(q+2)), weighted by C(127, q) and by the 63 / 1953 steps a cascade that
+// spans two runs (a lane pair's moved state) takes f and g through, must stay below 256 units of
+// 2^-32 turn: with the rounding (1008.5) and the third differences (512) of such a cascade, below
+// the 2500 of an unshared minimum-jerk run.
+bool low3_negligible(uint64_t F0, uint64_t F1, int64_t L, int profile) {
+  const double l = (double)L;
+  double d4, d5, d6;
+  if (profile == AWG_PROFILE_MINJERK) {
+    const double D = std::fabs((double)F1 - (double)F0);
+    d4 = 60.0 * D / (l * l * l);
+    d5 = 360.0 * D / (l * l * l * l);
+    d6 = 720.0 * D / (l * l * l * l * l);
+  } else if (profile == AWG_PROFILE_EXPONENTIAL && F0 != F1) {
+    const double a = std::fabs(exp_params(F0, F1, L).alpha) * 1.01;
+    const double Fm = (double)std::max(F0, F1) * 1.01;
+    d4 = Fm * a * a * a;
+    d5 = d4 * a;
+    d6 = d5 * a;
+  } else {
+    return false;
+  }
+  const double c2 = 8001.0, c3 = 333375.0, c4 = 10334625.0, c5 = 254231775.0, c6 = 5169379425.0;
+  const double p2 = 1024.0, p3 = 32768.0, p4 = 1048576.0, p5 = 33554432.0, p6 = 1073741824.0;   // 32^q
+  const double B = p5 * d5 * c5 + p6 * d6 * c6;
+  const double E = p3 * d4 * c3 + p4 * d5 * c4 + p5 * d6 * c5;
+  const double G = p2 * d4 * c2 + p3 * d5 * c3 + p4 * d6 * c4;
+  return B + 63.0 * E + 1953.0 * G < 256.0 * 4294967296.0;
+}
+
 // Whether two lanes may share the chirp's run set-up (TONE_PAIR): the render then takes a run's
 // cascade state from the neighbouring run's exact set-up, moved by 32 samples with the cascade's
 // integer steps, so a cascade spans up to 63 steps instead of 31.  Linear chirps: the third
@@ -1729,7 +1760,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   struct Coeffs {
     W192 d[7];
     uint64_t end_offset;
-    bool exact, flat3, low6, pair;
+    bool exact, flat3, low6, low3, pair;
     float rot_c, rot_s;   // rotator constants of F_end
   };
   std::vector<Coeffs> co(pend.size());
@@ -1743,6 +1774,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
       co[i].flat3 = flat_third_difference(p.F0, p.F1, p.L, p.profile);
       co[i].low6 = co[i].flat3 && low_order_negligible(p.F0, p.F1, p.L, p.profile);
       co[i].pair = !co[i].exact && pair_setup_ok(p.F0, p.F1, p.L, p.profile, co[i].low6);
+      co[i].low3 = co[i].low6 && low3_negligible(p.F0, p.F1, p.L, p.profile);
       rotation_of(p.F1, &co[i].rot_c, &co[i].rot_s);
     }
   };
@@ -1781,7 +1813,8 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     c.tone = p.tone;
     c.flags = (co[pi].exact ? awgk::TONE_EXACT : 0) | (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0) |
               (p.profile == AWG_PROFILE_EXPONENTIAL ? awgk::TONE_EXP : 0) | (co[pi].flat3 ? awgk::TONE_FLAT3 : 0) |
-              (co[pi].low6 ? awgk::TONE_LOW6 : 0) | (co[pi].pair ? awgk::TONE_PAIR : 0);
+              (co[pi].low6 ? awgk::TONE_LOW6 : 0) | (co[pi].low3 ? awgk::TONE_LOW3 : 0) |
+              (co[pi].pair ? awgk::TONE_PAIR : 0);
     const uint64_t phi_end = c.phi_start + co[pi].end_offset;
     t.slot = slot;
     t.n_s = p.ns;

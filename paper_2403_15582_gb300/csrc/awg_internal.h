@@ -52,6 +52,8 @@ constexpr int32_t TONE_FLAT3 = 32;        // the chirp's third unit difference s
                                           // the run cascade's h rounds to 0 in every run
 constexpr int32_t TONE_LOW6 = 64;         // FLAT3, and B_6, E_5, G_2..G_4 move a run's phase by
                                           // < 64 units of 2^-32 turn: left out of the run set-up
+constexpr int32_t TONE_LOW3 = 256;        // LOW6, and B_5, E_3, E_4 negligible too (< 256 units
+                                          // with the others over a two-run cascade): left out as well
 constexpr int32_t TONE_PAIR = 128;        // a lane pair may share the chirp's run set-up: linear, or
                                           // LOW6 with C(63,3) max |Delta^3 P| below 512 units of 2^-32
                                           // turn (the render's run set-up, see render_tile)

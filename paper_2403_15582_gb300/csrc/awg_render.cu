@@ -305,6 +305,22 @@ __device__ __forceinline__ RunPoly poly_state_low6(const TileRec& rc, const RunB
   return RunPoly{top_get(p), top_get(f), top_get(g), 0u};
 }
 
+// poly_state for a TONE_LOW3 chirp: LOW6, and B_5, E_3, E_4 left out as well (the set-up bounds all
+// left-out terms below 256 units of 2^-32 turn over a two-run cascade).
+__device__ __forceinline__ RunPoly poly_state_low3(const TileRec& rc, const RunBin& b) {
+  Top32 p = top_init(rc.B[0]);
+  top_mac(p, rc.B[1], b.c1);
+  top_mac(p, rc.B[2], b.c2);
+  top_mac(p, rc.B[3], b.c3);
+  top_mac(p, rc.B[4], b.c4);
+  Top32 f = top_init(rc.E[0]);
+  top_mac(f, rc.E[1], b.c1);
+  top_mac(f, rc.E[2], b.c2);
+  Top32 g = top_init(rc.G[0]);
+  top_mac(g, rc.G[1], b.c1);
+  return RunPoly{top_get(p), top_get(f), top_get(g), 0u};
+}
+
 
 __device__ __forceinline__ uint32_t static_p0(uint64_t phi_ref, uint64_t F, int64_t n0) {
   return (uint32_t)((phi_ref + (uint64_t)n0 * F + P_OFFSET) >> 32);
@@ -848,11 +864,13 @@ struct alignas(16) Desc {
 };
 enum { DESC_STATIC = 0, DESC_LINEAR = 1, DESC_MINJERK = 2, DESC_MIXED = 3, DESC_STATIC_ROT = 4, DESC_SKIP = 5,
        DESC_FLAT3 = 6,     // FLAT3: a degree-6 chirp whose h is 0 in every run (TONE_FLAT3)
-       DESC_LOW6 = 7 };    // LOW6: FLAT3 without the negligible high orders (TONE_LOW6)
+       DESC_LOW6 = 7,      // LOW6: FLAT3 without the negligible high orders (TONE_LOW6)
+       DESC_LOW3 = 8 };    // LOW3: LOW6 without B_5, E_3, E_4 (TONE_LOW3)
 
 // Kind of a chirp tile that the chirp covers from start to end (no table, no ramp in the tile).
 __device__ __forceinline__ int chirp_inside_kind(int32_t flags) {
-  return (flags & TONE_LINEAR) ? DESC_LINEAR : (flags & TONE_LOW6) ? DESC_LOW6 : (flags & TONE_FLAT3) ? DESC_FLAT3 : DESC_MINJERK;
+  return (flags & TONE_LINEAR) ? DESC_LINEAR : (flags & TONE_LOW3) ? DESC_LOW3 : (flags & TONE_LOW6) ? DESC_LOW6
+         : (flags & TONE_FLAT3) ? DESC_FLAT3 : DESC_MINJERK;
 }
 
 // Descriptor kind of a tone in the tile [T0, T0 + TILE): DESC_STATIC for a static segment (the
@@ -874,12 +892,15 @@ __device__ __forceinline__ int tile_kind(const ToneRec& tr, int64_t T0, bool ski
 }
 
 // Visit group of a stage's tone: chirps in linear form that may share their run set-up (TONE_PAIR),
-// the other linear ones, the same two for LOW6 form, static segments, then the rest (every tone of
-// a listed render).  Shared set-ups only in renders without the tensor-core engine (pair false).
-enum { GRP_LIN_PAIR = 0, GRP_LIN = 1, GRP_LOW6_PAIR = 2, GRP_LOW6 = 3, GRP_STATIC = 4, GRP_REST = 5, N_GRP = 6 };
+// the other linear ones, chirps in LOW3 form that may share it, the same two for LOW6 form, static
+// segments, then the rest (every tone of a listed render; LOW3 chirps that may not share).  Shared
+// set-ups only in renders without the tensor-core engine (pair false).
+enum { GRP_LIN_PAIR = 0, GRP_LIN = 1, GRP_LOW3_PAIR = 2, GRP_LOW6_PAIR = 3, GRP_LOW6 = 4, GRP_STATIC = 5, GRP_REST = 6,
+       N_GRP = 7 };
 __device__ __forceinline__ int visit_group(int kind, bool listed, bool pair) {
   if (listed) return GRP_REST;
   if (kind == DESC_LINEAR) return pair ? GRP_LIN_PAIR : GRP_LIN;
+  if (kind == DESC_LOW3) return pair ? GRP_LOW3_PAIR : GRP_REST;
   if (kind == DESC_LOW6) return pair ? GRP_LOW6_PAIR : GRP_LOW6;
   return (kind == DESC_STATIC || kind == DESC_STATIC_ROT) ? GRP_STATIC : GRP_REST;
 }
@@ -1199,11 +1220,12 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
     ok = __all_sync(0xffffffffu, ok);
     if (ok) {
       const int cnt = min(STAGE, l_end - (l_begin + st * STAGE));
-      const int e_lp = s_ngrp[b][GRP_LIN_PAIR], e_lin = s_ngrp[b][GRP_LIN], e_l6p = s_ngrp[b][GRP_LOW6_PAIR],
-                e_low6 = s_ngrp[b][GRP_LOW6], e_static = s_ngrp[b][GRP_STATIC];
+      const int e_lp = s_ngrp[b][GRP_LIN_PAIR], e_lin = s_ngrp[b][GRP_LIN], e_l3p = s_ngrp[b][GRP_LOW3_PAIR],
+                e_l6p = s_ngrp[b][GRP_LOW6_PAIR], e_low6 = s_ngrp[b][GRP_LOW6], e_static = s_ngrp[b][GRP_STATIC];
       auto linear = [&](int i) { cascade<0, RUN, false>(poly_state(s_rec[b][i], rb0, true), s_desc[b][i].A, acc); };
       // LOW6, FLAT3: the third difference rounds to 0 everywhere (set-up bound), g is constant
       auto low6 = [&](int i) { cascade<0, RUN, false>(poly_state_low6(s_rec[b][i], rb0), s_desc[b][i].A, acc); };
+      auto low3 = [&](int i) { cascade<0, RUN, false>(poly_state_low3(s_rec[b][i], rb0), s_desc[b][i].A, acc); };
       auto flat3 = [&](int i) { cascade<0, RUN, false>(poly_state_flat3(s_rec[b][i], rb0), s_desc[b][i].A, acc); };
       auto static_sfu = [&](int i) {
         const Desc& d = s_desc[b][i];
@@ -1239,14 +1261,22 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
         cascade<0, RUN, false>(odd ? own : oth, s_desc[b][k].A, acc);
       }
       for (int o = e_lp & ~1; o < e_lin; ++o) linear(s_order[b][o]);
-      for (int o = e_lin; o + 1 < e_l6p; o += 2) {
+      for (int o = e_lin; o + 1 < e_l3p; o += 2) {
+        const int i = s_order[b][o], k = s_order[b][o + 1];
+        const RunPoly own = poly_state_low3(s_rec[b][odd ? k : i], rb0);
+        const RunPoly oth = partner_state(own, odd);
+        cascade<0, RUN, false>(odd ? oth : own, s_desc[b][i].A, acc);
+        cascade<0, RUN, false>(odd ? own : oth, s_desc[b][k].A, acc);
+      }
+      if ((e_l3p - e_lin) & 1) low3(s_order[b][e_l3p - 1]);
+      for (int o = e_l3p; o + 1 < e_l6p; o += 2) {
         const int i = s_order[b][o], k = s_order[b][o + 1];
         const RunPoly own = poly_state_low6(s_rec[b][odd ? k : i], rb0);
         const RunPoly oth = partner_state(own, odd);
         cascade<0, RUN, false>(odd ? oth : own, s_desc[b][i].A, acc);
         cascade<0, RUN, false>(odd ? own : oth, s_desc[b][k].A, acc);
       }
-      for (int o = e_lin + ((e_l6p - e_lin) & ~1); o < e_low6; ++o) low6(s_order[b][o]);
+      for (int o = e_l3p + ((e_l6p - e_l3p) & ~1); o < e_low6; ++o) low6(s_order[b][o]);
       if (a.sine_mode == SINE_ROTATOR) {
         for (int o = e_low6; o < e_static; ++o) static_rot(s_order[b][o]);
       } else {
@@ -1266,6 +1296,8 @@ __device__ __forceinline__ void render_tile(const RenderArgs& a, const int tile,
           linear(i);
         } else if (kind == DESC_LOW6) {
           low6(i);
+        } else if (kind == DESC_LOW3) {
+          low3(i);
         } else if (kind == DESC_FLAT3) {
           flat3(i);
         } else if (kind == DESC_MINJERK) {
@@ -1391,7 +1423,8 @@ __device__ __noinline__ uint32_t phase32_at(const ToneRec& t, const TileRec* rec
     const bool moved = (role == 1 && odd) || (role == 2 && !odd);
     const int js = moved ? (odd ? j - 1 : j + 1) : j;
     const RunBin b = run_binomials(js);
-    q = kind == DESC_LOW6 ? poly_state_low6(*rec, b)
+    q = kind == DESC_LOW3 ? poly_state_low3(*rec, b)
+        : kind == DESC_LOW6 ? poly_state_low6(*rec, b)
         : kind == DESC_FLAT3 ? poly_state_flat3(*rec, b) : poly_state(*rec, b, kind == DESC_LINEAR);
     if (moved) {
       if (odd) {
@@ -1430,7 +1463,7 @@ __global__ void exact_table_kernel(const __grid_constant__ TableArgs a, int64_t 
 __device__ __noinline__ int pair_role(const TraceArgs& a, int k, int64_t T0) {
   if (a.listed || !(a.tones[k].flags & TONE_PAIR)) return 0;
   const int g = visit_group(tile_kind(a.tones[k], T0, false), false, true);
-  if (g != GRP_LIN_PAIR && g != GRP_LOW6_PAIR) return 0;
+  if (g != GRP_LIN_PAIR && g != GRP_LOW3_PAIR && g != GRP_LOW6_PAIR) return 0;
   const int64_t K = a.K, S = a.split;
   int c = (int)((int64_t)k * S / K);
   while (c + 1 < S && K * (c + 1) / S <= k) ++c;
