@@ -43,8 +43,8 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # DRAM traffic (ncu dram__bytes_read.sum + dram__bytes_write.sum) of one render launch of the timed
 # step (a 2^18-sample chunk of the 1000-chirp record), from one ncu capture of the render kernel as
 # it stands in this file's revision; None when the kernel has changed since that capture.
-RENDER_TRAFFIC_BYTES = 11.929344e6
-RENDER_TRAFFIC_SOURCE = "ncu --set full capture of one render_split_kernel launch (2^18 samples, 1000 chirps; shared run set-up, 7 CTAs per SM)"
+RENDER_TRAFFIC_BYTES = 11.92832e6
+RENDER_TRAFFIC_SOURCE = "ncu --set full capture of one render_split_kernel launch (2^18 samples, 1000 chirps; shared LOW3 run set-up, 7 CTAs per SM)"
 
 CLOCK_FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
                 "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
