@@ -120,8 +120,8 @@ def test_render_phase_cascade_within_bound(awg, oracle, dur_ms):
     """The 32-bit phases the kernel feeds to the sine stay within the stated bound of the exact
     words: 2500 units of 2^-32 turn for minimum-jerk runs (g, h rounding over 31 steps of a
     32-sample run; or, where two lanes share a run set-up and a cascade spans 63 steps, f and g
-    rounding over 63 steps plus the neglected third order and LOW6 terms, 31.5 + 976.5 + 512 +
-    269), 1100 for linear chirps (f and g rounding over 63 steps: 31.5 + 976.5), 40 for static
+    rounding over 63 steps plus the neglected third order and the left-out LOW6 or LOW3 terms,
+    31.5 + 976.5 + 512 + 269), 1100 for linear chirps (f and g rounding over 63 steps: 31.5 + 976.5), 40 for static
     segments.  Tones 0 and 2 (minimum-jerk) and 1 and 4 (linear) form the render's lane pairs
     where their chirps allow it, so both roles of a shared set-up are traced."""
     fs = 280e6
