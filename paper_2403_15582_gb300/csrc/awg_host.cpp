@@ -667,8 +667,9 @@ int ensure(T** ptr, size_t* cap, size_t need, awg_t* h, const char* what) {
 
 // Host worker threads for the set-up arithmetic of large chirp batches, started once per process
 // (starting threads per call cost more than the work at 1000 chirps).  parallel_for(n, fn) runs
-// fn(lo, hi) over [0, n) in `parts` ranges, one on the calling thread, and returns when all are
-// done.  Calls are serialised.
+// fn(lo, hi) over [0, n) in `parts` ranges, which the calling thread and the workers claim one at
+// a time (so a worker that wakes late delays nothing but the range it takes), and returns when all
+// are done.  Calls are serialised.
 class HostPool {
  public:
   static HostPool& get() {
@@ -677,8 +678,8 @@ class HostPool {
   }
   size_t threads() const { return workers_.size() + 1; }
   void parallel_for(size_t n, size_t parts, const std::function<void(size_t, size_t)>& fn) {
-    parts = std::max<size_t>(1, std::min(parts, threads()));
-    if (parts == 1) {
+    parts = std::max<size_t>(1, std::min(parts, 8 * threads()));
+    if (parts == 1 || threads() == 1) {
       fn(0, n);
       return;
     }
@@ -688,12 +689,22 @@ class HostPool {
       fn_ = &fn;
       n_ = n;
       parts_ = parts;
-      next_ = 1;
-      pending_ = parts - 1;
+      next_ = 0;
+      pending_ = parts;
       ++gen_;
     }
     cv_.notify_all();
-    fn(0, n / parts);   // part 0 here
+    for (;;) {   // the calling thread claims ranges too
+      size_t part;
+      {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (next_ >= parts_) break;
+        part = next_++;
+      }
+      fn(n * part / parts, n * (part + 1) / parts);
+      std::lock_guard<std::mutex> lk(mu_);
+      --pending_;
+    }
     std::unique_lock<std::mutex> lk(mu_);
     done_cv_.wait(lk, [&] { return pending_ == 0; });
     fn_ = nullptr;
