@@ -92,6 +92,20 @@ int awg_chirp_length(double duration_s, double fs_hz, int64_t* out_L);
  * F_end is 0.  With F_start == F_end the chirp is the linear one (the same phase). */
 int awg_chirp_coeffs(uint64_t F_start, uint64_t F_end, int64_t L, int32_t profile, uint64_t* out21);
 
+/* Host-only classification hook: the flags the render gives a chirp from word F_start to word
+ * F_end over L samples, written to *out_flags, with the bounds that decide them (the paper has no
+ * counterpart; its run set-up is the library's own).  AWG_CHIRP_LINEAR / AWG_CHIRP_EXP: the
+ * profile; AWG_CHIRP_TABLE: rendered from a per-sample table of exact phases (very short, fast
+ * chirps); AWG_CHIRP_FLAT3: the third unit difference stays below 2^30 words (the run cascade's
+ * third difference rounds to 0); AWG_CHIRP_LOW6 / AWG_CHIRP_LOW3: the run set-up leaves out the
+ * stride differences it proves negligible (below 64 units of 2^-32 turn over a run, and all of
+ * them with B_5, E_3, E_4 below 256 units over a two-run cascade); AWG_CHIRP_PAIR: two lanes may
+ * share the chirp's run set-up (linear, or LOW6 with C(63,3) max |Delta^3 P| below 512 units).
+ * EINVAL as awg_set_chirps (L >= 1, known profile, exponential ends > 0). */
+enum { AWG_CHIRP_TABLE = 1, AWG_CHIRP_LINEAR = 2, AWG_CHIRP_EXP = 16, AWG_CHIRP_FLAT3 = 32, AWG_CHIRP_LOW6 = 64,
+       AWG_CHIRP_PAIR = 128, AWG_CHIRP_LOW3 = 256 };
+int awg_chirp_render_flags(uint64_t F_start, uint64_t F_end, int64_t L, int32_t profile, int32_t* out_flags);
+
 /* ------------------------------------------------------------------------------------------
  * Synthesiser handle (device-resident tone and chirp state).
  * ---------------------------------------------------------------------------------------- */

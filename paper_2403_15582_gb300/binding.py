@@ -27,6 +27,7 @@ SIGNATURES = [
     ("awg_grid_word", ctypes.c_int, [dbl, dbl, i32, P, P]),
     ("awg_chirp_length", ctypes.c_int, [dbl, dbl, P]),
     ("awg_chirp_coeffs", ctypes.c_int, [u64, u64, i64, i32, P]),
+    ("awg_chirp_render_flags", ctypes.c_int, [u64, u64, i64, i32, P]),
     ("awg_create", P, [dbl]),
     ("awg_destroy", None, [P]),
     ("awg_set_tones", ctypes.c_int, [P, P, P, P, i32]),
@@ -143,6 +144,16 @@ def grid_word(f_hz: float, fs: float, log2_len: int):
 def chirp_length(duration: float, fs: float) -> int:
     out = np.zeros(1, dtype=np.int64)
     _check(lib().awg_chirp_length(float(duration), float(fs), _p(out)))
+    return int(out[0])
+
+
+CHIRP_TABLE, CHIRP_LINEAR, CHIRP_EXP, CHIRP_FLAT3, CHIRP_LOW6, CHIRP_PAIR, CHIRP_LOW3 = 1, 2, 16, 32, 64, 128, 256
+
+
+def chirp_render_flags(F_start: int, F_end: int, L: int, profile: int) -> int:
+    """The render's flags of a chirp (host only): CHIRP_* bits, see awg_chirp_render_flags."""
+    out = np.zeros(1, dtype=np.int32)
+    _check(lib().awg_chirp_render_flags(int(F_start), int(F_end), int(L), int(profile), _p(out)))
     return int(out[0])
 
 

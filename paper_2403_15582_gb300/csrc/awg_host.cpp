@@ -24,6 +24,10 @@ using awgk::ToneRec;
 // The public limits of awg_render_noalloc are the sizes of its fixed scratch.
 static_assert(awgk::NOALLOC_MAX_RECORDS == AWG_NOALLOC_MAX_RECORDS, "awg.h: AWG_NOALLOC_MAX_RECORDS");
 static_assert(awgk::NOALLOC_MAX_SLOTS == AWG_NOALLOC_MAX_SLOTS, "awg.h: AWG_NOALLOC_MAX_SLOTS");
+static_assert(AWG_CHIRP_TABLE == awgk::TONE_EXACT && AWG_CHIRP_LINEAR == awgk::TONE_LINEAR && AWG_CHIRP_EXP == awgk::TONE_EXP &&
+                  AWG_CHIRP_FLAT3 == awgk::TONE_FLAT3 && AWG_CHIRP_LOW6 == awgk::TONE_LOW6 &&
+                  AWG_CHIRP_PAIR == awgk::TONE_PAIR && AWG_CHIRP_LOW3 == awgk::TONE_LOW3,
+              "awg.h: AWG_CHIRP_* flags");
 
 namespace {
 
@@ -468,6 +472,22 @@ bool pair_setup_ok(uint64_t F0, uint64_t F1, int64_t L, int profile, bool low6) 
   if (!low6) return false;
   const double bound = third_difference_bound(F0, F1, L, profile);
   return bound >= 0 && 39711.0 * bound < 512.0 * 4294967296.0;
+}
+
+bool needs_exact(uint64_t F0, uint64_t F1, int64_t L, int profile);
+
+// The render's flags of a chirp (ChirpRec::flags; the low bits of ToneRec::flags): its profile
+// (TONE_LINEAR, TONE_EXP), a per-sample table (TONE_EXACT), and the run set-up it takes (TONE_FLAT3,
+// TONE_LOW6, TONE_LOW3, TONE_PAIR), from the bounds above.
+int32_t chirp_render_flags(uint64_t F0, uint64_t F1, int64_t L, int profile) {
+  const bool exact = needs_exact(F0, F1, L, profile);
+  const bool flat3 = flat_third_difference(F0, F1, L, profile);
+  const bool low6 = flat3 && low_order_negligible(F0, F1, L, profile);
+  const bool pair = !exact && pair_setup_ok(F0, F1, L, profile, low6);
+  const bool low3 = low6 && low3_negligible(F0, F1, L, profile);
+  return (exact ? awgk::TONE_EXACT : 0) | (profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0) |
+         (profile == AWG_PROFILE_EXPONENTIAL ? awgk::TONE_EXP : 0) | (flat3 ? awgk::TONE_FLAT3 : 0) |
+         (low6 ? awgk::TONE_LOW6 : 0) | (low3 ? awgk::TONE_LOW3 : 0) | (pair ? awgk::TONE_PAIR : 0);
 }
 
 // Phase offset at the end of an exponential chirp, R(L), the same FP64 formula as the render's.
@@ -1638,6 +1658,18 @@ int awg_chirp_length(double duration_s, double fs_hz, int64_t* out_L) {
   return chirp_length_impl(duration_s, fs_hz, out_L);
 }
 
+int awg_chirp_render_flags(uint64_t F_start, uint64_t F_end, int64_t L, int32_t profile, int32_t* out_flags) {
+  if (!out_flags) return fail(AWG_EINVAL, "null output");
+  if (L < 1) return fail(AWG_EINVAL, "chirp length must be >= 1");
+  if (profile != AWG_PROFILE_LINEAR && profile != AWG_PROFILE_MINJERK && profile != AWG_PROFILE_EXPONENTIAL)
+    return fail(AWG_EINVAL, "unknown chirp profile");
+  if (profile == AWG_PROFILE_EXPONENTIAL && (F_start == 0 || F_end == 0))
+    return fail(AWG_EINVAL, "an exponential chirp needs f_start, f_end > 0");
+  if (profile == AWG_PROFILE_EXPONENTIAL && F_start == F_end) profile = AWG_PROFILE_LINEAR;
+  *out_flags = chirp_render_flags(F_start, F_end, L, profile);
+  return AWG_OK;
+}
+
 int awg_chirp_coeffs(uint64_t F_start, uint64_t F_end, int64_t L, int32_t profile, uint64_t* out21) {
   if (!out21) return fail(AWG_EINVAL, "null output");
   W192 d[7];
@@ -1771,7 +1803,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
   struct Coeffs {
     W192 d[7];
     uint64_t end_offset;
-    bool exact, flat3, low6, low3, pair;
+    int32_t flags;   // chirp_render_flags
     float rot_c, rot_s;   // rotator constants of F_end
   };
   std::vector<Coeffs> co(pend.size());
@@ -1781,11 +1813,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
       (void)chirp_coeffs_impl(p.F0, p.F1, p.L, p.profile, co[i].d);   // validated above
       co[i].end_offset = p.profile == AWG_PROFILE_EXPONENTIAL ? exp_end_offset(p.F0, p.F1, p.L)
                                                                : chirp_offset_word(co[i].d, p.L);
-      co[i].exact = needs_exact(p.F0, p.F1, p.L, p.profile);
-      co[i].flat3 = flat_third_difference(p.F0, p.F1, p.L, p.profile);
-      co[i].low6 = co[i].flat3 && low_order_negligible(p.F0, p.F1, p.L, p.profile);
-      co[i].pair = !co[i].exact && pair_setup_ok(p.F0, p.F1, p.L, p.profile, co[i].low6);
-      co[i].low3 = co[i].low6 && low3_negligible(p.F0, p.F1, p.L, p.profile);
+      co[i].flags = chirp_render_flags(p.F0, p.F1, p.L, p.profile);
       rotation_of(p.F1, &co[i].rot_c, &co[i].rot_s);
     }
   };
@@ -1822,10 +1850,7 @@ int awg_set_chirps(awg_t* h, const int32_t* tone, const double* f_start_hz, cons
     c.n_s = p.ns;
     c.L = p.L;
     c.tone = p.tone;
-    c.flags = (co[pi].exact ? awgk::TONE_EXACT : 0) | (p.profile == AWG_PROFILE_LINEAR ? awgk::TONE_LINEAR : 0) |
-              (p.profile == AWG_PROFILE_EXPONENTIAL ? awgk::TONE_EXP : 0) | (co[pi].flat3 ? awgk::TONE_FLAT3 : 0) |
-              (co[pi].low6 ? awgk::TONE_LOW6 : 0) | (co[pi].low3 ? awgk::TONE_LOW3 : 0) |
-              (co[pi].pair ? awgk::TONE_PAIR : 0);
+    c.flags = co[pi].flags;
     const uint64_t phi_end = c.phi_start + co[pi].end_offset;
     t.slot = slot;
     t.n_s = p.ns;
